@@ -1,0 +1,199 @@
+/*
+ * flapw.h -- C ABI of the GB300 (sm_103a) muffin-tin Hamiltonian/overlap builder.
+ *
+ * The library computes, for every k-point of a crystal, the LAPW matching
+ * coefficients A and B and the muffin-tin Hamiltonian H and overlap S
+ * (Davidovic et al., "Accelerating the computation of FLAPW methods on
+ * heterogeneous architectures", Sec. 2 and Sec. 3):
+ *
+ *   A^{a,G}_{lm}, B^{a,G}_{lm}   matching coefficients          Sec. 2, Eq. (basis)
+ *   S = sum_a A_a^H A_a + B_a^H U_a^H U_a B_a                    Eq. (s), Eq. (def_overlap)
+ *   H = sum_a [A_a;B_a]^H [[T^AA T^AB];[T^BA T^BB]]_a [A_a;B_a]  Eq. (h), Eq. (def_hamilton)
+ *
+ * Plain pointers and sizes only.  Complex numbers are interleaved pairs of
+ * doubles (re, im), the layout of C99 double _Complex and cuDoubleComplex.
+ *
+ * Conventions used by every call:
+ *   lattice     double[9], rows are the lattice vectors a1, a2, a3 (bohr).
+ *   k_frac      k-points in fractional coordinates of the reciprocal basis.
+ *   N_L         (lmax+1)^2; the index L = l*l + l + m, -l <= m <= l.
+ *   Y_lm        complex, orthonormal, Condon-Shortley phase.
+ *   A_{lm}(G)   = 4 pi / sqrt(Omega) e^{i (k+G).tau_a} i^l conj(Y_lm(K_hat)) a_l(|K|),
+ *   B_{lm}(G)   = same with b_l, where (a_l, b_l) solve
+ *                 a u(R) + b udot(R) = j_l(|K| R),  a u'(R) + b udot'(R) = |K| j_l'(|K| R)
+ *                 (continuity of value and slope at the sphere, Sec. 2).  K = k+G.
+ *   G order     ascending |k+G|^2 quantised to 2^-40 K_max^2, ties by (n1,n2,n3).
+ *   H, S        row G', column G; only the lower triangle G' >= G is written.
+ *
+ * Errors: every call returns FLAPW_OK (0) or a negative FLAPW_ERR_* code and
+ * records a message readable with flapw_last_error(handle) (or with a NULL
+ * handle for calls that have none).  Work is enqueued asynchronously on the
+ * given CUDA stream; errors detected on the device (a bounded wait that ran
+ * out) are reported by flapw_sync().  A handle is not thread-safe.
+ */
+#ifndef FLAPW_H
+#define FLAPW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct flapw_ctx* flapw_handle;
+
+#define FLAPW_OK 0
+#define FLAPW_ERR_ARG (-1)         /* invalid argument: the message names it */
+#define FLAPW_ERR_CUDA (-2)        /* a CUDA runtime or driver call failed */
+#define FLAPW_ERR_OOM (-3)         /* device memory could not be allocated */
+#define FLAPW_ERR_FACTOR (-4)      /* a T block has a zero 2x2 pivot and cannot be factorised */
+#define FLAPW_ERR_TIMEOUT (-5)     /* a bounded device-side wait ran out; results are invalid */
+#define FLAPW_ERR_STATE (-6)       /* call out of order (e.g. a handle made for flapw_herk only) */
+#define FLAPW_ERR_UNSUPPORTED (-7) /* size outside what the kernels support */
+
+#define FLAPW_PREC_FP64 0 /* plain FP64 contraction (DMMA tensor cores) */
+#define FLAPW_PREC_EMU 1  /* split-precision emulation of complex FP64 on FP16 tensor cores */
+
+#define FLAPW_LAYOUT_LOWER_FULL 0   /* element (i, j), i >= j, at j*ld + i (column-major) */
+#define FLAPW_LAYOUT_LOWER_PACKED 1 /* LAPACK 'L' packed: j*N - j*(j-1)/2 + (i - j) */
+
+#define FLAPW_OPERANDS_FROM_AB 0  /* build_HS forms its operands from the A, B it is given */
+#define FLAPW_OPERANDS_FACTORED 1 /* build_HS regenerates the per-type part of A, B itself */
+
+typedef struct flapw_options {
+  int precision; /* FLAPW_PREC_EMU (default) or FLAPW_PREC_FP64 */
+  int n_slices;  /* emulation: 7-bit slices per operand entry, 4..9 (0 = default 7) */
+  int layout;    /* FLAPW_LAYOUT_LOWER_FULL (default) or FLAPW_LAYOUT_LOWER_PACKED */
+  int operands;  /* FLAPW_OPERANDS_FROM_AB (default) or FLAPW_OPERANDS_FACTORED */
+  int use_graph; /* 1: capture build_HS into a CUDA graph and replay it while the
+                    arguments repeat (default 0) */
+  int autotune;  /* 1: time the contraction's tile-order variants once per shape and
+                    keep the fastest (default 0: fixed choice) */
+  int reserved[10];
+} flapw_options;
+
+typedef struct flapw_stats {
+  double ms_ab;        /* last build_AB, device time (ms), if timing was on */
+  double ms_factor;    /* last build_HS: T factorisation */
+  double ms_operands;  /* operand formation */
+  double ms_slice;     /* slicing (emulated precision only) */
+  double ms_contract;  /* contraction */
+  double ms_hs_total;  /* whole build_HS */
+  double flops_herk;   /* 16 N_A N_L sum_k N_G(k)^2: H and S in the Hermitian rank-K count */
+  double flops_tensor; /* tensor-core flops executed by the contraction */
+  int64_t k_total;     /* inner dimension K = 2 N_A N_L */
+  int n_pos;           /* rows of the H operand with sigma = +1 (all atoms) */
+  int n_neg;           /* rows with sigma = -1 */
+  int n_pivot2;        /* 2x2 pivots taken by the factorisation (all slots) */
+  int n_slices;        /* slices used (emulated precision) */
+  int n_tiles;         /* output tiles of the last contraction launch */
+  int tile_order;      /* tile-order variant in use */
+  int graph_replays;   /* build_HS calls served by CUDA-graph replay */
+  int reserved[8];
+} flapw_stats;
+
+/* Defaults listed in flapw_options. */
+void flapw_default_options(flapw_options* opt);
+
+/* Plane-wave set of Sec. 2: all integer n with |(n + k_frac) . B| <= kmax,
+ * B the reciprocal basis (b_i = 2 pi (a_j x a_k) / (a_1 . (a_2 x a_3))), in the
+ * order stated above.  Host-only; needs no GPU.  Writes *n_g (always) and up
+ * to max_g triples into n3[i*3 + 0..2] (n3 may be NULL to query the count).
+ * Errors: FLAPW_ERR_ARG for a singular lattice, kmax <= 0 or NULL n_g. */
+int flapw_enumerate_g(const double lattice[9], const double k_frac[3], double kmax, int max_g,
+                      int* n3, int* n_g);
+
+/* Creates a handle for one crystal (Sec. 2; sizes as in Sec. 3, "typical values").
+ *   n_atoms, pos_frac[n_atoms*3]  fractional atom positions (copied)
+ *   atom_type[n_atoms]            type index in [0, n_types) (copied)
+ *   mt_radius[n_types]            muffin-tin radius per type, > 0
+ *   lmax                          0..12
+ *   n_k, k_frac[n_k*3], kmax[n_k] k-points and their cut-offs (copied)
+ *   opt                           NULL for defaults
+ * Enumerates every k-point's plane waves on the host and uploads the
+ * geometry to the current CUDA device.  Device workspaces are allocated on
+ * first use and released by flapw_destroy.  *out receives the handle. */
+int flapw_hs_create(const double lattice[9], int n_atoms, const double* pos_frac,
+                    const int* atom_type, int n_types, const double* mt_radius, int lmax,
+                    int n_k, const double* k_frac, const double* kmax,
+                    const flapw_options* opt, flapw_handle* out);
+
+/* A handle without a crystal, usable only with flapw_herk. */
+int flapw_engine_create(const flapw_options* opt, flapw_handle* out);
+
+/* Replaces the handle's options (takes effect at the next build call). */
+int flapw_set_options(flapw_handle h, const flapw_options* opt);
+
+/* Number of plane waves N_G(k) of k-point k. */
+int flapw_num_g(flapw_handle h, int k, int* n_g);
+
+/* The plane waves of k-point k as integer triples n3[i*3 + 0..2], i < N_G(k). */
+int flapw_get_gvectors(flapw_handle h, int k, int* n3);
+
+/* Offset, in complex elements, of k-point k's block inside the A and B
+ * buffers of flapw_build_AB; offset(n_k) is the total element count. */
+int flapw_ab_offset(flapw_handle h, int k, int64_t* offset);
+
+/* Matching coefficients A and B of Sec. 2, Eq. (basis), for every k-point and atom.
+ *   radial[n_types*(lmax+1)*4] (host): u_l(R), u_l'(R), udot_l(R), udot_l'(R)
+ *                                      per (type, l); copied.
+ *   A, B: complex128 buffers of flapw_ab_offset(h, n_k) elements, device or
+ *         host memory (host memory is staged through the device).  Element
+ *         (k, a, L, G) sits at offset(k) + (a*N_L + L)*N_G(k) + G.
+ * The radial data is retained by the handle for FLAPW_OPERANDS_FACTORED. */
+int flapw_build_AB(flapw_handle h, const double* radial, void* A, void* B, void* stream);
+
+/* Hamiltonian and overlap of Eqs. (h) and (s) for every k-point.
+ *   T[n_slots*(2N_L)^2] (host, complex row-major): per slot the Hermitian
+ *       matrix [[T^AA, T^AB],[T^BA, T^BB]], rows/cols [A-part L; B-part L];
+ *       only its lower triangle is read.
+ *   atom_slot[n_atoms] (host): which T block each atom uses.
+ *   U[n_types*(lmax+1)] (host): ||udot_l|| per (type, l); S carries U^2.
+ *   A, B: the buffers written by flapw_build_AB (device or host memory);
+ *       ignored (may be NULL) with FLAPW_OPERANDS_FACTORED, which requires a
+ *       previous flapw_build_AB on this handle for the radial data.
+ *   H[n_k], S[n_k]: per k-point output pointers (device or host memory),
+ *       complex128, lower triangle in the handle's layout; the full layout
+ *       uses ld = N_G(k).  Elements above the diagonal are not written.
+ * Each T block is factorised as T = C diag(sigma) C^H (Bunch-Kaufman
+ * pivoted LDL^H, then 2x2 eigen-splitting; Sec. 3, Alg. 1's Cholesky step
+ * generalised to indefinite T), so that H = Z^H diag(sigma) Z with
+ * Z_a = C^H [A_a; B_a] and S = Z_S^H Z_S with Z_S,a = [A_a; U B_a]: one
+ * lower-triangle rank-K contraction each, K = 2 N_A N_L (Fig. agg stacking).
+ * Errors: FLAPW_ERR_FACTOR if a block is singular in a way the pivoting
+ * cannot handle; FLAPW_ERR_OOM if the workspaces do not fit. */
+int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom_slot,
+                   const double* U, const void* A, const void* B, void* const* H,
+                   void* const* S, void* stream);
+
+/* The contraction step alone: lower triangle of Z^H diag(sigma) Z.
+ *   Z: device, complex128, column-major K x N (element (k, g) at g*ldz + k).
+ *   sigma[K] (host): +1 or -1 per row, or NULL for all +1.
+ *   H: device or host, complex128, layout/ld as in flapw_build_HS (ldh >= N).
+ * Precision and slice count come from the handle's options. */
+int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const int* sigma,
+               void* H, int64_t ldh, void* stream);
+
+/* Waits for the handle's enqueued work; reports device-side errors. */
+int flapw_sync(flapw_handle h);
+
+/* Statistics of the last calls (stage times need flapw_sync first). */
+int flapw_get_stats(flapw_handle h, flapw_stats* st);
+
+/* Debug export of the last T factorisation of slot `slot`: CH[(2N_L)^2]
+ * complex row-major receives C^H with its rows ordered sigma = +1 first,
+ * then -1; *n_pos and *n_neg give the counts (rows past them are zero).
+ * Synchronises the stream. */
+int flapw_get_factor(flapw_handle h, int slot, double* CH, int* n_pos, int* n_neg);
+
+/* Message for the last error on h (or of the last handle-less call if h is NULL). */
+const char* flapw_last_error(flapw_handle h);
+
+/* Releases the handle and every device workspace it owns. */
+int flapw_destroy(flapw_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

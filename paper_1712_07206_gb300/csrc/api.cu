@@ -1,0 +1,915 @@
+// C ABI of the muffin-tin H/S builder: handle, workspaces and the enqueue
+// sequence of each call.  See include/flapw.h for the contract of every entry
+// point; the kernels live in the other translation units.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "flapw_internal.h"
+
+using namespace flapw;
+
+namespace {
+
+std::string g_last_error;  // errors of calls without a handle
+
+// Device buffer that grows on demand.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes && p) return cudaSuccess;
+    release();
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      (void)cudaGetLastError();
+      return e;
+    }
+    bytes = n;
+    return cudaSuccess;
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+// Pinned host staging that grows on demand.
+struct PinBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~PinBuf() {
+    if (p) cudaFreeHost(p);
+  }
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes && p) return cudaSuccess;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMallocHost(&p, n ? n : 16);
+    if (e == cudaSuccess) bytes = n ? n : 16;
+    return e;
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct flapw_ctx {
+  std::string err;
+  flapw_options opt{};
+  bool engine_only = false;
+  int device = 0;
+  int num_sms = 0;
+
+  // crystal
+  double lat[9]{}, rec[9]{}, volume = 0;
+  int n_atoms = 0, n_types = 0, lmax = 0, n_L = 0, n_k = 0;
+  std::vector<double> pos, radius, kfrac, kmax, ktau;
+  std::vector<int> type;
+  std::vector<std::vector<int>> n3;
+  std::vector<int64_t> goff;
+  int64_t g_total = 0;
+  std::vector<int> gt128, gt64;
+
+  DevBuf d_rec, d_pos, d_type, d_radius, d_kfrac, d_ktau, d_n3, d_gk, d_goff, d_coef, d_gt128,
+      d_gt64;
+
+  // radial data from build_AB
+  std::vector<double> radial;
+  bool have_radial = false;
+  DevBuf d_radial;
+  DevBuf d_Yc, d_al, d_bl, d_ph;
+  bool prep_valid = false;
+
+  // build_HS workspaces
+  DevBuf d_T, d_work, d_CH, d_cnt, d_slot, d_U, d_off, d_probs, d_rowprob, d_Z, d_SL, d_rexp,
+      d_emu_tiles, d_f64_tiles, d_combo, d_kmap, d_stageA, d_stageB, d_stageOut;
+  PinBuf pin_in, pin_probs;
+  int64_t k_alloc = 0, rows = 0;
+  int n_emu_tiles = 0, n_f64_tiles = 0, tiles_order = -1;
+  int64_t tiles_rows_key = -1;
+  CUtensorMap tmap{};
+  void* tmap_base = nullptr;
+  int64_t tmap_k = 0, tmap_rows = 0;
+  int tmap_s = 0;
+
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev[8]{};
+  bool ev_recorded = false, ev_ab = false;
+  cudaStream_t last_stream = nullptr;
+  flapw_stats stats{};
+  int last_n_slots = 0;
+
+  // CUDA graph replay of build_HS
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uintptr_t> gkey;
+
+  ~flapw_ctx() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
+};
+
+namespace {
+
+int fail(flapw_ctx* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(flapw_ctx* h, cudaError_t e, const char* what) {
+  const int code = (e == cudaErrorMemoryAllocation) ? FLAPW_ERR_OOM : FLAPW_ERR_CUDA;
+  return fail(h, code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, expr, what)                              \
+  do {                                                 \
+    cudaError_t _e = (expr);                           \
+    if (_e != cudaSuccess) return cuda_fail(h, _e, what); \
+  } while (0)
+
+int check_options(flapw_ctx* h, const flapw_options& o) {
+  if (o.precision != FLAPW_PREC_FP64 && o.precision != FLAPW_PREC_EMU)
+    return fail(h, FLAPW_ERR_ARG, "options.precision must be FLAPW_PREC_FP64 or FLAPW_PREC_EMU");
+  if (o.n_slices != 0 && (o.n_slices < 4 || o.n_slices > 8))
+    return fail(h, FLAPW_ERR_ARG, "options.n_slices must be 0 or in 4..8");
+  if (o.layout != FLAPW_LAYOUT_LOWER_FULL && o.layout != FLAPW_LAYOUT_LOWER_PACKED)
+    return fail(h, FLAPW_ERR_ARG, "options.layout is not a FLAPW_LAYOUT_* value");
+  if (o.operands != FLAPW_OPERANDS_FROM_AB && o.operands != FLAPW_OPERANDS_FACTORED)
+    return fail(h, FLAPW_ERR_ARG, "options.operands is not a FLAPW_OPERANDS_* value");
+  return FLAPW_OK;
+}
+
+int slices_of(const flapw_ctx* h) { return h->opt.n_slices ? h->opt.n_slices : 7; }
+
+int device_setup(flapw_ctx* h) {
+  CK(h, cudaGetDevice(&h->device), "cudaGetDevice");
+  CK(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device),
+     "cudaDeviceGetAttribute");
+  for (auto& e : h->ev) CK(h, cudaEventCreate(&e), "cudaEventCreate");
+  CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  CK(h, opform_init(), "constant table upload");
+  return FLAPW_OK;
+}
+
+template <class T>
+int upload(flapw_ctx* h, DevBuf& d, const std::vector<T>& v) {
+  CK(h, d.ensure(v.size() * sizeof(T)), "cudaMalloc");
+  if (!v.empty()) CK(h, cudaMemcpy(d.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "cudaMemcpy");
+  return FLAPW_OK;
+}
+
+// Emulated contraction tiles (128 x 64) and FP64 tiles (64 x 64) of every
+// problem's lower triangle.  order 0: row blocks outer; 1: column blocks outer.
+void make_tiles(const std::vector<Prob>& probs, int order, std::vector<EmuTile>* emu,
+                std::vector<F64Tile>* f64) {
+  emu->clear();
+  f64->clear();
+  for (int p = 0; p < (int)probs.size(); ++p) {
+    const int ng = probs[p].n_g;
+    const int nib = (ng + 127) / 128, njb = (ng + 63) / 64;
+    if (order == 0) {
+      for (int ib = 0; ib < nib; ++ib)
+        for (int jb = 0; jb < njb; ++jb)
+          if (jb * 64 <= ib * 128 + 127) emu->push_back(EmuTile{p, ib, jb, 0});
+    } else {
+      for (int jb = 0; jb < njb; ++jb)
+        for (int ib = 0; ib < nib; ++ib)
+          if (jb * 64 <= ib * 128 + 127) emu->push_back(EmuTile{p, ib, jb, 0});
+    }
+    const int nb = (ng + 63) / 64;
+    for (int ib = 0; ib < nb; ++ib)
+      for (int jb = 0; jb <= ib; ++jb) f64->push_back(F64Tile{p, ib, jb, 0});
+  }
+}
+
+// Output pointers: device pointers are used in place; host pointers get a
+// device staging area and a copy back after the contraction.
+struct OutPlan {
+  std::vector<double2*> dev;
+  std::vector<void*> host;
+  std::vector<size_t> bytes;
+  std::vector<size_t> stage_off;
+  size_t stage_bytes = 0;
+};
+
+size_t out_bytes(int layout, int64_t ng) {
+  return (layout == FLAPW_LAYOUT_LOWER_PACKED) ? (size_t)(ng * (ng + 1) / 2) * 16
+                                               : (size_t)(ng * ng) * 16;
+}
+
+// Enqueues the contraction of prepared operand rows (d_Z) into the outputs
+// described by `probs` (already uploaded to d_probs).
+int enqueue_contraction(flapw_ctx* h, const std::vector<Prob>& probs, cudaStream_t st) {
+  const int s = slices_of(h);
+  const int64_t rows = h->rows;
+  if (h->opt.precision == FLAPW_PREC_EMU) {
+    CK(h, h->d_SL.ensure((size_t)s * 2 * rows * h->k_alloc * 2), "slice workspace");
+    CK(h, launch_slicer(h->d_Z.as<double2>(), h->k_alloc, h->d_probs.as<Prob>(), (int)probs.size(),
+                        h->d_rowprob.as<int>(), rows, s, h->d_SL.as<__half>(), h->d_rexp.as<int>(), st),
+       "slicer launch");
+    CK(h, cudaEventRecord(h->ev[3], st), "cudaEventRecord");
+    if (h->tmap_base != h->d_SL.p || h->tmap_k != h->k_alloc || h->tmap_rows != rows ||
+        h->tmap_s != s) {
+      std::string e;
+      if (!make_slice_tmap(&h->tmap, h->d_SL.p, h->k_alloc, rows, s, &e))
+        return fail(h, FLAPW_ERR_CUDA, e);
+      h->tmap_base = h->d_SL.p;
+      h->tmap_k = h->k_alloc;
+      h->tmap_rows = rows;
+      h->tmap_s = s;
+    }
+    const int grid = std::min(h->n_emu_tiles, h->num_sms);
+    CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>(), h->n_emu_tiles,
+                          h->d_rexp.as<int>(), s, h->d_cnt.as<int>() + 2, grid, st),
+       "emulated contraction launch");
+  } else {
+    CK(h, cudaEventRecord(h->ev[3], st), "cudaEventRecord");
+    CK(h, launch_herk_f64(h->d_Z.as<double2>(), h->k_alloc, h->d_probs.as<Prob>(),
+                          h->d_f64_tiles.as<F64Tile>(), h->n_f64_tiles, st),
+       "FP64 contraction launch");
+  }
+  CK(h, cudaEventRecord(h->ev[4], st), "cudaEventRecord");
+  return FLAPW_OK;
+}
+
+int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int64_t key) {
+  const int order = 0;
+  if (h->tiles_rows_key == key && h->tiles_order == order) return FLAPW_OK;
+  std::vector<EmuTile> emu;
+  std::vector<F64Tile> f64;
+  make_tiles(probs, order, &emu, &f64);
+  h->n_emu_tiles = (int)emu.size();
+  h->n_f64_tiles = (int)f64.size();
+  if (upload(h, h->d_emu_tiles, emu)) return FLAPW_ERR_CUDA;
+  if (upload(h, h->d_f64_tiles, f64)) return FLAPW_ERR_CUDA;
+  h->tiles_rows_key = key;
+  h->tiles_order = order;
+  return FLAPW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void flapw_default_options(flapw_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = FLAPW_PREC_EMU;
+  opt->n_slices = 7;
+  opt->layout = FLAPW_LAYOUT_LOWER_FULL;
+  opt->operands = FLAPW_OPERANDS_FROM_AB;
+  opt->use_graph = 0;
+  opt->autotune = 0;
+}
+
+int flapw_enumerate_g(const double lattice[9], const double k_frac[3], double kmax, int max_g,
+                      int* n3, int* n_g) {
+  if (!lattice || !k_frac || !n_g) return fail(nullptr, FLAPW_ERR_ARG, "NULL argument");
+  std::vector<int> v;
+  const int n = enumerate_g(lattice, k_frac, kmax, &v);
+  if (n < 0) return fail(nullptr, FLAPW_ERR_ARG, "singular lattice or kmax <= 0");
+  *n_g = n;
+  if (n3) std::memcpy(n3, v.data(), sizeof(int) * 3 * (size_t)std::min(n, std::max(max_g, 0)));
+  return FLAPW_OK;
+}
+
+int flapw_engine_create(const flapw_options* opt, flapw_handle* out) {
+  if (!out) return fail(nullptr, FLAPW_ERR_ARG, "NULL out");
+  std::unique_ptr<flapw_ctx> h(new flapw_ctx);
+  flapw_default_options(&h->opt);
+  if (opt) h->opt = *opt;
+  if (check_options(nullptr, h->opt)) return FLAPW_ERR_ARG;
+  h->engine_only = true;
+  if (int rc = device_setup(h.get())) {
+    g_last_error = h->err;
+    return rc;
+  }
+  *out = h.release();
+  return FLAPW_OK;
+}
+
+int flapw_hs_create(const double lattice[9], int n_atoms, const double* pos_frac,
+                    const int* atom_type, int n_types, const double* mt_radius, int lmax,
+                    int n_k, const double* k_frac, const double* kmax,
+                    const flapw_options* opt, flapw_handle* out) {
+  if (!out || !lattice || !pos_frac || !atom_type || !mt_radius || !k_frac || !kmax)
+    return fail(nullptr, FLAPW_ERR_ARG, "NULL argument");
+  if (n_atoms < 1 || n_types < 1 || n_k < 1) return fail(nullptr, FLAPW_ERR_ARG, "n_atoms, n_types and n_k must be >= 1");
+  if (lmax < 0 || lmax > kMaxLmax) return fail(nullptr, FLAPW_ERR_UNSUPPORTED, "lmax must be in 0..12");
+  for (int a = 0; a < n_atoms; ++a)
+    if (atom_type[a] < 0 || atom_type[a] >= n_types) return fail(nullptr, FLAPW_ERR_ARG, "atom_type out of range");
+  for (int t = 0; t < n_types; ++t)
+    if (!(mt_radius[t] > 0)) return fail(nullptr, FLAPW_ERR_ARG, "mt_radius must be > 0");
+  std::unique_ptr<flapw_ctx> h(new flapw_ctx);
+  flapw_default_options(&h->opt);
+  if (opt) h->opt = *opt;
+  if (check_options(nullptr, h->opt)) return FLAPW_ERR_ARG;
+  std::memcpy(h->lat, lattice, sizeof(h->lat));
+  double det;
+  reciprocal(h->lat, h->rec, &det);
+  if (!(std::fabs(det) > 0)) return fail(nullptr, FLAPW_ERR_ARG, "singular lattice");
+  h->volume = std::fabs(det);
+  h->n_atoms = n_atoms;
+  h->n_types = n_types;
+  h->lmax = lmax;
+  h->n_L = (lmax + 1) * (lmax + 1);
+  h->n_k = n_k;
+  h->pos.assign(pos_frac, pos_frac + 3 * n_atoms);
+  h->type.assign(atom_type, atom_type + n_atoms);
+  h->radius.assign(mt_radius, mt_radius + n_types);
+  h->kfrac.assign(k_frac, k_frac + 3 * n_k);
+  h->kmax.assign(kmax, kmax + n_k);
+  h->n3.resize(n_k);
+  h->goff.assign(n_k + 1, 0);
+  for (int k = 0; k < n_k; ++k) {
+    const int ng = enumerate_g(h->lat, &h->kfrac[3 * k], h->kmax[k], &h->n3[k]);
+    if (ng < 0) return fail(nullptr, FLAPW_ERR_ARG, "kmax must be > 0");
+    if (ng == 0) return fail(nullptr, FLAPW_ERR_ARG, "a k-point has no plane wave below kmax");
+    h->goff[k + 1] = h->goff[k] + ng;
+  }
+  h->g_total = h->goff[n_k];
+  if (h->g_total > (int64_t)1 << 30) return fail(nullptr, FLAPW_ERR_UNSUPPORTED, "too many plane waves");
+  h->ktau.resize((size_t)n_k * n_atoms);
+  for (int k = 0; k < n_k; ++k)
+    for (int a = 0; a < n_atoms; ++a)
+      h->ktau[(size_t)k * n_atoms + a] = h->kfrac[3 * k] * h->pos[3 * a] +
+                                         h->kfrac[3 * k + 1] * h->pos[3 * a + 1] +
+                                         h->kfrac[3 * k + 2] * h->pos[3 * a + 2];
+  for (int k = 0; k < n_k; ++k) {
+    const int ng = (int)(h->goff[k + 1] - h->goff[k]);
+    for (int g0 = 0; g0 < ng; g0 += 128) {
+      h->gt128.push_back(k);
+      h->gt128.push_back(g0);
+    }
+    for (int g0 = 0; g0 < ng; g0 += 64) {
+      h->gt64.push_back(k);
+      h->gt64.push_back(g0);
+    }
+  }
+  if (int rc = device_setup(h.get())) {
+    g_last_error = h->err;
+    return rc;
+  }
+  // geometry to the device
+  std::vector<double> rec(h->rec, h->rec + 9);
+  std::vector<int> n3all, gk;
+  n3all.reserve(3 * h->g_total);
+  gk.reserve(h->g_total);
+  for (int k = 0; k < n_k; ++k) {
+    n3all.insert(n3all.end(), h->n3[k].begin(), h->n3[k].end());
+    gk.insert(gk.end(), h->n3[k].size() / 3, k);
+  }
+  // normalised-Legendre recurrence coefficients, index 2*(l(l+1)/2 + m)
+  std::vector<double> coef((size_t)(lmax + 2) * (lmax + 3), 0.0);
+  for (int l = 0; l <= lmax; ++l)
+    for (int m = 0; m <= l; ++m) {
+      const size_t i = 2 * ((size_t)l * (l + 1) / 2 + m);
+      if (l == m) {
+        coef[i] = (m > 0) ? std::sqrt((2.0 * m + 1.0) / (2.0 * m)) : 0.0;
+      } else if (l == m + 1) {
+        coef[i] = std::sqrt(2.0 * m + 3.0);
+      } else {
+        coef[i] = std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+        coef[i + 1] = std::sqrt(((l - 1.0) * (l - 1.0) - (double)m * m) /
+                                (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
+      }
+    }
+  flapw_ctx* hp = h.get();
+  if (upload(hp, h->d_rec, rec) || upload(hp, h->d_pos, h->pos) || upload(hp, h->d_type, h->type) ||
+      upload(hp, h->d_radius, h->radius) || upload(hp, h->d_kfrac, h->kfrac) ||
+      upload(hp, h->d_ktau, h->ktau) || upload(hp, h->d_n3, n3all) || upload(hp, h->d_gk, gk) ||
+      upload(hp, h->d_goff, h->goff) || upload(hp, h->d_coef, coef) ||
+      upload(hp, h->d_gt128, h->gt128) || upload(hp, h->d_gt64, h->gt64)) {
+    g_last_error = h->err;
+    return FLAPW_ERR_CUDA;
+  }
+  *out = h.release();
+  return FLAPW_OK;
+}
+
+int flapw_set_options(flapw_handle h, const flapw_options* opt) {
+  if (!h || !opt) return fail(h, FLAPW_ERR_ARG, "NULL argument");
+  if (int rc = check_options(h, *opt)) return rc;
+  h->opt = *opt;
+  return FLAPW_OK;
+}
+
+int flapw_num_g(flapw_handle h, int k, int* n_g) {
+  if (!h || !n_g) return fail(h, FLAPW_ERR_ARG, "NULL argument");
+  if (h->engine_only) return fail(h, FLAPW_ERR_STATE, "handle has no crystal");
+  if (k < 0 || k >= h->n_k) return fail(h, FLAPW_ERR_ARG, "k out of range");
+  *n_g = (int)(h->goff[k + 1] - h->goff[k]);
+  return FLAPW_OK;
+}
+
+int flapw_get_gvectors(flapw_handle h, int k, int* n3) {
+  if (!h || !n3) return fail(h, FLAPW_ERR_ARG, "NULL argument");
+  if (h->engine_only) return fail(h, FLAPW_ERR_STATE, "handle has no crystal");
+  if (k < 0 || k >= h->n_k) return fail(h, FLAPW_ERR_ARG, "k out of range");
+  std::memcpy(n3, h->n3[k].data(), sizeof(int) * h->n3[k].size());
+  return FLAPW_OK;
+}
+
+int flapw_ab_offset(flapw_handle h, int k, int64_t* offset) {
+  if (!h || !offset) return fail(h, FLAPW_ERR_ARG, "NULL argument");
+  if (h->engine_only) return fail(h, FLAPW_ERR_STATE, "handle has no crystal");
+  if (k < 0 || k > h->n_k) return fail(h, FLAPW_ERR_ARG, "k out of range");
+  *offset = (int64_t)h->n_atoms * h->n_L * h->goff[k];
+  return FLAPW_OK;
+}
+
+static int prepare_prep(flapw_ctx* h, cudaStream_t st) {
+  const int64_t G = h->g_total;
+  CK(h, h->d_Yc.ensure((size_t)h->n_L * G * 16), "workspace");
+  CK(h, h->d_al.ensure((size_t)h->n_types * (h->lmax + 1) * G * 8), "workspace");
+  CK(h, h->d_bl.ensure((size_t)h->n_types * (h->lmax + 1) * G * 8), "workspace");
+  CK(h, h->d_ph.ensure((size_t)h->n_atoms * G * 16), "workspace");
+  Geom geo{h->n_atoms, h->n_types, h->lmax, h->n_L, h->n_k, G,
+           h->d_rec.as<double>(), h->d_pos.as<double>(), h->d_type.as<int>(),
+           h->d_radius.as<double>(), h->d_kfrac.as<double>(), h->d_ktau.as<double>(),
+           4.0 * M_PI / std::sqrt(h->volume)};
+  GData gd{h->d_n3.as<int>(), h->d_gk.as<int>(), h->d_goff.as<int64_t>()};
+  CK(h, launch_ab_prep(geo, gd, h->d_radial.as<double>(), h->d_coef.as<double>(),
+                       h->d_Yc.as<double2>(), h->d_al.as<double>(), h->d_bl.as<double>(),
+                       h->d_ph.as<double2>(), st),
+     "A/B preparation launch");
+  h->prep_valid = true;
+  return FLAPW_OK;
+}
+
+int flapw_build_AB(flapw_handle h, const double* radial, void* A, void* B, void* stream) {
+  if (!h || !radial || !A || !B) return fail(h, FLAPW_ERR_ARG, "NULL argument");
+  if (h->engine_only) return fail(h, FLAPW_ERR_STATE, "handle has no crystal");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t nrad = (size_t)h->n_types * (h->lmax + 1) * 4;
+  for (size_t i = 0; i < nrad; i += 4) {
+    const double D = radial[i] * radial[i + 3] - radial[i + 1] * radial[i + 2];
+    if (!(D != 0.0) || !std::isfinite(D))
+      return fail(h, FLAPW_ERR_ARG, "radial data: u udot' - u' udot must be finite and nonzero");
+  }
+  h->radial.assign(radial, radial + nrad);
+  h->have_radial = true;
+  CK(h, h->d_radial.ensure(nrad * 8), "workspace");
+  CK(h, cudaMemcpyAsync(h->d_radial.p, h->radial.data(), nrad * 8, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+  CK(h, cudaEventRecord(h->ev[6], st), "cudaEventRecord");
+  if (int rc = prepare_prep(h, st)) return rc;
+  const size_t total = (size_t)h->n_atoms * h->n_L * h->g_total;
+  const bool devA = is_device_ptr(A), devB = is_device_ptr(B);
+  double2* dA = static_cast<double2*>(A);
+  double2* dB = static_cast<double2*>(B);
+  if (!devA) {
+    CK(h, h->d_stageA.ensure(total * 16), "staging");
+    dA = h->d_stageA.as<double2>();
+  }
+  if (!devB) {
+    CK(h, h->d_stageB.ensure(total * 16), "staging");
+    dB = h->d_stageB.as<double2>();
+  }
+  Geom geo{h->n_atoms, h->n_types, h->lmax, h->n_L, h->n_k, h->g_total,
+           h->d_rec.as<double>(), h->d_pos.as<double>(), h->d_type.as<int>(),
+           h->d_radius.as<double>(), h->d_kfrac.as<double>(), h->d_ktau.as<double>(),
+           4.0 * M_PI / std::sqrt(h->volume)};
+  CK(h, launch_ab_assemble_tiles(geo, h->d_gt128.as<int>(), (int)(h->gt128.size() / 2),
+                                 h->d_goff.as<int64_t>(), h->d_Yc.as<double2>(), h->d_al.as<double>(),
+                                 h->d_bl.as<double>(), h->d_ph.as<double2>(), dA, dB, st),
+     "A/B assembly launch");
+  CK(h, cudaEventRecord(h->ev[7], st), "cudaEventRecord");
+  h->ev_ab = true;
+  if (!devA) CK(h, cudaMemcpyAsync(A, dA, total * 16, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+  if (!devB) CK(h, cudaMemcpyAsync(B, dB, total * 16, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+  h->last_stream = st;
+  return FLAPW_OK;
+}
+
+int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom_slot,
+                   const double* U, const void* A, const void* B, void* const* H,
+                   void* const* S, void* stream) {
+  if (!h || !T || !atom_slot || !U || !H || !S) return fail(h, FLAPW_ERR_ARG, "NULL argument");
+  if (h->engine_only) return fail(h, FLAPW_ERR_STATE, "handle has no crystal");
+  const bool factored = h->opt.operands == FLAPW_OPERANDS_FACTORED;
+  if (!factored && (!A || !B)) return fail(h, FLAPW_ERR_ARG, "A and B are required with FLAPW_OPERANDS_FROM_AB");
+  if (factored && !h->have_radial)
+    return fail(h, FLAPW_ERR_STATE, "FLAPW_OPERANDS_FACTORED needs a previous flapw_build_AB");
+  if (n_slots < 1) return fail(h, FLAPW_ERR_ARG, "n_slots must be >= 1");
+  for (int a = 0; a < h->n_atoms; ++a)
+    if (atom_slot[a] < 0 || atom_slot[a] >= n_slots) return fail(h, FLAPW_ERR_ARG, "atom_slot out of range");
+  for (int k = 0; k < h->n_k; ++k)
+    if (!H[k] || !S[k]) return fail(h, FLAPW_ERR_ARG, "NULL H[k] or S[k]");
+  cudaStream_t user_st = static_cast<cudaStream_t>(stream);
+  const int n = 2 * h->n_L;
+  const int nlp = h->lmax + 1;
+  const int64_t K = (int64_t)h->n_atoms * n;
+  if (K >= ((int64_t)1 << 17)) return fail(h, FLAPW_ERR_UNSUPPORTED, "2 N_A N_L must be below 131072");
+  const int layout = h->opt.layout;
+
+  // ---- host-side preparation (not captured) ----
+  const size_t t_bytes = (size_t)n_slots * n * n * 16;
+  const size_t slot_bytes = (size_t)h->n_atoms * 4;
+  const size_t u_bytes = (size_t)h->n_types * nlp * 8;
+  // factored mode: (slot, type) combos and their atom lists
+  std::vector<int> combo_slot, combo_type, combo_atoms, combo_start{0};
+  if (factored) {
+    std::map<std::pair<int, int>, std::vector<int>> cmb;
+    for (int a = 0; a < h->n_atoms; ++a) cmb[{atom_slot[a], h->type[a]}].push_back(a);
+    for (auto& kv : cmb) {
+      combo_slot.push_back(kv.first.first);
+      combo_type.push_back(kv.first.second);
+      combo_atoms.insert(combo_atoms.end(), kv.second.begin(), kv.second.end());
+      combo_start.push_back((int)combo_atoms.size());
+    }
+  }
+  const int n_combo = (int)combo_slot.size();
+  const size_t cmb_ints = combo_slot.size() * 2 + combo_atoms.size() + combo_start.size();
+  const size_t in_bytes = t_bytes + slot_bytes + u_bytes + cmb_ints * 4 + 256;
+  CK(h, h->pin_in.ensure(in_bytes), "cudaMallocHost");
+
+  // outputs
+  OutPlan op;
+  op.dev.resize(2 * h->n_k);
+  op.host.assign(2 * h->n_k, nullptr);
+  op.bytes.resize(2 * h->n_k);
+  op.stage_off.resize(2 * h->n_k);
+  for (int k = 0; k < h->n_k; ++k) {
+    const int64_t ng = h->goff[k + 1] - h->goff[k];
+    for (int w = 0; w < 2; ++w) {
+      void* p = w ? S[k] : H[k];
+      const int idx = 2 * k + w;
+      op.bytes[idx] = out_bytes(layout, ng);
+      if (is_device_ptr(p)) {
+        op.dev[idx] = static_cast<double2*>(p);
+      } else {
+        op.host[idx] = p;
+        op.stage_off[idx] = op.stage_bytes;
+        op.stage_bytes += round_up((int64_t)op.bytes[idx], 256);
+      }
+    }
+  }
+  if (op.stage_bytes) {
+    CK(h, h->d_stageOut.ensure(op.stage_bytes), "staging");
+    for (int i = 0; i < 2 * h->n_k; ++i)
+      if (op.host[i]) op.dev[i] = reinterpret_cast<double2*>(h->d_stageOut.as<char>() + op.stage_off[i]);
+  }
+  // A/B may be host memory: stage it
+  const size_t ab_total = (size_t)h->n_atoms * h->n_L * h->g_total;
+  const double2* dA = static_cast<const double2*>(A);
+  const double2* dB = static_cast<const double2*>(B);
+  bool stage_ab = false;
+  if (!factored && (!is_device_ptr(A) || !is_device_ptr(B))) {
+    CK(h, h->d_stageA.ensure(ab_total * 16), "staging");
+    CK(h, h->d_stageB.ensure(ab_total * 16), "staging");
+    stage_ab = true;
+  }
+
+  // problems
+  std::vector<Prob> probs(2 * h->n_k);
+  for (int k = 0; k < h->n_k; ++k) {
+    const int ng = (int)(h->goff[k + 1] - h->goff[k]);
+    Prob ph{(int)(2 * h->goff[k]), ng, 0, 0, layout, 0, ng, op.dev[2 * k]};
+    Prob ps{(int)(2 * h->goff[k] + ng), ng, (int)K, 0, layout, 0, ng, op.dev[2 * k + 1]};
+    probs[2 * k] = ph;
+    probs[2 * k + 1] = ps;
+  }
+  h->rows = 2 * h->g_total;
+  h->k_alloc = round_up(K, kChunk) + kChunk;
+  // workspaces
+  CK(h, h->d_T.ensure(t_bytes), "workspace");
+  CK(h, h->d_work.ensure(t_bytes), "workspace");
+  CK(h, h->d_CH.ensure(t_bytes), "workspace");
+  CK(h, h->d_cnt.ensure(sizeof(int) * (8 + 2 * (size_t)n_slots)), "workspace");
+  CK(h, h->d_slot.ensure(slot_bytes + cmb_ints * 4 + 64), "workspace");
+  CK(h, h->d_U.ensure(u_bytes), "workspace");
+  CK(h, h->d_off.ensure(sizeof(int) * (2 * (size_t)h->n_atoms + 8)), "workspace");
+  CK(h, h->d_probs.ensure(sizeof(Prob) * probs.size()), "workspace");
+  CK(h, h->d_Z.ensure((size_t)h->rows * h->k_alloc * 16), "operand workspace");
+  CK(h, h->d_rexp.ensure((size_t)h->rows * 4), "workspace");
+  if (h->d_rowprob.bytes < (size_t)h->rows * 4 || h->tiles_rows_key != h->rows) {
+    std::vector<int> rp(h->rows);
+    for (int p = 0; p < (int)probs.size(); ++p)
+      for (int g = 0; g < probs[p].n_g; ++g) rp[probs[p].row_base + g] = p;
+    if (upload(h, h->d_rowprob, rp)) return FLAPW_ERR_CUDA;
+  }
+  if (int rc = ensure_tiles(h, probs, h->rows)) return rc;
+  CK(h, h->pin_probs.ensure(sizeof(Prob) * probs.size()), "cudaMallocHost");
+
+  // pinned inputs (previous replays read them; wait for the stream first)
+  if (h->last_stream) CK(h, cudaStreamSynchronize(h->last_stream), "cudaStreamSynchronize");
+  char* pin = static_cast<char*>(h->pin_in.p);
+  std::memcpy(pin, T, t_bytes);
+  std::memcpy(pin + t_bytes, atom_slot, slot_bytes);
+  std::memcpy(pin + t_bytes + slot_bytes, U, u_bytes);
+  int* pc = reinterpret_cast<int*>(pin + t_bytes + slot_bytes + u_bytes);
+  std::memcpy(pc, combo_slot.data(), combo_slot.size() * 4);
+  std::memcpy(pc + n_combo, combo_type.data(), combo_type.size() * 4);
+  std::memcpy(pc + 2 * n_combo, combo_atoms.data(), combo_atoms.size() * 4);
+  std::memcpy(pc + 2 * n_combo + combo_atoms.size(), combo_start.data(), combo_start.size() * 4);
+  std::memcpy(h->pin_probs.p, probs.data(), sizeof(Prob) * probs.size());
+  h->last_n_slots = n_slots;
+
+  // ---- the enqueued sequence (graph-capturable) ----
+  auto enqueue = [&](cudaStream_t st) -> int {
+    CK(h, cudaEventRecord(h->ev[0], st), "cudaEventRecord");
+    CK(h, cudaMemcpyAsync(h->d_T.p, pin, t_bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    CK(h, cudaMemcpyAsync(h->d_slot.p, pin + t_bytes, slot_bytes + 0, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    CK(h, cudaMemcpyAsync(h->d_slot.as<char>() + slot_bytes, pc, cmb_ints * 4, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    CK(h, cudaMemcpyAsync(h->d_U.p, pin + t_bytes + slot_bytes, u_bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    CK(h, cudaMemcpyAsync(h->d_probs.p, h->pin_probs.p, sizeof(Prob) * probs.size(), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    if (stage_ab) {
+      CK(h, cudaMemcpyAsync(h->d_stageA.p, A, ab_total * 16, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+      CK(h, cudaMemcpyAsync(h->d_stageB.p, B, ab_total * 16, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+      dA = h->d_stageA.as<double2>();
+      dB = h->d_stageB.as<double2>();
+    }
+    int* cnt = h->d_cnt.as<int>();  // [0]=npiv2 [1]=unused [2]=err [8..]=npos, nneg
+    CK(h, cudaMemsetAsync(cnt, 0, sizeof(int) * 8, st), "cudaMemsetAsync");
+    int* npos = cnt + 8;
+    int* nneg = cnt + 8 + n_slots;
+    CK(h, launch_tfactor(h->d_T.as<double2>(), n, n_slots, h->d_work.as<double2>(), h->d_CH.as<double2>(),
+                         npos, nneg, cnt, cnt + 2, st),
+       "T factorisation launch");
+    int* pos_off = h->d_off.as<int>();
+    int* neg_off = pos_off + h->n_atoms;
+    int* kpk = neg_off + h->n_atoms;
+    CK(h, launch_layout(npos, nneg, h->d_slot.as<int>(), h->n_atoms, h->n_k, pos_off, neg_off, kpk,
+                        h->d_probs.as<Prob>(), (int)K, st),
+       "layout launch");
+    CK(h, cudaEventRecord(h->ev[1], st), "cudaEventRecord");
+    OpformArgs oa{};
+    oa.n_atoms = h->n_atoms;
+    oa.n_L = h->n_L;
+    oa.n = n;
+    oa.n_k = h->n_k;
+    oa.atom_slot = h->d_slot.as<int>();
+    oa.atom_type = h->d_type.as<int>();
+    oa.CH = h->d_CH.as<double2>();
+    oa.npos = npos;
+    oa.nneg = nneg;
+    oa.pos_off = pos_off;
+    oa.neg_off = neg_off;
+    oa.kpk = kpk;
+    oa.U = h->d_U.as<double>();
+    oa.lmax = h->lmax;
+    oa.k_alloc = h->k_alloc;
+    oa.Z = h->d_Z.as<double2>();
+    oa.gtiles = h->d_gt64.as<int>();
+    oa.n_gtiles = (int)(h->gt64.size() / 2);
+    oa.goff = h->d_goff.as<int64_t>();
+    oa.g_total = h->g_total;
+    oa.A = dA;
+    oa.B = dB;
+    oa.Yc = h->d_Yc.as<double2>();
+    oa.al = h->d_al.as<double>();
+    oa.bl = h->d_bl.as<double>();
+    oa.ph = h->d_ph.as<double2>();
+    oa.n_types = h->n_types;
+    const int* dc = reinterpret_cast<const int*>(h->d_slot.as<char>() + slot_bytes);
+    oa.combo_slot = dc;
+    oa.combo_type = dc + n_combo;
+    oa.combo_atoms = dc + 2 * n_combo;
+    oa.combo_start = dc + 2 * n_combo + combo_atoms.size();
+    oa.n_combo = n_combo;
+    CK(h, launch_opform_H(oa, factored, st), "H operand launch");
+    CK(h, launch_opform_S(oa, factored, st), "S operand launch");
+    CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
+    if (int rc = enqueue_contraction(h, probs, st)) return rc;
+    for (int i = 0; i < 2 * h->n_k; ++i)
+      if (op.host[i]) CK(h, cudaMemcpyAsync(op.host[i], op.dev[i], op.bytes[i], cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    CK(h, cudaEventRecord(h->ev[5], st), "cudaEventRecord");
+    return FLAPW_OK;
+  };
+
+  if (factored && !h->prep_valid) {
+    if (int rc = prepare_prep(h, user_st)) return rc;
+  }
+  h->ev_recorded = true;
+  h->last_stream = user_st;
+  if (!h->opt.use_graph) return enqueue(user_st);
+
+  // graph replay keyed on everything the captured sequence bakes in
+  std::vector<uintptr_t> key{(uintptr_t)A, (uintptr_t)B, (uintptr_t)n_slots, (uintptr_t)h->opt.precision,
+                             (uintptr_t)layout, (uintptr_t)h->opt.operands, (uintptr_t)slices_of(h),
+                             (uintptr_t)h->d_Z.p, (uintptr_t)h->d_SL.p, (uintptr_t)h->pin_in.p};
+  for (int k = 0; k < h->n_k; ++k) {
+    key.push_back((uintptr_t)H[k]);
+    key.push_back((uintptr_t)S[k]);
+  }
+  if (!h->gexec || key != h->gkey) {
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+    // make sure every workspace exists before capture (no allocation inside)
+    if (h->opt.precision == FLAPW_PREC_EMU)
+      CK(h, h->d_SL.ensure((size_t)slices_of(h) * 2 * h->rows * h->k_alloc * 2), "slice workspace");
+    key[8] = (uintptr_t)h->d_SL.p;
+    CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    const int rc = enqueue(h->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    CK(h, e2, "cudaStreamEndCapture");
+    const cudaError_t e3 = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    CK(h, e3, "cudaGraphInstantiate");
+    h->gkey = key;
+  } else {
+    ++h->stats.graph_replays;
+  }
+  CK(h, cudaGraphLaunch(h->gexec, user_st), "cudaGraphLaunch");
+  return FLAPW_OK;
+}
+
+int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const int* sigma,
+               void* H, int64_t ldh, void* stream) {
+  if (!h || !Z || !H) return fail(h, FLAPW_ERR_ARG, "NULL argument");
+  if (K < 1 || N < 1 || ldz < K) return fail(h, FLAPW_ERR_ARG, "need K >= 1, N >= 1, ldz >= K");
+  if (K >= (1 << 17)) return fail(h, FLAPW_ERR_UNSUPPORTED, "K must be below 131072");
+  if (h->opt.layout == FLAPW_LAYOUT_LOWER_FULL && ldh < N) return fail(h, FLAPW_ERR_ARG, "ldh < N");
+  if (!is_device_ptr(Z)) return fail(h, FLAPW_ERR_ARG, "Z must be device memory");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<int> pos, neg;
+  for (int k = 0; k < K; ++k) {
+    const int s = sigma ? sigma[k] : 1;
+    if (s != 1 && s != -1) return fail(h, FLAPW_ERR_ARG, "sigma entries must be +1 or -1");
+    (s > 0 ? pos : neg).push_back(k);
+  }
+  const int64_t kp_pad = round_up((int64_t)pos.size(), kChunk);
+  const int64_t k_alloc = std::max<int64_t>(kp_pad + round_up((int64_t)neg.size(), kChunk), kChunk);
+  std::vector<int> kmap(k_alloc, -1);
+  for (size_t i = 0; i < pos.size(); ++i) kmap[i] = pos[i];
+  for (size_t i = 0; i < neg.size(); ++i) kmap[kp_pad + i] = neg[i];
+  const bool devH = is_device_ptr(H);
+  const size_t ob = out_bytes(h->opt.layout, N);
+  double2* dH = static_cast<double2*>(H);
+  if (!devH) {
+    CK(h, h->d_stageOut.ensure(ob), "staging");
+    dH = h->d_stageOut.as<double2>();
+  }
+  std::vector<Prob> probs{Prob{0, N, (int)pos.size(), (int)neg.size(), h->opt.layout, 0,
+                               h->opt.layout == FLAPW_LAYOUT_LOWER_FULL ? ldh : N, dH}};
+  h->rows = N;
+  h->k_alloc = k_alloc;
+  if (upload(h, h->d_kmap, kmap) || upload(h, h->d_probs, probs)) return FLAPW_ERR_CUDA;
+  std::vector<int> rp(N, 0);
+  if (upload(h, h->d_rowprob, rp)) return FLAPW_ERR_CUDA;
+  h->tiles_rows_key = -1;  // force a rebuild
+  if (int rc = ensure_tiles(h, probs, -2 - (int64_t)N)) return rc;
+  h->tiles_rows_key = -1;  // the next build_HS rebuilds its own
+  CK(h, h->d_Z.ensure((size_t)N * k_alloc * 16), "operand workspace");
+  CK(h, h->d_rexp.ensure((size_t)N * 4), "workspace");
+  CK(h, h->d_cnt.ensure(sizeof(int) * 16), "workspace");
+  CK(h, cudaMemsetAsync(h->d_cnt.p, 0, sizeof(int) * 8, st), "cudaMemsetAsync");
+  CK(h, cudaEventRecord(h->ev[0], st), "cudaEventRecord");
+  CK(h, cudaEventRecord(h->ev[1], st), "cudaEventRecord");
+  CK(h, launch_gather_Z(static_cast<const double2*>(Z), ldz, K, N, h->d_kmap.as<int>(), k_alloc,
+                        h->d_Z.as<double2>(), st),
+     "gather launch");
+  CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
+  if (int rc = enqueue_contraction(h, probs, st)) return rc;
+  if (!devH) CK(h, cudaMemcpyAsync(H, dH, ob, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+  CK(h, cudaEventRecord(h->ev[5], st), "cudaEventRecord");
+  h->ev_recorded = true;
+  h->last_stream = st;
+  h->gkey.clear();
+  return FLAPW_OK;
+}
+
+int flapw_sync(flapw_handle h) {
+  if (!h) return fail(h, FLAPW_ERR_ARG, "NULL handle");
+  CK(h, cudaStreamSynchronize(h->last_stream), "cudaStreamSynchronize");
+  CK(h, cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  if (h->d_cnt.p) {
+    int c[8];
+    CK(h, cudaMemcpy(c, h->d_cnt.p, sizeof(c), cudaMemcpyDeviceToHost), "cudaMemcpy");
+    if (c[2] == FLAPW_ERR_TIMEOUT)
+      return fail(h, FLAPW_ERR_TIMEOUT, "a bounded device wait expired in the contraction");
+    if (c[2] == FLAPW_ERR_FACTOR)
+      return fail(h, FLAPW_ERR_FACTOR, "a T block has a singular 2x2 pivot");
+    if (c[2] != 0) return fail(h, FLAPW_ERR_CUDA, "device error flag " + std::to_string(c[2]));
+  }
+  return FLAPW_OK;
+}
+
+int flapw_get_stats(flapw_handle h, flapw_stats* st) {
+  if (!h || !st) return fail(h, FLAPW_ERR_ARG, "NULL argument");
+  auto el = [&](int a, int b) -> double {
+    float ms = 0.f;
+    if (cudaEventQuery(h->ev[b]) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return -1.0;
+    }
+    if (cudaEventElapsedTime(&ms, h->ev[a], h->ev[b]) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return -1.0;
+    }
+    return ms;
+  };
+  flapw_stats s = h->stats;
+  if (h->ev_ab) s.ms_ab = el(6, 7);
+  if (h->ev_recorded) {
+    s.ms_factor = el(0, 1);
+    s.ms_operands = el(1, 2);
+    s.ms_slice = (h->opt.precision == FLAPW_PREC_EMU) ? el(2, 3) : 0.0;
+    s.ms_contract = el(3, 4);
+    s.ms_hs_total = el(0, 5);
+  }
+  s.n_slices = slices_of(h);
+  s.n_tiles = (h->opt.precision == FLAPW_PREC_EMU) ? h->n_emu_tiles : h->n_f64_tiles;
+  s.tile_order = h->tiles_order;
+  if (!h->engine_only) {
+    s.k_total = (int64_t)h->n_atoms * 2 * h->n_L;
+    double ng2 = 0;
+    for (int k = 0; k < h->n_k; ++k) {
+      const double ng = (double)(h->goff[k + 1] - h->goff[k]);
+      ng2 += ng * ng;
+    }
+    s.flops_herk = 16.0 * h->n_atoms * h->n_L * ng2;
+  }
+  if (h->d_cnt.p && h->d_off.p && h->ev_recorded && !h->engine_only && cudaEventQuery(h->ev[5]) == cudaSuccess) {
+    int c[8];
+    int kpk[3] = {0, 0, 0};
+    if (cudaMemcpy(c, h->d_cnt.p, sizeof(c), cudaMemcpyDeviceToHost) == cudaSuccess &&
+        cudaMemcpy(kpk, h->d_off.as<int>() + 2 * h->n_atoms, sizeof(kpk), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      s.n_pivot2 = c[0];
+      s.n_pos = kpk[1];
+      s.n_neg = kpk[2];
+      // tensor flops: per tile, pairs x chunks x 2 MMAs x 4 x (2*128*128*16)
+      const int S_ = slices_of(h);
+      const double pairs = S_ * (S_ + 1) / 2.0;
+      const double chH = std::ceil(kpk[1] / 64.0) + std::ceil(kpk[2] / 64.0);
+      const double chS = std::ceil((double)s.k_total / 64.0);
+      double tf = 0;
+      for (int k = 0; k < h->n_k; ++k) {
+        const int ng = (int)(h->goff[k + 1] - h->goff[k]);
+        const int nib = (ng + 127) / 128, njb = (ng + 63) / 64;
+        double nt = 0;
+        for (int ib = 0; ib < nib; ++ib) nt += std::min(njb, 2 * ib + 2);
+        tf += nt * pairs * (chH + chS) * 2.0 * 4.0 * (2.0 * 128 * 128 * 16);
+      }
+      s.flops_tensor = tf;
+    } else {
+      (void)cudaGetLastError();
+    }
+  }
+  *st = s;
+  return FLAPW_OK;
+}
+
+int flapw_get_factor(flapw_handle h, int slot, double* CH, int* n_pos, int* n_neg) {
+  if (!h || !CH || !n_pos || !n_neg) return fail(h, FLAPW_ERR_ARG, "NULL argument");
+  if (slot < 0 || slot >= h->last_n_slots) return fail(h, FLAPW_ERR_ARG, "slot out of range");
+  const int n = 2 * h->n_L;
+  CK(h, cudaStreamSynchronize(h->last_stream), "cudaStreamSynchronize");
+  CK(h, cudaMemcpy(CH, h->d_CH.as<double2>() + (size_t)slot * n * n, (size_t)n * n * 16, cudaMemcpyDeviceToHost), "cudaMemcpy");
+  int* cnt = h->d_cnt.as<int>();
+  CK(h, cudaMemcpy(n_pos, cnt + 8 + slot, 4, cudaMemcpyDeviceToHost), "cudaMemcpy");
+  CK(h, cudaMemcpy(n_neg, cnt + 8 + h->last_n_slots + slot, 4, cudaMemcpyDeviceToHost), "cudaMemcpy");
+  return FLAPW_OK;
+}
+
+const char* flapw_last_error(flapw_handle h) {
+  return h ? h->err.c_str() : g_last_error.c_str();
+}
+
+int flapw_destroy(flapw_handle h) {
+  if (!h) return fail(nullptr, FLAPW_ERR_ARG, "NULL handle");
+  if (h->last_stream) cudaStreamSynchronize(h->last_stream);
+  delete h;
+  return FLAPW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "flapw.h"
+
+namespace flapw {
+
+constexpr int kMaxLmax = 12;
+constexpr int kMaxNL = (kMaxLmax + 1) * (kMaxLmax + 1);
+constexpr int kChunk = 64;        // columns of K per pipeline step (one 128-byte fp16 row)
+constexpr int kSliceBits = 7;     // magnitude bits per emulation slice
+constexpr int kFixedFrac = 45;    // fractional bits of the 64-bit fixed-point accumulators
+constexpr int kUnitChunks = 16;   // K chunks per exact FP32 accumulation (16*64 = 1024 terms)
+
+// One lower-triangle contraction problem: H or S of one k-point.
+struct Prob {
+  int row_base;   // first row of this problem in the operand / slice arrays
+  int n_g;        // N_G of the problem
+  int kp;         // operand rows (K index) with sigma = +1; columns [0, kp)
+  int kn;         // rows with sigma = -1; columns [ceil(kp/64)*64, ... + kn)
+  int layout;     // FLAPW_LAYOUT_*
+  int pad;
+  int64_t ld;     // leading dimension of the full layout
+  double2* out;   // lower triangle, complex128
+};
+
+// Output tile of the emulated contraction: 128 rows (G') x 64 columns (G).
+struct EmuTile {
+  int prob;
+  int ib;  // row block (128)
+  int jb;  // column block (64)
+  int pad;
+};
+
+// Output tile of the FP64 contraction: 64 x 64.
+struct F64Tile {
+  int prob;
+  int ib;
+  int jb;
+  int pad;
+};
+
+// Per-G data for A/B generation, indexed by the global plane-wave index.
+struct GData {
+  const int* n3;      // [G_total][3]
+  const int* gk;      // [G_total] k-point of each plane wave
+  const int64_t* goff;  // [n_k+1]
+};
+
+// Geometry on the device.
+struct Geom {
+  int n_atoms, n_types, lmax, n_L, n_k;
+  int64_t g_total;
+  const double* rec;        // [9] reciprocal rows b1,b2,b3
+  const double* pos;        // [n_atoms][3]
+  const int* type;          // [n_atoms]
+  const double* radius;     // [n_types]
+  const double* kfrac;      // [n_k][3]
+  const double* ktau;       // [n_k][n_atoms]: k . tau_frac
+  double pref;              // 4 pi / sqrt(Omega)
+};
+
+// ---- kernels (launch wrappers) -------------------------------------------
+
+// Per plane wave: Yc[L][g] = pref i^l conj(Y_lm(K_hat)), radial factors
+// al/bl[t][l][g], atom phases ph[a][g].
+cudaError_t launch_ab_prep(const Geom& geo, const GData& gd, const double* radial,
+                           const double* ylm_coef, double2* Yc, double* al, double* bl,
+                           double2* ph, cudaStream_t st);
+// A/B assembly for all k-points into [k][a][L][G] blocks.
+cudaError_t launch_ab_assemble_tiles(const Geom& geo, const int* gtiles, int n_gtiles,
+                                     const int64_t* goff, const double2* Yc, const double* al,
+                                     const double* bl, const double2* ph, double2* A, double2* B,
+                                     cudaStream_t st);
+
+// Bunch-Kaufman LDL^H of each T block and C^H = |L|^{1/2} Q^H L^H P^T.
+cudaError_t launch_tfactor(const double2* T, int n, int n_slots, double2* work, double2* CH,
+                           int* npos, int* nneg, int* npiv2, int* err, cudaStream_t st);
+
+// Atom offsets in the sigma-grouped K order and chunk counts of the H problems.
+cudaError_t launch_layout(const int* npos, const int* nneg, const int* atom_slot, int n_atoms,
+                          int n_k, int* pos_off, int* neg_off, int* kpk, Prob* probs,
+                          int k_total, cudaStream_t st);
+
+struct OpformArgs {
+  int n_atoms, n_L, n, n_k;
+  const int* atom_slot;
+  const int* atom_type;
+  const double2* CH;    // [slot][n][n]
+  const int* npos;      // [slot]
+  const int* nneg;      // [slot]
+  const int* pos_off;   // [atom]
+  const int* neg_off;   // [atom]
+  const int* kpk;       // [0]=Kp_pad (start of the negative block)
+  const double* U;      // [type][lmax+1]
+  int lmax;
+  int64_t k_alloc;      // row stride of Z (complex elements)
+  double2* Z;           // operand rows
+  const int* gtiles;    // [n_gtiles][2] = (k, g0)
+  int n_gtiles;
+  const int64_t* goff;  // [n_k+1]
+  int64_t g_total;      // plane waves over all k-points
+  // from A/B
+  const double2* A;
+  const double2* B;
+  // factored
+  const double2* Yc;
+  const double* al;
+  const double* bl;
+  const double2* ph;
+  int n_types;
+  const int* combo_slot;   // [n_combo]
+  const int* combo_type;   // [n_combo]
+  const int* combo_atoms;  // atoms grouped by combo
+  const int* combo_start;  // [n_combo+1]
+  int n_combo;
+};
+cudaError_t opform_init();
+cudaError_t launch_opform_H(const OpformArgs& a, bool factored, cudaStream_t st);
+cudaError_t launch_opform_S(const OpformArgs& a, bool factored, cudaStream_t st);
+
+// Copies a user Z (column-major K x N) into operand rows, sigma-grouped.
+cudaError_t launch_gather_Z(const double2* Zin, int64_t ldz, int K, int N, const int* kmap,
+                            int64_t k_alloc, double2* Z, cudaStream_t st);
+
+// FP64 -> integer slices (fp16 carriers) with per-row power-of-two scaling.
+cudaError_t launch_slicer(const double2* Z, int64_t k_alloc, const Prob* probs, int n_prob,
+                          const int* row_prob, int64_t rows, int n_slices, __half* SL,
+                          int* rexp, cudaStream_t st);
+
+// Contractions.
+cudaError_t launch_herk_f64(const double2* Z, int64_t k_alloc, const Prob* probs,
+                            const F64Tile* tiles, int n_tiles, cudaStream_t st);
+cudaError_t launch_herk_emu(const CUtensorMap& tmap, const Prob* probs, const EmuTile* tiles,
+                            int n_tiles, const int* rexp, int n_slices, int* err, int grid,
+                            cudaStream_t st);
+size_t herk_emu_smem_bytes();
+
+// Tensor map for the slice array [slice][plane][row][k] (fp16).
+bool make_slice_tmap(CUtensorMap* map, void* base, int64_t k_alloc, int64_t rows, int n_slices,
+                     std::string* err);
+
+// ---- host G enumeration ----------------------------------------------------
+int enumerate_g(const double lat[9], const double k[3], double kmax, std::vector<int>* n3);
+void reciprocal(const double lat[9], double rec[9], double* det);
+
+}  // namespace flapw

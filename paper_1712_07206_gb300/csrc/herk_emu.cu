@@ -1,0 +1,468 @@
+// Emulated complex-FP64 lower-triangle contraction  X = Z^H diag(sigma) Z  on
+// the FP16 tensor cores (tcgen05.mma, TMEM accumulators, TMA operand loads).
+//
+// The operand is given as s integer slices per entry (see slicer.cu):
+//     Z = 2^{e_row} sum_i d_i 128^{-(i+1)}   (Re and Im planes separately).
+// Then X_{G'G} = 2^{e_G' + e_G} sum_{t} 128^{-t} sum_{i+j=t} D_i(G')^H D_j(G),
+// and the truncated sum keeps the s(s+1)/2 slice pairs with i + j <= s + 1
+// (Ozaki-style split-precision product).  Each slice product is computed
+// EXACTLY: digit products are <= 2^14 and a TMEM FP32 accumulator sums at most
+// 1024 of them between drains (|sum| <= 2^24).  Every drain converts the FP32
+// partial sums to integers and adds them, shifted by the level of the slice
+// pair, into 64-bit fixed-point accumulators held in registers (45 fractional
+// bits), so the cross-slice, cross-atom accumulation is exact integer
+// arithmetic; FP64 is used once per output element at the end.
+//
+// CTA tile: 128 rows (G') x 64 columns (G) of complex output.  Per 64-wide K
+// chunk the producer loads, with TMA and 128-byte swizzle:
+//     A_R = Re slice i, rows G' (128x64 fp16)    A_I = Im slice i, rows G'
+//     B   = [Re slice j, rows G (64x64); Im slice j, rows G (64x64)]
+// and the MMA warp issues two M=128, N=128, K=16 MMAs per 16 columns:
+//     acc1 = A_R B = [RR | RI],   acc2 = A_I B = [IR | II]
+// so  Re X = RR + II,  Im X = RI - IR  (assembled in the drain).  Rows with
+// sigma = -1 form their own K units, subtracted in the drain.
+//
+// Warp roles: warp 0 TMA producer, warp 1 TMEM allocator + MMA issuer,
+// warps 2..9 drain/epilogue (warp w reads TMEM lanes 32*(w%4)..+31; warps
+// 2-5 assemble Re, 6-9 Im).  TMEM: two 256-column buffers (acc1 | acc2) so the
+// drain of one K unit overlaps the MMAs of the next.  Persistent CTAs walk
+// the lower-triangle tile list.  Every wait is bounded by a wall-clock limit;
+// on expiry the CTA records an error, lets its in-flight copies and MMAs
+// complete, frees TMEM and exits.
+#include <cstdint>
+
+#include "flapw_internal.h"
+
+namespace flapw {
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kThreads = 320;
+constexpr uint32_t kHalfTile = 64 * 128;                 // 64 rows x 128 B
+constexpr uint32_t kTileA = 2 * kHalfTile;               // 128 rows
+constexpr uint32_t kStageBytes = 3 * kTileA;             // A_R, A_I, B
+constexpr uint32_t kTmemCols = 512;
+constexpr unsigned long long kWaitNs = 4000000000ull;    // 4 s
+constexpr int kMaxS = 8;
+
+// instruction descriptor: D = F32, A = B = F16, K-major both, N = 128, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((128u >> 3) << 17) |
+                            ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait.  Returns false if the wall-clock limit passed or another role
+// aborted; the first role to time out raises the abort flag.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*abort_flag) return false;
+      if (global_ns() - t0 > kWaitNs) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+// K-major, 128-byte-swizzled operand: 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Slice pairs (i, j), 0-based, are visited by level: t = i + j = 0..s-1
+// (i.e. 1-based levels i + j + 2 <= s + 1), i = 0..t.  Every role walks the
+// same order.
+
+struct Units {
+  int kpc, knc;  // positive / negative chunk counts
+  __device__ int count() const {
+    return (kpc + kUnitChunks - 1) / kUnitChunks + (knc + kUnitChunks - 1) / kUnitChunks;
+  }
+  // unit u -> [c0, c1) chunk range and sign (1 = negative)
+  __device__ void get(int u, int& c0, int& c1, int& neg) const {
+    const int up = (kpc + kUnitChunks - 1) / kUnitChunks;
+    if (u < up) {
+      c0 = u * kUnitChunks;
+      c1 = min(kpc, c0 + kUnitChunks);
+      neg = 0;
+    } else {
+      c0 = kpc + (u - up) * kUnitChunks;
+      c1 = min(kpc + knc, c0 + kUnitChunks);
+      neg = 1;
+    }
+  }
+};
+
+__device__ __forceinline__ Units units_of(const Prob& P) {
+  Units u;
+  u.kpc = (P.kp + kChunk - 1) / kChunk;
+  u.knc = (P.kn + kChunk - 1) / kChunk;
+  return u;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    herk_emu_kernel(const __grid_constant__ CUtensorMap tmap, const Prob* __restrict__ probs,
+                    const EmuTile* __restrict__ tiles, int n_tiles, const int* __restrict__ rexp,
+                    int n_slices, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  // bars: full[4], empty[4], tfull[2], tempty[2], drain[1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * kStages + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * kStages + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 4);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), 256);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const EmuTile T = tiles[tile];
+        const Prob P = probs[T.prob];
+        const Units U = units_of(P);
+        const int nch = U.kpc + U.knc;
+        const int rowA = P.row_base + T.ib * 128, rowB = P.row_base + T.jb * 64;
+        for (int pt = 0; pt < n_slices && ok; ++pt)
+        for (int si = 0; si <= pt && ok; ++si) {
+          const int sj = pt - si;
+          for (int c = 0; c < nch; ++c) {
+            const int stage = it % kStages;
+            const uint32_t round = it / kStages;
+            if (!mbar_wait(empty_bar(stage), (round & 1u) ^ 1u, abort_flag)) {
+              ok = false;
+              break;
+            }
+            const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
+            const uint32_t fb = full_bar(stage);
+            mbar_expect_tx(fb, kStageBytes);
+            const int kc = c * kChunk;
+            tma_load_4d(sbase, &tmap, fb, kc, rowA, 0, si);
+            tma_load_4d(sbase + kHalfTile, &tmap, fb, kc, rowA + 64, 0, si);
+            tma_load_4d(sbase + kTileA, &tmap, fb, kc, rowA, 1, si);
+            tma_load_4d(sbase + kTileA + kHalfTile, &tmap, fb, kc, rowA + 64, 1, si);
+            tma_load_4d(sbase + 2 * kTileA, &tmap, fb, kc, rowB, 0, sj);
+            tma_load_4d(sbase + 2 * kTileA + kHalfTile, &tmap, fb, kc, rowB, 1, sj);
+            ++it;
+          }
+        }
+      }
+      if (!ok) {
+        // let the copies already issued land before the CTA can exit
+        for (uint32_t q = (it > kStages ? it - kStages : 0); q < it; ++q) {
+          const unsigned long long t0 = global_ns();
+          while (!mbar_try_wait(full_bar(q % kStages), (q / kStages) & 1u))
+            if (global_ns() - t0 > kWaitNs) break;
+        }
+        atomicExch(err, FLAPW_ERR_TIMEOUT);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t it = 0, acc_it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const EmuTile T = tiles[tile];
+        const Prob P = probs[T.prob];
+        const Units U = units_of(P);
+        const int nu = U.count();
+        const int npairs = n_slices * (n_slices + 1) / 2;
+        for (int p = 0; p < npairs && ok; ++p) {
+          for (int u = 0; u < nu && ok; ++u) {
+            int c0, c1, neg;
+            U.get(u, c0, c1, neg);
+            const int buf = acc_it & 1;
+            const uint32_t use = acc_it >> 1;
+            if (!mbar_wait(tempty_bar(buf), (use & 1u) ^ 1u, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t d1 = tmem_base + (uint32_t)buf * 256u;
+            const uint32_t d2 = d1 + 128u;
+            for (int c = c0; c < c1; ++c) {
+              const int stage = it % kStages;
+              if (!mbar_wait(full_bar(stage), (it / kStages) & 1u, abort_flag)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
+              const uint64_t dar = sdesc(sbase), dai = sdesc(sbase + kTileA),
+                             db = sdesc(sbase + 2 * kTileA);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t acc = (c > c0 || kk > 0) ? 1u : 0u;
+                umma(d1, dar + 2 * kk, db + 2 * kk, acc);
+                umma(d2, dai + 2 * kk, db + 2 * kk, acc);
+              }
+              umma_commit(empty_bar(stage));
+              ++it;
+            }
+            if (!ok) break;
+            umma_commit(tfull_bar(buf));
+            ++acc_it;
+          }
+        }
+      }
+      // all MMAs issued so far complete before teardown
+      umma_commit(drain_bar);
+      const unsigned long long t0 = global_ns();
+      while (!mbar_try_wait(drain_bar, 0))
+        if (global_ns() - t0 > kWaitNs) break;
+      if (!ok) atomicExch(err, FLAPW_ERR_TIMEOUT);
+    }
+  } else {
+    // ---------------- drain + epilogue (256 threads) ----------------
+    const int ew = warp - 2;
+    const int q = warp & 3;       // TMEM lane quadrant this warp may access
+    const int h = ew >> 2;        // 0: Re, 1: Im
+    const int m = q * 32 + lane;  // row within the tile
+    uint32_t acc_it = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      const EmuTile T = tiles[tile];
+      const Prob P = probs[T.prob];
+      const Units U = units_of(P);
+      const int nu = U.count();
+      long long acc[64];
+#pragma unroll
+      for (int n = 0; n < 64; ++n) acc[n] = 0;
+      for (int pt = 0; pt < n_slices && ok; ++pt)
+      for (int pi = 0; pi <= pt && ok; ++pi) {
+        const int sh = kFixedFrac - kSliceBits * (pt + 2);
+        for (int u = 0; u < nu; ++u) {
+          int c0, c1, neg;
+          U.get(u, c0, c1, neg);
+          const int buf = acc_it & 1;
+          const uint32_t use = acc_it >> 1;
+          if (!mbar_wait(tfull_bar(buf), use & 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * 256u;
+          // Re: acc1[0:64] + acc2[64:128];  Im: acc1[64:128] - acc2[0:64]
+          const uint32_t col1 = h ? 64u : 0u, col2 = h ? 128u : 192u;
+#pragma unroll
+          for (int cb = 0; cb < 8; ++cb) {
+            uint32_t x1[8], x2[8];
+            tmem_ld8(tb + col1 + 8u * cb, x1);
+            tmem_ld8(tb + col2 + 8u * cb, x2);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int v1 = __float2int_rn(__uint_as_float(x1[e]));
+              const int v2 = __float2int_rn(__uint_as_float(x2[e]));
+              int v = h ? v1 - v2 : v1 + v2;
+              if (neg) v = -v;
+              long long w;
+              if (sh >= 0) w = (long long)v * (1ll << sh);
+              else w = (long long)((v + (1 << (-sh - 1))) >> (-sh));
+              acc[8 * cb + e] += w;
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(tempty_bar(buf));
+          ++acc_it;
+        }
+      }
+      if (!ok) break;
+      // write the lower-triangle part of the tile
+      const int64_t ng = P.n_g;
+      const int64_t gr = (int64_t)T.ib * 128 + m;
+      if (gr < ng) {
+        const int er = rexp[P.row_base + gr];
+        double* outd = reinterpret_cast<double*>(P.out);
+#pragma unroll
+        for (int n = 0; n < 64; ++n) {
+          const int64_t gc = (int64_t)T.jb * 64 + n;
+          if (gc < ng && gc <= gr) {
+            const int ex = er + rexp[P.row_base + gc] - kFixedFrac;
+            const double scale = __longlong_as_double((long long)(ex + 1023) << 52);
+            const double val = (double)acc[n] * scale;
+            const int64_t o = (P.layout == FLAPW_LAYOUT_LOWER_PACKED)
+                                  ? gc * ng - gc * (gc - 1) / 2 + (gr - gc)
+                                  : gc * P.ld + gr;
+            outd[2 * o + h] = val;
+          }
+        }
+      }
+    }
+    if (!ok) atomicExch(err, FLAPW_ERR_TIMEOUT);
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+}  // namespace
+
+size_t herk_emu_smem_bytes() { return kStages * kStageBytes + 1024 + 256; }
+
+cudaError_t launch_herk_emu(const CUtensorMap& tmap, const Prob* probs, const EmuTile* tiles,
+                            int n_tiles, const int* rexp, int n_slices, int* err, int grid,
+                            cudaStream_t st) {
+  if (n_tiles == 0) return cudaSuccess;
+  if (n_slices < 1 || n_slices > kMaxS) return cudaErrorInvalidValue;
+  static bool attr = false;
+  const size_t smem = herk_emu_smem_bytes();
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(herk_emu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  herk_emu_kernel<<<grid, kThreads, smem, st>>>(tmap, probs, tiles, n_tiles, rexp, n_slices, err);
+  return cudaGetLastError();
+}
+
+// Tensor map over SL[slice][plane][row][k] (fp16), 64 x 64 boxes, 128-byte swizzle.
+bool make_slice_tmap(CUtensorMap* map, void* base, int64_t k_alloc, int64_t rows, int n_slices,
+                     std::string* err) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p) {
+      *err = "cuTensorMapEncodeTiled is not available from the driver";
+      return false;
+    }
+    fn = reinterpret_cast<EncodeFn>(p);
+  }
+  const cuuint64_t dims[4] = {(cuuint64_t)k_alloc, (cuuint64_t)rows, 2, (cuuint64_t)n_slices};
+  const cuuint64_t strides[3] = {(cuuint64_t)k_alloc * 2, (cuuint64_t)(rows * k_alloc * 2),
+                                 (cuuint64_t)(2 * rows * k_alloc * 2)};
+  const cuuint32_t box[4] = {64, 64, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    *err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+    return false;
+  }
+  return true;
+}
+
+}  // namespace flapw

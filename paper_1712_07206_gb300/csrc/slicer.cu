@@ -1,0 +1,133 @@
+// Split-precision slicing of the FP64 operand for the emulated contraction.
+//
+// Every operand row (one plane wave G of one problem) gets a power-of-two
+// scale 2^e with max_k max(|Re Z_kG|, |Im Z_kG|) < 2^e.  Each entry x is then
+// rounded to the fixed-point integer X = round(x 2^{7s - e}) (|X| <= 2^{7s})
+// and written as s balanced base-128 digits
+//     X = sum_{i=0}^{s-1} d_i 128^{s-1-i},  |d_0| <= 128,  |d_i| <= 64 (i > 0),
+// each carried exactly by an fp16 value.  Products of two digits are at most
+// 2^14, so 1024 of them sum exactly in FP32.  Everything here is integer bit
+// manipulation of the IEEE-754 encoding: FP64 arithmetic is scarce on this
+// part.  The rounding of X is the only approximation (|x - X 2^{e-7s}| <=
+// 2^{e-7s-1}).
+//
+// Output layout: SL[slice][plane][row][k], k contiguous, fp16; plane 0 = Re,
+// 1 = Im.  Columns outside the problem's valid K ranges are written as 0.
+#include <cstdint>
+
+#include "flapw_internal.h"
+
+namespace flapw {
+namespace {
+
+__device__ __forceinline__ uint64_t absbits(double x) {
+  return (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// round(x * 2^shift0) as a signed integer, from the bit pattern.
+__device__ __forceinline__ long long fixed_point(double x, int shift0) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return 0;  // zero or subnormal: below every slice
+  const uint64_t mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = ex - 1075 + shift0;
+  long long X;
+  if (sh >= 0) {
+    X = (long long)(mant << sh);
+  } else {
+    const int r = -sh;
+    X = (r > 62) ? 0 : (long long)((mant + (1ull << (r - 1))) >> r);
+  }
+  return (b >> 63) ? -X : X;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(256) slicer_kernel(const double2* __restrict__ Z, int64_t k_alloc,
+                                                     const Prob* __restrict__ probs,
+                                                     const int* __restrict__ row_prob, int64_t rows,
+                                                     __half* __restrict__ SL, int* __restrict__ rexp) {
+  __shared__ unsigned long long red[8];
+  const int64_t row = blockIdx.x;
+  const Prob P = probs[row_prob[row]];
+  const int64_t kp = P.kp, kn = P.kn;
+  const int64_t kp_pad = (kp + kChunk - 1) / kChunk * kChunk;
+  const double2* zr = Z + row * k_alloc;
+  auto valid = [&](int64_t c) { return c < kp || (c >= kp_pad && c < kp_pad + kn); };
+  unsigned long long m = 0;
+  for (int64_t c = threadIdx.x; c < k_alloc; c += blockDim.x) {
+    if (valid(c)) {
+      const double2 z = zr[c];
+      const unsigned long long a = absbits(z.x), b = absbits(z.y);
+      m = a > m ? a : m;
+      m = b > m ? b : m;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_down_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_down_sync(0xffffffffu, m, o);
+      m = v > m ? v : m;
+    }
+    if (threadIdx.x == 0) red[0] = m;
+  }
+  __syncthreads();
+  const unsigned long long M = red[0];
+  const int e = (M == 0) ? 0 : (int)((M >> 52) & 0x7FF) - 1022;  // M < 2^e
+  if (threadIdx.x == 0) rexp[row] = e;
+  const int shift0 = kSliceBits * NS - e;
+  const int64_t plane_stride = rows * k_alloc;
+  for (int64_t c0 = (int64_t)threadIdx.x * 8; c0 < k_alloc; c0 += (int64_t)blockDim.x * 8) {
+    double2 z[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) z[q] = valid(c0 + q) ? zr[c0 + q] : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int plane = 0; plane < 2; ++plane) {
+      __align__(16) __half d[NS][8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        long long X = fixed_point(plane ? z[q].y : z[q].x, shift0);
+#pragma unroll
+        for (int i = NS - 1; i >= 1; --i) {
+          const long long di = ((X + 64) & 127) - 64;
+          d[i][q] = __ll2half_rn(di);
+          X = (X - di) >> kSliceBits;
+        }
+        d[0][q] = __ll2half_rn(X);
+      }
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        __half* dst = SL + ((int64_t)(2 * i + plane)) * plane_stride + row * k_alloc + c0;
+        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(d[i]);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_slicer(const double2* Z, int64_t k_alloc, const Prob* probs, int n_prob,
+                          const int* row_prob, int64_t rows, int n_slices, __half* SL,
+                          int* rexp, cudaStream_t st) {
+  (void)n_prob;
+  if (rows == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)rows;
+  switch (n_slices) {
+    case 4: slicer_kernel<4><<<grid, 256, 0, st>>>(Z, k_alloc, probs, row_prob, rows, SL, rexp); break;
+    case 5: slicer_kernel<5><<<grid, 256, 0, st>>>(Z, k_alloc, probs, row_prob, rows, SL, rexp); break;
+    case 6: slicer_kernel<6><<<grid, 256, 0, st>>>(Z, k_alloc, probs, row_prob, rows, SL, rexp); break;
+    case 7: slicer_kernel<7><<<grid, 256, 0, st>>>(Z, k_alloc, probs, row_prob, rows, SL, rexp); break;
+    case 8: slicer_kernel<8><<<grid, 256, 0, st>>>(Z, k_alloc, probs, row_prob, rows, SL, rexp); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace flapw

@@ -1,0 +1,347 @@
+// Factorisation of each Hermitian T block (Sec. 3, Alg. 1: the Cholesky
+// factorisation of T^AA that turns A^H T A into a Hermitian rank-K update).
+//
+// The full 2N_L x 2N_L block T = [[T^AA, T^AB],[T^BA, T^BB]] is factorised at
+// once, so that  H_a = W_a^H T W_a = (C^H W_a)^H diag(sigma) (C^H W_a),
+// W_a = [A_a; B_a].  T is generally indefinite (the paper notes that even
+// T^AA's Cholesky "may fail"), so instead of plain Cholesky the kernel runs
+// the Bunch-Kaufman diagonal-pivoting LDL^H (1x1 and 2x2 pivots) in FP64:
+//     P^T T P = L D L^H,
+// splits every 2x2 block of D as Q Lambda Q^H, and returns
+//     C^H = |Lambda|^{1/2} Q^H L^H P^T,   sigma = sign(Lambda),
+// with the rows of C^H reordered sigma = +1 first, then -1 (zero pivots drop).
+//
+// One CTA per T slot, the matrix in global memory (L2 resident), lower
+// triangle only.  The work is tiny next to the contraction; it is latency-
+// bound (n sequential pivot steps).
+#include <cmath>
+
+#include "flapw_internal.h"
+
+namespace flapw {
+namespace {
+
+constexpr int kMaxN = 2 * kMaxNL;
+constexpr int kTfThreads = 512;
+
+__device__ __forceinline__ double cabs1(double2 z) { return fabs(z.x) + fabs(z.y); }
+__device__ __forceinline__ double2 cconj(double2 z) { return make_double2(z.x, -z.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Block-wide argmax of v (ties: smallest index).  Returns through shared.
+__device__ void block_argmax(double v, int idx, double* s_val, int* s_idx, double* out_v,
+                             int* out_i) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, v, o);
+    const int oi = __shfl_down_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) {
+      v = ov;
+      idx = oi;
+    }
+  }
+  if (lane == 0) {
+    s_val[w] = v;
+    s_idx[w] = idx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bv = s_val[0];
+    int bi = s_idx[0];
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i)
+      if (s_val[i] > bv || (s_val[i] == bv && s_idx[i] < bi)) {
+        bv = s_val[i];
+        bi = s_idx[i];
+      }
+    *out_v = bv;
+    *out_i = bi;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, int n,
+                                                             double2* work, double2* CH,
+                                                             int* npos, int* nneg, int* npiv2,
+                                                             int* err) {
+  const int slot = blockIdx.x;
+  const double2* Ts = T + (int64_t)slot * n * n;
+  double2* A = work + (int64_t)slot * n * n;
+  double2* C = CH + (int64_t)slot * n * n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  __shared__ int perm[kMaxN], pinv[kMaxN], blk[kMaxN], outrow[kMaxN];
+  __shared__ double lam[kMaxN];
+  __shared__ double2 qv[kMaxN][2];
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ double s_colmax, s_rowmax;
+  __shared__ int s_imax, s_jmax;
+  __shared__ int s_bad;
+
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx % n;
+    A[idx] = (i >= j) ? Ts[idx] : make_double2(0.0, 0.0);
+    C[idx] = make_double2(0.0, 0.0);
+  }
+  for (int i = tid; i < n; i += nt) perm[i] = i;
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+
+  const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+  int k = 0, n2 = 0;
+  while (k < n) {
+    // largest off-diagonal entry of column k
+    double v = -1.0;
+    int vi = n;
+    for (int i = k + 1 + tid; i < n; i += nt) {
+      const double c = cabs1(A[(int64_t)i * n + k]);
+      if (c > v) {
+        v = c;
+        vi = i;
+      }
+    }
+    block_argmax(v, vi, red_v, red_i, &s_colmax, &s_imax);
+    const double colmax = (k + 1 < n) ? s_colmax : 0.0;
+    const int imax = s_imax;
+    const double absakk = fabs(A[(int64_t)k * n + k].x);
+    int kstep = 1, kp = k;
+    if (fmax(absakk, colmax) == 0.0) {
+      kstep = 1;
+      kp = k;  // zero column: zero pivot, dropped below
+    } else if (absakk >= alpha * colmax) {
+      kstep = 1;
+      kp = k;
+    } else {
+      // largest off-diagonal entry of row/column imax in the trailing matrix
+      double r = -1.0;
+      int ri = n;
+      for (int j = k + tid; j < n; j += nt) {
+        if (j == imax) continue;
+        const double c = (j < imax) ? cabs1(A[(int64_t)imax * n + j]) : cabs1(A[(int64_t)j * n + imax]);
+        if (c > r) {
+          r = c;
+          ri = j;
+        }
+      }
+      block_argmax(r, ri, red_v, red_i, &s_rowmax, &s_jmax);
+      const double rowmax = s_rowmax;
+      if (absakk >= alpha * colmax * (colmax / rowmax)) {
+        kstep = 1;
+        kp = k;
+      } else if (fabs(A[(int64_t)imax * n + imax].x) >= alpha * rowmax) {
+        kstep = 1;
+        kp = imax;
+      } else {
+        kstep = 2;
+        kp = imax;
+      }
+    }
+    const int kk = k + kstep - 1;
+    if (kp != kk) {
+      // symmetric interchange of rows/cols kk and kp (kk < kp), lower storage;
+      // also swaps the rows of the L columns already computed.
+      for (int j = tid; j < n; j += nt) {
+        if (j < kk) {
+          const double2 t = A[(int64_t)kk * n + j];
+          A[(int64_t)kk * n + j] = A[(int64_t)kp * n + j];
+          A[(int64_t)kp * n + j] = t;
+        } else if (j > kk && j < kp) {
+          const double2 t = A[(int64_t)j * n + kk];
+          A[(int64_t)j * n + kk] = cconj(A[(int64_t)kp * n + j]);
+          A[(int64_t)kp * n + j] = cconj(t);
+        } else if (j > kp) {
+          const double2 t = A[(int64_t)j * n + kk];
+          A[(int64_t)j * n + kk] = A[(int64_t)j * n + kp];
+          A[(int64_t)j * n + kp] = t;
+        }
+      }
+      if (tid == 0) {
+        const double2 dk = A[(int64_t)kk * n + kk];
+        A[(int64_t)kk * n + kk] = make_double2(A[(int64_t)kp * n + kp].x, 0.0);
+        A[(int64_t)kp * n + kp] = make_double2(dk.x, 0.0);
+        A[(int64_t)kp * n + kk] = cconj(A[(int64_t)kp * n + kk]);
+        const int t = perm[kk];
+        perm[kk] = perm[kp];
+        perm[kp] = t;
+      }
+    }
+    __syncthreads();
+    const int m = n - k - kstep;  // trailing size
+    if (kstep == 1) {
+      const double d = A[(int64_t)k * n + k].x;
+      if (d != 0.0) {
+        const double rd = 1.0 / d;
+        for (int idx = tid; idx < m * m; idx += nt) {
+          const int ii = idx / m, jj = idx % m;
+          if (jj > ii) continue;
+          const int i = k + 1 + ii, j = k + 1 + jj;
+          const double2 a = A[(int64_t)i * n + k], b = A[(int64_t)j * n + k];
+          double2 u = cmul(a, cconj(b));
+          double2 x = A[(int64_t)i * n + j];
+          x.x -= u.x * rd;
+          x.y = (i == j) ? 0.0 : x.y - u.y * rd;
+          A[(int64_t)i * n + j] = x;
+        }
+        __syncthreads();
+        for (int i = k + 1 + tid; i < n; i += nt) {
+          const double2 a = A[(int64_t)i * n + k];
+          A[(int64_t)i * n + k] = make_double2(a.x * rd, a.y * rd);
+        }
+      }
+      if (tid == 0) {
+        lam[k] = d;
+        blk[k] = 1;
+        qv[k][0] = make_double2(1.0, 0.0);
+        qv[k][1] = make_double2(0.0, 0.0);
+      }
+    } else {
+      const double d11 = A[(int64_t)k * n + k].x, d22 = A[(int64_t)(k + 1) * n + k + 1].x;
+      const double2 d21 = A[(int64_t)(k + 1) * n + k];
+      const double det = d11 * d22 - (d21.x * d21.x + d21.y * d21.y);
+      if (det == 0.0) {
+        if (tid == 0) s_bad = 1;
+      } else {
+        const double rdet = 1.0 / det;
+        // W D^{-1}:  l1 = (w1 d22 - w2 d21)/det,  l2 = (w2 d11 - w1 conj(d21))/det
+        for (int idx = tid; idx < m * m; idx += nt) {
+          const int ii = idx / m, jj = idx % m;
+          if (jj > ii) continue;
+          const int i = k + 2 + ii, j = k + 2 + jj;
+          const double2 w1 = A[(int64_t)i * n + k], w2 = A[(int64_t)i * n + k + 1];
+          const double2 t1 = cmul(w2, d21);
+          const double2 t2 = cmul(w1, cconj(d21));
+          const double2 l1 = make_double2((w1.x * d22 - t1.x) * rdet, (w1.y * d22 - t1.y) * rdet);
+          const double2 l2 = make_double2((w2.x * d11 - t2.x) * rdet, (w2.y * d11 - t2.y) * rdet);
+          const double2 v1 = A[(int64_t)j * n + k], v2 = A[(int64_t)j * n + k + 1];
+          const double2 u = cmul(l1, cconj(v1)), u2 = cmul(l2, cconj(v2));
+          double2 x = A[(int64_t)i * n + j];
+          x.x -= u.x + u2.x;
+          x.y = (i == j) ? 0.0 : x.y - (u.y + u2.y);
+          A[(int64_t)i * n + j] = x;
+        }
+        __syncthreads();
+        for (int i = k + 2 + tid; i < n; i += nt) {
+          const double2 w1 = A[(int64_t)i * n + k], w2 = A[(int64_t)i * n + k + 1];
+          const double2 t1 = cmul(w2, d21);
+          const double2 t2 = cmul(w1, cconj(d21));
+          A[(int64_t)i * n + k] = make_double2((w1.x * d22 - t1.x) * rdet, (w1.y * d22 - t1.y) * rdet);
+          A[(int64_t)i * n + k + 1] = make_double2((w2.x * d11 - t2.x) * rdet, (w2.y * d11 - t2.y) * rdet);
+        }
+      }
+      if (tid == 0) {
+        // D = [[a, conj(b)], [b, c]] = Q diag(l+, l-) Q^H
+        const double a = d11, c = d22;
+        const double bb = sqrt(d21.x * d21.x + d21.y * d21.y);
+        const double h = 0.5 * (a - c);
+        const double rt = sqrt(h * h + bb * bb);
+        const double lp = 0.5 * (a + c) + rt, lm = 0.5 * (a + c) - rt;
+        // v+ = [conj(b), l+ - a], v- = [l- - c, b]  (orthogonal since l+ + l- = a + c)
+        double2 p0 = cconj(d21), p1 = make_double2(lp - a, 0.0);
+        double2 q0 = make_double2(lm - c, 0.0), q1 = d21;
+        const double np = sqrt(p0.x * p0.x + p0.y * p0.y + p1.x * p1.x);
+        const double nq = sqrt(q0.x * q0.x + q1.x * q1.x + q1.y * q1.y);
+        p0 = make_double2(p0.x / np, p0.y / np);
+        p1 = make_double2(p1.x / np, 0.0);
+        q0 = make_double2(q0.x / nq, 0.0);
+        q1 = make_double2(q1.x / nq, q1.y / nq);
+        lam[k] = lp;
+        lam[k + 1] = lm;
+        qv[k][0] = p0;      // Q[0][0]
+        qv[k][1] = p1;      // Q[1][0]
+        qv[k + 1][0] = q0;  // Q[0][1]
+        qv[k + 1][1] = q1;  // Q[1][1]
+        blk[k] = 2;
+        blk[k + 1] = 0;
+        ++n2;
+      }
+    }
+    __syncthreads();
+    k += kstep;
+  }
+  for (int i = tid; i < n; i += nt) pinv[perm[i]] = i;
+  if (tid == 0) {
+    int np = 0, nn = 0;
+    for (int r = 0; r < n; ++r)
+      if (lam[r] > 0) ++np;
+      else if (lam[r] < 0) ++nn;
+    int ip = 0, in = np;
+    for (int r = 0; r < n; ++r) {
+      if (lam[r] > 0) outrow[r] = ip++;
+      else if (lam[r] < 0) outrow[r] = in++;
+      else outrow[r] = -1;
+    }
+    npos[slot] = np;
+    nneg[slot] = nn;
+    atomicAdd(npiv2, n2);
+    if (s_bad) atomicExch(err, FLAPW_ERR_FACTOR);
+  }
+  __syncthreads();
+  // C^H[r][c] = sqrt|lam_r| sum_{j in block(r)} conj(Q[j][r]) (L^H P^T)[j][c],
+  // (L^H P^T)[j][c] = conj(L[pinv(c)][j]) with unit diagonal, zero above.
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx / n, c = idx % n;
+    if (outrow[r] < 0) continue;
+    const int i = pinv[c];
+    const int b0 = (blk[r] == 0) ? r - 1 : r;  // first row of r's block
+    const int bs = (blk[b0] == 2) ? 2 : 1;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int e = 0; e < bs; ++e) {
+      const int j = b0 + e;
+      double2 lv;
+      if (i == j) lv = make_double2(1.0, 0.0);
+      else if (i > b0 + bs - 1) lv = cconj(A[(int64_t)i * n + j]);
+      else lv = make_double2(0.0, 0.0);
+      // Q[e][r - b0] for 2x2; 1 for 1x1
+      const double2 q = (bs == 2) ? qv[b0 + (r - b0)][e] : make_double2(1.0, 0.0);
+      const double2 t = cmul(cconj(q), lv);
+      acc.x += t.x;
+      acc.y += t.y;
+    }
+    const double s = sqrt(fabs(lam[r]));
+    C[(int64_t)outrow[r] * n + c] = make_double2(s * acc.x, s * acc.y);
+  }
+}
+
+__global__ void layout_kernel(const int* npos, const int* nneg, const int* atom_slot, int n_atoms,
+                              int n_k, int* pos_off, int* neg_off, int* kpk, Prob* probs,
+                              int k_total) {
+  if (threadIdx.x != 0) return;
+  int p = 0, q = 0;
+  for (int a = 0; a < n_atoms; ++a) {
+    pos_off[a] = p;
+    neg_off[a] = q;
+    p += npos[atom_slot[a]];
+    q += nneg[atom_slot[a]];
+  }
+  const int kp_pad = (p + kChunk - 1) / kChunk * kChunk;
+  kpk[0] = kp_pad;
+  kpk[1] = p;
+  kpk[2] = q;
+  for (int k = 0; k < n_k; ++k) {
+    probs[2 * k].kp = p;
+    probs[2 * k].kn = q;
+  }
+  (void)k_total;
+}
+
+}  // namespace
+
+cudaError_t launch_tfactor(const double2* T, int n, int n_slots, double2* work, double2* CH,
+                           int* npos, int* nneg, int* npiv2, int* err, cudaStream_t st) {
+  if (n > kMaxN) return cudaErrorInvalidValue;
+  tfactor_kernel<<<n_slots, kTfThreads, 0, st>>>(T, n, work, CH, npos, nneg, npiv2, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layout(const int* npos, const int* nneg, const int* atom_slot, int n_atoms,
+                          int n_k, int* pos_off, int* neg_off, int* kpk, Prob* probs,
+                          int k_total, cudaStream_t st) {
+  layout_kernel<<<1, 32, 0, st>>>(npos, nneg, atom_slot, n_atoms, n_k, pos_off, neg_off, kpk,
+                                  probs, k_total);
+  return cudaGetLastError();
+}
+
+}  // namespace flapw

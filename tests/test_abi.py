@@ -1,0 +1,84 @@
+"""C-ABI library: loads without a GPU, exports what include/flapw.h declares,
+and its host-side logic (plane-wave set, argument checks) is right."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1712_07206_gb300 as fl
+from paper_1712_07206_gb300 import inputs
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    fl.build()
+
+
+def test_library_exports_every_declared_symbol():
+    lib = fl.load()
+    syms = fl.declared_symbols()
+    assert len(syms) >= 16
+    for s in syms:
+        assert hasattr(lib, s), s
+
+
+def test_default_options():
+    o = fl.default_options()
+    assert (o.precision, o.n_slices, o.layout, o.operands, o.use_graph) == (
+        fl.PREC_EMU, 7, fl.LAYOUT_LOWER_FULL, fl.OPERANDS_FROM_AB, 0)
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5])
+def test_plane_wave_set_matches_oracle(cfg):
+    p = inputs.CONFIGS[cfg]()
+    for k in range(p.n_k):
+        a = fl.enumerate_g(p.lattice, p.k_frac[k], p.kmax[k])
+        b = oracle.gvectors(p.lattice, p.k_frac[k], p.kmax[k])
+        assert a.shape == b.shape
+        assert np.array_equal(a, b)
+
+
+def test_plane_wave_set_triclinic_and_ties():
+    for seed in range(5):
+        p = inputs.small(100 + seed, n_target=(700,), skew=0.3)
+        a = fl.enumerate_g(p.lattice, p.k_frac[0], p.kmax[0])
+        assert np.array_equal(a, oracle.gvectors(p.lattice, p.k_frac[0], p.kmax[0]))
+    # k = 0 in a cubic cell: large groups of exactly equal |G|
+    lat = np.eye(3) * 7.0
+    a = fl.enumerate_g(lat, [0, 0, 0], 3.1)
+    assert np.array_equal(a, oracle.gvectors(lat, [0, 0, 0], 3.1))
+    assert tuple(a[0]) == (0, 0, 0)
+
+
+def test_enumerate_g_errors():
+    with pytest.raises(fl.FlapwError) as e:
+        fl.enumerate_g(np.zeros((3, 3)), [0, 0, 0], 3.0)
+    assert e.value.code == -1
+    with pytest.raises(fl.FlapwError):
+        fl.enumerate_g(np.eye(3), [0, 0, 0], -1.0)
+    lib = fl.load()
+    assert lib.flapw_enumerate_g(None, None, 1.0, 0, None, None) == -1
+    assert b"NULL" in lib.flapw_last_error(None)
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device():
+    p = inputs.config1()
+    with pytest.raises(fl.FlapwError) as e:
+        fl.hs_create(p.lattice, p.pos_frac, p.atom_type, p.mt_radius, 13, p.k_frac, p.kmax)
+    assert e.value.code == -7
+    with pytest.raises(fl.FlapwError) as e:
+        fl.hs_create(p.lattice, p.pos_frac, [0, 5], p.mt_radius, 4, p.k_frac, p.kmax)
+    assert e.value.code == -1
+    with pytest.raises(fl.FlapwError) as e:
+        fl.hs_create(p.lattice, p.pos_frac, p.atom_type, [-1.0], 4, p.k_frac, p.kmax)
+    assert e.value.code == -1
+    bad = fl.default_options(n_slices=3)
+    with pytest.raises(fl.FlapwError):
+        fl.hs_create(p.lattice, p.pos_frac, p.atom_type, p.mt_radius, 4, p.k_frac, p.kmax, bad)
+
+
+def test_structs_match_header_sizes():
+    # flapw_options: 6 ints + 10 reserved; flapw_stats: 8 doubles + int64 + 8 ints + 8 reserved
+    assert ctypes.sizeof(fl.Options) == 16 * 4
+    assert ctypes.sizeof(fl.Stats) == 8 * 8 + 8 + 8 * 4 + 8 * 4

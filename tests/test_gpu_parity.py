@@ -1,0 +1,192 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: A, B within 1e-13 of the largest entry; H and S within 1e-12
+relative Frobenius error (the bound stated for the emulated path) and 1e-13
+for the FP64 path; integer-valued contractions bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1712_07206_gb300 as fl
+from paper_1712_07206_gb300 import inputs
+
+from helpers import (TOL_EMU, TOL_F64, alloc_out, ab_block, columns_from_lower, herm_relerr,
+                     lower_to_full, oracle_hs, run_ab, run_hs, torch_cuda)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    fl.build()
+    torch = torch_cuda()
+    assert torch.cuda.is_available()
+
+
+# ------------------------------------------------------------- A and B
+
+@pytest.mark.parametrize("seed,lmax,nt", [(1, 4, (300, 170)), (2, 8, (500,)), (3, 0, (40,)),
+                                          (4, 12, (90,))])
+def test_ab_matches_oracle(seed, lmax, nt):
+    p = inputs.small(seed, n_atoms=3, n_types=2, lmax=lmax, n_target=nt)
+    h, A, B = run_ab(p)
+    for k in range(p.n_k):
+        n3 = h.gvectors(k)
+        assert np.array_equal(n3, oracle.gvectors(p.lattice, p.k_frac[k], p.kmax[k]))
+        Ao, Bo = oracle.build_ab(p, k, n3)
+        Ag, Bg = ab_block(p, h, A, k), ab_block(p, h, B, k)
+        assert np.abs(Ag - Ao).max() <= 1e-13 * np.abs(Ao).max()
+        assert np.abs(Bg - Bo).max() <= 1e-13 * np.abs(Bo).max()
+
+
+def test_ab_config2_sampled():
+    p = inputs.config2()
+    h, A, B = run_ab(p)
+    n3 = h.gvectors(0)
+    sel = np.array([0, 1, 2, 100, 1234, 2999, len(n3) - 2, len(n3) - 1])
+    Ao, Bo = oracle.build_ab(p, 0, n3, sel)
+    Ag, Bg = ab_block(p, h, A, 0)[:, :, sel], ab_block(p, h, B, 0)[:, :, sel]
+    assert np.abs(Ag - Ao).max() <= 1e-13 * np.abs(Ao).max()
+    assert np.abs(Bg - Bo).max() <= 1e-13 * np.abs(Bo).max()
+
+
+# ------------------------------------------------------ factorisation
+
+@pytest.mark.parametrize("hpd", [False, True])
+def test_factor_reconstructs_T(hpd):
+    p = inputs.config2(hpd=hpd)
+    h, Hs, Ss, _ = run_hs(p, fl.PREC_FP64)
+    st = h.stats()
+    for slot in range(p.n_slots):
+        CH, npos, nneg = h.factor(slot)
+        n = CH.shape[0]
+        sig = np.concatenate([np.ones(npos), -np.ones(nneg), np.zeros(n - npos - nneg)])
+        R = CH.conj().T @ (sig[:, None] * CH)
+        assert np.linalg.norm(R - p.T[slot]) <= 1e-13 * np.linalg.norm(p.T[slot])
+        ev = np.linalg.eigvalsh(p.T[slot])
+        assert npos == np.sum(ev > 0) and nneg == np.sum(ev < 0)
+    if hpd:
+        assert st["n_neg"] == 0
+
+
+# ------------------------------------------------------ H and S, full
+
+@pytest.mark.parametrize("precision,tol", [(fl.PREC_FP64, TOL_F64), (fl.PREC_EMU, TOL_EMU)])
+@pytest.mark.parametrize("layout", [fl.LAYOUT_LOWER_FULL, fl.LAYOUT_LOWER_PACKED])
+def test_hs_config1_full(precision, tol, layout):
+    p = inputs.config1()
+    h, Hs, Ss, _ = run_hs(p, precision, layout)
+    Ho, So = oracle_hs(p)
+    ng = Ho.shape[0]
+    eh = herm_relerr(lower_to_full(Hs[0], ng, layout), Ho)
+    es = herm_relerr(lower_to_full(Ss[0], ng, layout), So)
+    assert eh <= tol and es <= tol, (eh, es)
+
+
+@pytest.mark.parametrize("precision,tol", [(fl.PREC_FP64, TOL_F64), (fl.PREC_EMU, TOL_EMU)])
+@pytest.mark.parametrize("operands", [fl.OPERANDS_FROM_AB, fl.OPERANDS_FACTORED])
+def test_hs_small_multi_k_ragged(precision, tol, operands):
+    # 2 k-points, N_G not multiples of the tiles, 3 atoms of 2 types, slots != types
+    p = inputs.small(7, n_atoms=3, n_types=2, lmax=3, n_target=(333, 190))
+    p.atom_slot = np.array([1, 0, 1], dtype=np.int32)
+    h, Hs, Ss, _ = run_hs(p, precision, operands=operands)
+    for k in range(p.n_k):
+        Ho, So = oracle_hs(p, k)
+        ng = Ho.shape[0]
+        eh = herm_relerr(lower_to_full(Hs[k], ng, 0), Ho)
+        es = herm_relerr(lower_to_full(Ss[k], ng, 0), So)
+        assert eh <= tol and es <= tol, (k, eh, es)
+
+
+@pytest.mark.parametrize("precision", [fl.PREC_FP64, fl.PREC_EMU])
+def test_hs_edge_one_atom_lmax0_tiny(precision):
+    p = inputs.small(9, n_atoms=1, n_types=1, lmax=0, n_target=(20,))
+    h, Hs, Ss, _ = run_hs(p, precision)
+    Ho, So = oracle_hs(p)
+    ng = Ho.shape[0]
+    tol = TOL_EMU if precision == fl.PREC_EMU else TOL_F64
+    assert herm_relerr(lower_to_full(Hs[0], ng, 0), Ho) <= tol
+    assert herm_relerr(lower_to_full(Ss[0], ng, 0), So) <= tol
+
+
+def test_hs_hpd_T_has_no_negative_rows():
+    p = inputs.small(11, n_atoms=2, n_types=2, lmax=3, n_target=(260,), hpd=True)
+    h, Hs, Ss, _ = run_hs(p, fl.PREC_EMU)
+    assert h.stats()["n_neg"] == 0
+    Ho, So = oracle_hs(p)
+    assert herm_relerr(lower_to_full(Hs[0], Ho.shape[0], 0), Ho) <= TOL_EMU
+
+
+def test_upper_triangle_untouched():
+    p = inputs.config1()
+    torch = torch_cuda()
+    h = fl.from_problem(p, fl.default_options(precision=fl.PREC_EMU))
+    _, A, B = run_ab(p, h)
+    ng = h.num_g(0)
+    H = torch.full((ng * ng,), 7.0 + 3.0j, dtype=torch.complex128, device="cuda")
+    S = torch.full((ng * ng,), 7.0 + 3.0j, dtype=torch.complex128, device="cuda")
+    h.build_HS(p.T, p.atom_slot, p.U, A, B, [H], [S])
+    h.sync()
+    M = H.cpu().numpy().reshape(ng, ng).T  # [row][col]
+    assert np.all(M[np.triu_indices(ng, 1)] == 7.0 + 3.0j)
+
+
+# --------------------------------------------- the contraction step alone
+
+@pytest.mark.parametrize("precision", [fl.PREC_FP64, fl.PREC_EMU])
+@pytest.mark.parametrize("K,N", [(1, 1), (37, 200), (1000, 129), (2100, 321)])
+def test_herk_step_vs_numpy(precision, K, N):
+    torch = torch_cuda()
+    rng = np.random.default_rng(K * 1000 + N)
+    Z = rng.normal(size=(K, N)) + 1j * rng.normal(size=(K, N))
+    Z *= np.exp(rng.uniform(-3, 3, size=(1, N)))          # uneven column scales
+    sig = np.where(rng.uniform(size=K) < 0.2, -1, 1).astype(np.int32)
+    h = fl.engine_create(fl.default_options(precision=precision))
+    Zd = torch.from_numpy(np.asfortranarray(Z).ravel(order="F")).cuda()
+    H = alloc_out(N, 0)
+    h.herk(Zd, K, K, N, sig, H, N)
+    h.sync()
+    R = oracle.herk_lower(Z, sig)
+    tol = TOL_EMU if precision == fl.PREC_EMU else TOL_F64
+    assert herm_relerr(lower_to_full(H, N, 0), R) <= tol
+
+
+@pytest.mark.parametrize("K", [64, 1023, 1024, 1025, 3000])
+def test_herk_integer_data_bit_exact(K):
+    """Entries m/128 with |m| <= 127: one slice carries them exactly, so the
+    emulated product must equal the exact (integer-valued) sum bit for bit,
+    with every partial sum at its largest (exactness of the FP32 tensor-core
+    accumulation over 1024 terms and of the integer drain)."""
+    torch = torch_cuda()
+    N = 192
+    rng = np.random.default_rng(K)
+    M = rng.integers(-127, 128, size=(K, N)) + 1j * rng.integers(-127, 128, size=(K, N))
+    M[:, :3] = 127 + 127j                                   # saturate some columns
+    M[0, :] = 127 + 127j                                    # and make every row max reach 127/128
+    Z = M / 128.0
+    h = fl.engine_create(fl.default_options(precision=fl.PREC_EMU, n_slices=4))
+    Zd = torch.from_numpy(np.asfortranarray(Z).ravel(order="F")).cuda()
+    H = alloc_out(N, 0)
+    h.herk(Zd, K, K, N, None, H, N)
+    h.sync()
+    R = (M.conj().T @ M) / 16384.0                          # exact in FP64 (integers < 2^53)
+    G = lower_to_full(H, N, 0)
+    assert np.array_equal(np.tril(G), np.tril(R))
+
+
+# ------------------------------------------------ larger configs, sampled
+
+@pytest.mark.parametrize("precision,tol", [(fl.PREC_FP64, TOL_F64), (fl.PREC_EMU, TOL_EMU)])
+def test_hs_config2_sampled_columns(precision, tol):
+    p = inputs.config2()
+    h, Hs, Ss, _ = run_hs(p, precision)
+    n3 = h.gvectors(0)
+    ng = len(n3)
+    cols = [0, 1, 63, 64, 127, 128, 1000, 2047, ng - 65, ng - 1]
+    Ho, So = oracle.hs_columns(p, 0, n3, cols)
+    Hg = columns_from_lower(Hs[0], ng, 0, cols)
+    Sg = columns_from_lower(Ss[0], ng, 0, cols)
+    eh = np.linalg.norm(Hg - Ho) / np.linalg.norm(Ho)
+    es = np.linalg.norm(Sg - So) / np.linalg.norm(So)
+    assert eh <= tol and es <= tol, (eh, es)
