@@ -1,0 +1,349 @@
+"""Benchmark of the muffin-tin H/S build on GB300.
+
+One step = one pass of the whole hot path over the workload's k-points:
+plane waves (set up once per handle), A/B generation (flapw_build_AB), T
+factorisation, operand formation, slicing and the lower-triangle contraction
+(flapw_build_HS).  Metric: H+S build TFLOP/s at the Hermitian rank-K count
+16 N_A N_L N_G^2 per k-point (H and S), and ms per k-point; the emulated
+(FP16-slice) path is the headline, the plain FP64 path is measured beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config 2] [--operands factored|from_ab]
+
+Under torchrun with N > 1 every rank runs the same workload on its own GPU
+(independent replicas; the method has no cross-GPU exchange here) and rank 0
+prints one JSON line with the whole-job aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H+S build TFLOP/s & ms/k-point, emulated vs FP64 path, at ≤1e-12 rel err"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), \
+            float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 1900.0, 1700.0, 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.out, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.out):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                pass
+        os.unlink(self.out)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": rows[0][1],
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload(cfg):
+    from paper_1712_07206_gb300 import inputs
+    return inputs.CONFIGS[cfg]()
+
+
+def hs_flops(p, ngs):
+    return 16.0 * p.n_atoms * p.n_L * float(np.sum(np.asarray(ngs, dtype=np.float64) ** 2))
+
+
+def run_ours(args):
+    import torch
+    import paper_1712_07206_gb300 as fl
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    fl.build()
+    p = workload(args.config)
+    operands = fl.OPERANDS_FACTORED if args.operands == "factored" else fl.OPERANDS_FROM_AB
+    layout = fl.LAYOUT_LOWER_PACKED if p.layout == "packed" else fl.LAYOUT_LOWER_FULL
+    opt = fl.default_options(precision=fl.PREC_EMU, layout=layout, operands=operands, n_slices=args.slices)
+    h = fl.from_problem(p, opt)
+    ngs = [h.num_g(k) for k in range(p.n_k)]
+    flops = hs_flops(p, ngs)
+    dev = torch.device("cuda")
+    nab = h.ab_offset(p.n_k)
+    A = torch.empty(nab, dtype=torch.complex128, device=dev)
+    B = torch.empty_like(A)
+
+    def outsz(ng):
+        return ng * (ng + 1) // 2 if layout == fl.LAYOUT_LOWER_PACKED else ng * ng
+
+    H = [torch.zeros(outsz(ng), dtype=torch.complex128, device=dev) for ng in ngs]
+    S = [torch.zeros(outsz(ng), dtype=torch.complex128, device=dev) for ng in ngs]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h.build_AB(p.radial, A, B, stream)
+        h.build_HS(p.T, p.atom_slot, p.U, A, B, H, S, stream)
+
+    def timed(n_steps, collect_kernel=False):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
+        kms = []
+        for i in range(n_steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            if collect_kernel:
+                h.sync()
+                kms.append(h.stats()["ms_contract"])
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev], kms
+
+    for _ in range(args.warmup):
+        step()
+    h.sync()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_wall = time.time()
+    step_ms, _ = timed(args.steps)
+    t_wall = time.time() - t_wall
+    clk = clocks.stop()
+    ms = float(np.mean(step_ms))
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # contraction kernel duration, from the library's own events on the launching stream
+    _, kms = timed(3, collect_kernel=True)
+    st = h.stats()
+    k_ms = float(np.mean(kms))
+    bf16_burst, bf16_sus, hbm, src = peaks()
+    achieved = st["flops_tensor"] / (k_ms * 1e-3) / 1e12
+    n_pairs = args.slices * (args.slices + 1) // 2
+    alg_tensor = n_pairs * 4.0 * st["k_total"] * float(np.sum(np.asarray(ngs, float) ** 2)) * 2
+    achieved_alg = alg_tensor / (k_ms * 1e-3) / 1e12
+    stage = {k: round(st[k], 4) for k in ("ms_ab", "ms_factor", "ms_operands", "ms_slice", "ms_contract",
+                                          "ms_hs_total")}
+    # the plain FP64 path on the same workload (fewer steps: ~0.3 s each)
+    f64_ms = None
+    if args.fp64_steps > 0:
+        h.set_options(fl.default_options(precision=fl.PREC_FP64, layout=layout, operands=operands))
+        step()
+        h.sync()
+        f_ms, _ = timed(args.fp64_steps)
+        f64_ms = float(np.mean(f_ms))
+        h.set_options(opt)
+    # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if args.e2e:
+        Ah = torch.empty(nab, dtype=torch.complex128).pin_memory()
+        Bh = torch.empty_like(Ah).pin_memory()
+        Hh = [torch.empty(outsz(ng), dtype=torch.complex128).pin_memory() for ng in ngs]
+        Sh = [torch.empty(outsz(ng), dtype=torch.complex128).pin_memory() for ng in ngs]
+
+        def step_host():
+            h.build_AB(p.radial, Ah, Bh, stream)
+            h.build_HS(p.T, p.atom_slot, p.U, Ah, Bh, Hh, Sh, stream)
+            h.sync()
+
+        step_host()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            step_host()
+        e_ms = (time.perf_counter() - t0) * 1e3 / args.e2e_steps
+        ab_bytes = 2 * nab * 16
+        h2d = p.T.nbytes + p.U.nbytes + p.radial.nbytes + p.atom_slot.nbytes + \
+            (ab_bytes if operands == fl.OPERANDS_FROM_AB else 0)
+        d2h = ab_bytes + 2 * sum(outsz(ng) for ng in ngs) * 16
+        e2e = {"value": round(flops / (e_ms * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
+               "ms_per_step": round(e_ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    value = flops / (ms * 1e-3) / 1e12 * ws
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "ms_per_kpoint": round(ms / p.n_k, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128 via fp16 slices (int64 accumulation)", "data": "synthetic",
+        "config": {"workload": p.name, "n_atoms": p.n_atoms, "n_types": p.n_types, "lmax": p.lmax,
+                   "n_L": p.n_L, "n_k": p.n_k, "n_g": ngs if len(ngs) <= 4 else [min(ngs), max(ngs)],
+                   "K": int(st["k_total"]), "slices": args.slices, "operands": args.operands,
+                   "layout": p.layout, "l2": "256 MB L2 flush between steps; A/B 166 MB and operands exceed L2",
+                   "flops_per_step": flops, "parallelism": f"replicas{ws}"},
+        "fp64_path": None if f64_ms is None else {
+            "value": round(flops / (f64_ms * 1e-3) / 1e12 * ws, 4), "unit": "TFLOP/s",
+            "ms_per_step": round(f64_ms, 3), "steps": args.fp64_steps},
+        "speedup_emu_vs_fp64": None if f64_ms is None else round(f64_ms / ms, 2),
+        "stages_ms": stage,
+        "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": bf16_burst,
+                     "unit": "TFLOP/s", "frac": round(achieved / bf16_burst, 4), "traffic": args.traffic,
+                     "kernel": "herk_emu_kernel", "kernel_ms": round(k_ms, 4),
+                     "achieved_algorithmic": round(achieved_alg, 2),
+                     "peak_source": f"{src} bf16 burst x 1.0 (fp16 = bf16 nominal rate)"},
+        "e2e": e2e,
+        "gpu_launches": 8 * args.steps,
+        "clocks": clk,
+        "timed_wall_s": round(t_wall, 3),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, h, H, S, layout, ngs, args)
+    h.destroy()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(p, h, H, S, layout, ngs, args):
+    """The oracle on sampled columns of the same workload, timed on the host
+    cores; the same columns check the GPU result (relative error)."""
+    import oracle
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from helpers import columns_from_lower
+
+    oracle.build()
+    n3 = h.gvectors(0)
+    ng = ngs[0]
+    rng = np.random.default_rng(0)
+    cols = np.unique(np.concatenate([[0, ng - 1], rng.integers(0, ng, size=args.cpu_cols - 2)]))
+    t0 = time.perf_counter()
+    Ho, So = oracle.hs_columns(p, 0, n3, cols)
+    dt = time.perf_counter() - t0
+    per_col = 16.0 * p.n_atoms * p.n_L * ng
+    Hg = columns_from_lower(H[0], ng, layout, cols)
+    Sg = columns_from_lower(S[0], ng, layout, cols)
+    eh = float(np.linalg.norm(Hg - Ho) / np.linalg.norm(Ho))
+    es = float(np.linalg.norm(Sg - So) / np.linalg.norm(So))
+    return {"value": round(len(cols) * per_col / dt / 1e12, 6), "unit": "TFLOP/s",
+            "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{len(cols)} of {ng} columns of H and S at k-point 0 (A/B recomputed for every row), {dt:.1f} s",
+            "parity_rel_err": {"H": eh, "S": es}}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1712_07206_gb300 import inputs
+
+    oracle.build()
+    p = inputs.CONFIGS[args.config]()
+    n3 = oracle.gvectors(p.lattice, p.k_frac[0], p.kmax[0])
+    ng = len(n3)
+    per_col = 16.0 * p.n_atoms * p.n_L * ng
+    rng = np.random.default_rng(1)
+
+    def step():
+        cols = rng.integers(0, ng, size=args.ref_cols)
+        oracle.hs_columns(p, 0, n3, cols)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = args.ref_cols * per_col / dt / 1e12
+    sample = f"{args.ref_cols} random columns of H and S per step (of {ng}), workload {p.name}"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "TFLOP/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": p.name, "parallelism": "host cores"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "cores": oracle.max_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--operands", choices=["factored", "from_ab"], default="factored")
+    ap.add_argument("--slices", type=int, default=7)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-cols", type=int, default=48)
+    ap.add_argument("--ref-cols", type=int, default=8)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per contraction launch from an ncu capture")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
