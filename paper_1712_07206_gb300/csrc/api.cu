@@ -27,7 +27,10 @@ struct DevBuf {
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      (void)cudaGetLastError();
+    }
     p = nullptr;
     bytes = 0;
   }
@@ -56,6 +59,7 @@ struct PinBuf {
   size_t bytes = 0;
   ~PinBuf() {
     if (p) cudaFreeHost(p);
+    (void)cudaGetLastError();
   }
   cudaError_t ensure(size_t n) {
     if (n <= bytes && p) return cudaSuccess;
@@ -110,20 +114,25 @@ struct flapw_ctx {
   bool prep_valid = false;
 
   // build_HS workspaces
-  DevBuf d_T, d_work, d_CH, d_cnt, d_slot, d_U, d_off, d_probs, d_rowprob, d_Z, d_SL, d_rexp,
+  DevBuf d_T, d_work, d_CH, d_fac, d_cnt, d_slot, d_U, d_off, d_probs, d_rowprob, d_Z, d_SL, d_rexp,
       d_emu_tiles, d_f64_tiles, d_combo, d_kmap, d_stageA, d_stageB, d_stageOut;
   PinBuf pin_in, pin_probs;
   int64_t k_alloc = 0, rows = 0;
-  int n_emu_tiles = 0, n_f64_tiles = 0, tiles_order = -1;
+  int n_emu_tiles = 0, n_f64_tiles = 0, split_emu = 0, split_f64 = 0, tiles_order = -1;
+  int tile_order = 2;            // emulated tile order in use (see make_tiles)
+  int64_t tuned_key = -1;        // shape the autotuner last ran on
   int64_t tiles_rows_key = -1;
   CUtensorMap tmap{};
   void* tmap_base = nullptr;
   int64_t tmap_k = 0, tmap_rows = 0;
   int tmap_s = 0;
 
-  cudaStream_t cap_stream = nullptr;
-  cudaEvent_t ev[8]{};
-  bool ev_recorded = false, ev_ab = false;
+  cudaStream_t cap_stream = nullptr, aux_stream = nullptr;
+  // events: 0 start, 1 factor done (aux), 2 S operands done, 3 S sliced, 4 S contracted,
+  // 5 end, 6/7 build_AB, 8 H operands start, 9 S operands start, 10 H operands done,
+  // 11 H sliced, 12 H contracted, 13 fork
+  cudaEvent_t ev[16]{};
+  bool ev_recorded = false, ev_ab = false, ev_engine = false;
   cudaStream_t last_stream = nullptr;
   flapw_stats stats{};
   int last_n_slots = 0;
@@ -137,6 +146,8 @@ struct flapw_ctx {
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (aux_stream) cudaStreamDestroy(aux_stream);
+    (void)cudaGetLastError();
   }
 };
 
@@ -179,6 +190,7 @@ int device_setup(flapw_ctx* h) {
      "cudaDeviceGetAttribute");
   for (auto& e : h->ev) CK(h, cudaEventCreate(&e), "cudaEventCreate");
   CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  CK(h, cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking), "cudaStreamCreate");
   CK(h, opform_init(), "constant table upload");
   return FLAPW_OK;
 }
@@ -190,23 +202,33 @@ int upload(flapw_ctx* h, DevBuf& d, const std::vector<T>& v) {
   return FLAPW_OK;
 }
 
-// Emulated contraction tiles (128 x 64) and FP64 tiles (64 x 64) of every
-// problem's lower triangle.  order 0: row blocks outer; 1: column blocks outer.
-void make_tiles(const std::vector<Prob>& probs, int order, std::vector<EmuTile>* emu,
-                std::vector<F64Tile>* f64) {
-  emu->clear();
-  f64->clear();
-  for (int p = 0; p < (int)probs.size(); ++p) {
+// Emulated contraction tiles (128 x 64) and FP64 tiles (64 x 64) of the
+// lower triangles of problems [p0, p1).  The order of the emulated tiles
+// decides which operand rows the ~150 concurrently running tiles share in L2:
+//   order 0: row blocks outer, column blocks inner;  1: column blocks outer;
+//   order 2/3/4: grouped raster -- bands of 8/4/16 row blocks, and within a
+//   band column by column, so the concurrent tiles touch a compact set of rows.
+constexpr int kNumTileOrders = 5;
+void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order,
+                std::vector<EmuTile>* emu, std::vector<F64Tile>* f64) {
+  for (int p = p0; p < p1; ++p) {
     const int ng = probs[p].n_g;
     const int nib = (ng + 127) / 128, njb = (ng + 63) / 64;
+    auto valid = [&](int ib, int jb) { return jb * 64 <= ib * 128 + 127; };
     if (order == 0) {
       for (int ib = 0; ib < nib; ++ib)
         for (int jb = 0; jb < njb; ++jb)
-          if (jb * 64 <= ib * 128 + 127) emu->push_back(EmuTile{p, ib, jb, 0});
-    } else {
+          if (valid(ib, jb)) emu->push_back(EmuTile{p, ib, jb, 0});
+    } else if (order == 1) {
       for (int jb = 0; jb < njb; ++jb)
         for (int ib = 0; ib < nib; ++ib)
-          if (jb * 64 <= ib * 128 + 127) emu->push_back(EmuTile{p, ib, jb, 0});
+          if (valid(ib, jb)) emu->push_back(EmuTile{p, ib, jb, 0});
+    } else {
+      const int band = (order == 2) ? 8 : (order == 3) ? 4 : 16;
+      for (int i0 = 0; i0 < nib; i0 += band)
+        for (int jb = 0; jb < njb; ++jb)
+          for (int ib = i0; ib < std::min(nib, i0 + band); ++ib)
+            if (valid(ib, jb)) emu->push_back(EmuTile{p, ib, jb, 0});
     }
     const int nb = (ng + 63) / 64;
     for (int ib = 0; ib < nb; ++ib)
@@ -229,53 +251,123 @@ size_t out_bytes(int layout, int64_t ng) {
                                                : (size_t)(ng * ng) * 16;
 }
 
-// Enqueues the contraction of prepared operand rows (d_Z) into the outputs
-// described by `probs` (already uploaded to d_probs).
-int enqueue_contraction(flapw_ctx* h, const std::vector<Prob>& probs, cudaStream_t st) {
+// One half of the work: problems [p0, p1), operand rows [row0, row0 + nrows),
+// tiles [t0, t0 + nt) of the uploaded lists.
+struct Half {
+  int64_t row0, nrows;
+  int emu_t0, emu_nt, f64_t0, f64_nt;
+};
+
+// Slices (emulated precision) and contracts one half.  Records ev_sl after
+// the slicer and ev_k after the contraction.
+int enqueue_contraction(flapw_ctx* h, const Half& hf, int max_grid, cudaStream_t st, int ev_sl,
+                        int ev_k) {
   const int s = slices_of(h);
   const int64_t rows = h->rows;
   if (h->opt.precision == FLAPW_PREC_EMU) {
-    CK(h, h->d_SL.ensure((size_t)s * 2 * rows * h->k_alloc * 2), "slice workspace");
-    CK(h, launch_slicer(h->d_Z.as<double2>(), h->k_alloc, h->d_probs.as<Prob>(), (int)probs.size(),
-                        h->d_rowprob.as<int>(), rows, s, h->d_SL.as<__half>(), h->d_rexp.as<int>(), st),
+    CK(h, launch_slicer(h->d_Z.as<double2>(), h->k_alloc, h->d_probs.as<Prob>(), h->d_rowprob.as<int>(),
+                        rows, hf.row0, hf.nrows, s, h->d_SL.as<__half>(), h->d_rexp.as<int>(), st),
        "slicer launch");
-    CK(h, cudaEventRecord(h->ev[3], st), "cudaEventRecord");
-    if (h->tmap_base != h->d_SL.p || h->tmap_k != h->k_alloc || h->tmap_rows != rows ||
-        h->tmap_s != s) {
-      std::string e;
-      if (!make_slice_tmap(&h->tmap, h->d_SL.p, h->k_alloc, rows, s, &e))
-        return fail(h, FLAPW_ERR_CUDA, e);
-      h->tmap_base = h->d_SL.p;
-      h->tmap_k = h->k_alloc;
-      h->tmap_rows = rows;
-      h->tmap_s = s;
-    }
-    const int grid = std::min(h->n_emu_tiles, h->num_sms);
-    CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>(), h->n_emu_tiles,
-                          h->d_rexp.as<int>(), s, h->d_cnt.as<int>() + 2, grid, st),
+    CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
+    const int grid = std::max(1, std::min(hf.emu_nt, max_grid));
+    CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf.emu_t0,
+                          hf.emu_nt, h->d_rexp.as<int>(), s, h->d_cnt.as<int>() + 2, grid, st),
        "emulated contraction launch");
   } else {
-    CK(h, cudaEventRecord(h->ev[3], st), "cudaEventRecord");
+    CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
     CK(h, launch_herk_f64(h->d_Z.as<double2>(), h->k_alloc, h->d_probs.as<Prob>(),
-                          h->d_f64_tiles.as<F64Tile>(), h->n_f64_tiles, st),
+                          h->d_f64_tiles.as<F64Tile>() + hf.f64_t0, hf.f64_nt, st),
        "FP64 contraction launch");
   }
-  CK(h, cudaEventRecord(h->ev[4], st), "cudaEventRecord");
+  CK(h, cudaEventRecord(h->ev[ev_k], st), "cudaEventRecord");
   return FLAPW_OK;
 }
 
-int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int64_t key) {
-  const int order = 0;
-  if (h->tiles_rows_key == key && h->tiles_order == order) return FLAPW_OK;
-  std::vector<EmuTile> emu;
-  std::vector<F64Tile> f64;
-  make_tiles(probs, order, &emu, &f64);
-  h->n_emu_tiles = (int)emu.size();
-  h->n_f64_tiles = (int)f64.size();
-  if (upload(h, h->d_emu_tiles, emu)) return FLAPW_ERR_CUDA;
-  if (upload(h, h->d_f64_tiles, f64)) return FLAPW_ERR_CUDA;
-  h->tiles_rows_key = key;
-  h->tiles_order = order;
+// Slice workspace and its tensor map (host-side; never inside stream capture).
+int ensure_slices(flapw_ctx* h) {
+  if (h->opt.precision != FLAPW_PREC_EMU) return FLAPW_OK;
+  const int s = slices_of(h);
+  CK(h, h->d_SL.ensure((size_t)s * 2 * h->rows * h->k_alloc * 2), "slice workspace");
+  if (h->tmap_base != h->d_SL.p || h->tmap_k != h->k_alloc || h->tmap_rows != h->rows ||
+      h->tmap_s != s) {
+    std::string e;
+    if (!make_slice_tmap(&h->tmap, h->d_SL.p, h->k_alloc, h->rows, s, &e)) return fail(h, FLAPW_ERR_CUDA, e);
+    h->tmap_base = h->d_SL.p;
+    h->tmap_k = h->k_alloc;
+    h->tmap_rows = h->rows;
+    h->tmap_s = s;
+  }
+  return FLAPW_OK;
+}
+
+// Tile lists of problems [0, n_first) then [n_first, n_prob).
+int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int64_t key,
+                 Half* first, Half* second) {
+  const int order = h->tile_order;
+  if (h->tiles_rows_key != key || h->tiles_order != order) {
+    std::vector<EmuTile> emu;
+    std::vector<F64Tile> f64;
+    make_tiles(probs, 0, n_first, order, &emu, &f64);
+    h->split_emu = (int)emu.size();
+    h->split_f64 = (int)f64.size();
+    make_tiles(probs, n_first, (int)probs.size(), order, &emu, &f64);
+    h->n_emu_tiles = (int)emu.size();
+    h->n_f64_tiles = (int)f64.size();
+    if (upload(h, h->d_emu_tiles, emu)) return FLAPW_ERR_CUDA;
+    if (upload(h, h->d_f64_tiles, f64)) return FLAPW_ERR_CUDA;
+    h->tiles_rows_key = key;
+    h->tiles_order = order;
+  }
+  first->emu_t0 = 0;
+  first->emu_nt = h->split_emu;
+  first->f64_t0 = 0;
+  first->f64_nt = h->split_f64;
+  second->emu_t0 = h->split_emu;
+  second->emu_nt = h->n_emu_tiles - h->split_emu;
+  second->f64_t0 = h->split_f64;
+  second->f64_nt = h->n_f64_tiles - h->split_f64;
+  return FLAPW_OK;
+}
+
+// Times the emulated contraction under every tile order on the slices the
+// last build left in place (the outputs are rewritten with the same values)
+// and keeps the fastest order for this shape.
+int autotune_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int64_t key,
+                   int n_slots, cudaStream_t st) {
+  CK(h, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  CK(h, cudaStreamSynchronize(h->aux_stream), "cudaStreamSynchronize");
+  const int s = slices_of(h);
+  float best = 1e30f;
+  int best_o = h->tile_order;
+  for (int o = 0; o < kNumTileOrders; ++o) {
+    h->tile_order = o;
+    Half a, b;
+    if (int rc = ensure_tiles(h, probs, n_first, key, &a, &b)) return rc;
+    float t_best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(h, cudaEventRecord(h->ev[14], st), "cudaEventRecord");
+      for (const Half* hf : {&b, &a}) {
+        const int grid = std::max(1, std::min(hf->emu_nt, h->num_sms));
+        CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf->emu_t0,
+                              hf->emu_nt, h->d_rexp.as<int>(), s, h->d_cnt.as<int>() + 2, grid, st),
+           "emulated contraction launch");
+      }
+      CK(h, cudaEventRecord(h->ev[15], st), "cudaEventRecord");
+      CK(h, cudaEventSynchronize(h->ev[15]), "cudaEventSynchronize");
+      float ms = 0.f;
+      CK(h, cudaEventElapsedTime(&ms, h->ev[14], h->ev[15]), "cudaEventElapsedTime");
+      t_best = std::min(t_best, ms);
+    }
+    if (t_best < best) {
+      best = t_best;
+      best_o = o;
+    }
+  }
+  (void)n_slots;
+  h->tile_order = best_o;
+  Half a, b;
+  if (int rc = ensure_tiles(h, probs, n_first, key, &a, &b)) return rc;
+  h->tuned_key = key;
   return FLAPW_OK;
 }
 
@@ -470,6 +562,7 @@ static int prepare_prep(flapw_ctx* h, cudaStream_t st) {
 }
 
 int flapw_build_AB(flapw_handle h, const double* radial, void* A, void* B, void* stream) {
+  (void)cudaGetLastError();  // a stale error of unrelated code must not fail our launch checks
   if (!h || !radial || !A || !B) return fail(h, FLAPW_ERR_ARG, "NULL argument");
   if (h->engine_only) return fail(h, FLAPW_ERR_STATE, "handle has no crystal");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -516,6 +609,7 @@ int flapw_build_AB(flapw_handle h, const double* radial, void* A, void* B, void*
 int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom_slot,
                    const double* U, const void* A, const void* B, void* const* H,
                    void* const* S, void* stream) {
+  (void)cudaGetLastError();  // a stale error of unrelated code must not fail our launch checks
   if (!h || !T || !atom_slot || !U || !H || !S) return fail(h, FLAPW_ERR_ARG, "NULL argument");
   if (h->engine_only) return fail(h, FLAPW_ERR_STATE, "handle has no crystal");
   const bool factored = h->opt.operands == FLAPW_OPERANDS_FACTORED;
@@ -530,15 +624,16 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   cudaStream_t user_st = static_cast<cudaStream_t>(stream);
   const int n = 2 * h->n_L;
   const int nlp = h->lmax + 1;
+  const int nk = h->n_k;
   const int64_t K = (int64_t)h->n_atoms * n;
   if (K >= ((int64_t)1 << 17)) return fail(h, FLAPW_ERR_UNSUPPORTED, "2 N_A N_L must be below 131072");
   const int layout = h->opt.layout;
 
-  // ---- host-side preparation (not captured) ----
+  // ---- host-side preparation (never captured) ----
   const size_t t_bytes = (size_t)n_slots * n * n * 16;
   const size_t slot_bytes = (size_t)h->n_atoms * 4;
   const size_t u_bytes = (size_t)h->n_types * nlp * 8;
-  // factored mode: (slot, type) combos and their atom lists
+  // factored operands: (slot, type) pairs and their atoms
   std::vector<int> combo_slot, combo_type, combo_atoms, combo_start{0};
   if (factored) {
     std::map<std::pair<int, int>, std::vector<int>> cmb;
@@ -552,36 +647,34 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   }
   const int n_combo = (int)combo_slot.size();
   const size_t cmb_ints = combo_slot.size() * 2 + combo_atoms.size() + combo_start.size();
-  const size_t in_bytes = t_bytes + slot_bytes + u_bytes + cmb_ints * 4 + 256;
-  CK(h, h->pin_in.ensure(in_bytes), "cudaMallocHost");
+  CK(h, h->pin_in.ensure(t_bytes + slot_bytes + u_bytes + cmb_ints * 4 + 256), "cudaMallocHost");
 
-  // outputs
+  // outputs: problem k = H of k-point k, problem nk + k = S of k-point k
   OutPlan op;
-  op.dev.resize(2 * h->n_k);
-  op.host.assign(2 * h->n_k, nullptr);
-  op.bytes.resize(2 * h->n_k);
-  op.stage_off.resize(2 * h->n_k);
-  for (int k = 0; k < h->n_k; ++k) {
-    const int64_t ng = h->goff[k + 1] - h->goff[k];
-    for (int w = 0; w < 2; ++w) {
-      void* p = w ? S[k] : H[k];
-      const int idx = 2 * k + w;
+  op.dev.resize(2 * nk);
+  op.host.assign(2 * nk, nullptr);
+  op.bytes.resize(2 * nk);
+  op.stage_off.resize(2 * nk);
+  for (int w = 0; w < 2; ++w)
+    for (int k = 0; k < nk; ++k) {
+      const int64_t ng = h->goff[k + 1] - h->goff[k];
+      void* ptr = w ? S[k] : H[k];
+      const int idx = w * nk + k;
       op.bytes[idx] = out_bytes(layout, ng);
-      if (is_device_ptr(p)) {
-        op.dev[idx] = static_cast<double2*>(p);
+      if (is_device_ptr(ptr)) {
+        op.dev[idx] = static_cast<double2*>(ptr);
       } else {
-        op.host[idx] = p;
+        op.host[idx] = ptr;
         op.stage_off[idx] = op.stage_bytes;
         op.stage_bytes += round_up((int64_t)op.bytes[idx], 256);
       }
     }
-  }
   if (op.stage_bytes) {
     CK(h, h->d_stageOut.ensure(op.stage_bytes), "staging");
-    for (int i = 0; i < 2 * h->n_k; ++i)
+    for (int i = 0; i < 2 * nk; ++i)
       if (op.host[i]) op.dev[i] = reinterpret_cast<double2*>(h->d_stageOut.as<char>() + op.stage_off[i]);
   }
-  // A/B may be host memory: stage it
+  // A/B in host memory are staged through the device
   const size_t ab_total = (size_t)h->n_atoms * h->n_L * h->g_total;
   const double2* dA = static_cast<const double2*>(A);
   const double2* dB = static_cast<const double2*>(B);
@@ -590,23 +683,22 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     CK(h, h->d_stageA.ensure(ab_total * 16), "staging");
     CK(h, h->d_stageB.ensure(ab_total * 16), "staging");
     stage_ab = true;
+    dA = h->d_stageA.as<double2>();
+    dB = h->d_stageB.as<double2>();
   }
-
-  // problems
-  std::vector<Prob> probs(2 * h->n_k);
-  for (int k = 0; k < h->n_k; ++k) {
+  // problems: H rows are [0, G_total), S rows [G_total, 2 G_total)
+  std::vector<Prob> probs(2 * nk);
+  for (int k = 0; k < nk; ++k) {
     const int ng = (int)(h->goff[k + 1] - h->goff[k]);
-    Prob ph{(int)(2 * h->goff[k]), ng, 0, 0, layout, 0, ng, op.dev[2 * k]};
-    Prob ps{(int)(2 * h->goff[k] + ng), ng, (int)K, 0, layout, 0, ng, op.dev[2 * k + 1]};
-    probs[2 * k] = ph;
-    probs[2 * k + 1] = ps;
+    probs[k] = Prob{(int)h->goff[k], ng, 0, 0, layout, 0, ng, op.dev[k]};
+    probs[nk + k] = Prob{(int)(h->g_total + h->goff[k]), ng, (int)K, 0, layout, 0, ng, op.dev[nk + k]};
   }
   h->rows = 2 * h->g_total;
   h->k_alloc = round_up(K, kChunk) + kChunk;
-  // workspaces
   CK(h, h->d_T.ensure(t_bytes), "workspace");
   CK(h, h->d_work.ensure(t_bytes), "workspace");
   CK(h, h->d_CH.ensure(t_bytes), "workspace");
+  CK(h, h->d_fac.ensure(sizeof(int) * 2 * (size_t)n_slots * n), "workspace");
   CK(h, h->d_cnt.ensure(sizeof(int) * (8 + 2 * (size_t)n_slots)), "workspace");
   CK(h, h->d_slot.ensure(slot_bytes + cmb_ints * 4 + 64), "workspace");
   CK(h, h->d_U.ensure(u_bytes), "workspace");
@@ -614,17 +706,27 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   CK(h, h->d_probs.ensure(sizeof(Prob) * probs.size()), "workspace");
   CK(h, h->d_Z.ensure((size_t)h->rows * h->k_alloc * 16), "operand workspace");
   CK(h, h->d_rexp.ensure((size_t)h->rows * 4), "workspace");
-  if (h->d_rowprob.bytes < (size_t)h->rows * 4 || h->tiles_rows_key != h->rows) {
+  if (h->tiles_rows_key != h->rows) {
     std::vector<int> rp(h->rows);
-    for (int p = 0; p < (int)probs.size(); ++p)
-      for (int g = 0; g < probs[p].n_g; ++g) rp[probs[p].row_base + g] = p;
+    for (int q = 0; q < (int)probs.size(); ++q)
+      for (int g = 0; g < probs[q].n_g; ++g) rp[probs[q].row_base + g] = q;
     if (upload(h, h->d_rowprob, rp)) return FLAPW_ERR_CUDA;
   }
-  if (int rc = ensure_tiles(h, probs, h->rows)) return rc;
+  Half hH, hS;
+  if (int rc = ensure_tiles(h, probs, nk, h->rows, &hH, &hS)) return rc;
+  hH.row0 = 0;
+  hH.nrows = h->g_total;
+  hS.row0 = h->g_total;
+  hS.nrows = h->g_total;
+  if (int rc = ensure_slices(h)) return rc;
   CK(h, h->pin_probs.ensure(sizeof(Prob) * probs.size()), "cudaMallocHost");
+  if (factored && !h->prep_valid) {
+    if (int rc = prepare_prep(h, user_st)) return rc;
+  }
 
-  // pinned inputs (previous replays read them; wait for the stream first)
+  // pinned inputs: earlier launches may still read them
   if (h->last_stream) CK(h, cudaStreamSynchronize(h->last_stream), "cudaStreamSynchronize");
+  CK(h, cudaStreamSynchronize(h->aux_stream), "cudaStreamSynchronize");
   char* pin = static_cast<char*>(h->pin_in.p);
   std::memcpy(pin, T, t_bytes);
   std::memcpy(pin + t_bytes, atom_slot, slot_bytes);
@@ -638,41 +740,49 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   h->last_n_slots = n_slots;
 
   // ---- the enqueued sequence (graph-capturable) ----
+  // S needs no factorisation: its operands, slices and contraction run on the
+  // caller's stream while the T blocks are factorised on the auxiliary
+  // stream; the H work joins both.
   auto enqueue = [&](cudaStream_t st) -> int {
     CK(h, cudaEventRecord(h->ev[0], st), "cudaEventRecord");
     CK(h, cudaMemcpyAsync(h->d_T.p, pin, t_bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
-    CK(h, cudaMemcpyAsync(h->d_slot.p, pin + t_bytes, slot_bytes + 0, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    CK(h, cudaMemcpyAsync(h->d_slot.p, pin + t_bytes, slot_bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
     CK(h, cudaMemcpyAsync(h->d_slot.as<char>() + slot_bytes, pc, cmb_ints * 4, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
     CK(h, cudaMemcpyAsync(h->d_U.p, pin + t_bytes + slot_bytes, u_bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
     CK(h, cudaMemcpyAsync(h->d_probs.p, h->pin_probs.p, sizeof(Prob) * probs.size(), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
     if (stage_ab) {
       CK(h, cudaMemcpyAsync(h->d_stageA.p, A, ab_total * 16, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
       CK(h, cudaMemcpyAsync(h->d_stageB.p, B, ab_total * 16, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
-      dA = h->d_stageA.as<double2>();
-      dB = h->d_stageB.as<double2>();
     }
-    int* cnt = h->d_cnt.as<int>();  // [0]=npiv2 [1]=unused [2]=err [8..]=npos, nneg
+    int* cnt = h->d_cnt.as<int>();  // [0] 2x2 pivots, [2] error flag, [8..] npos, nneg
     CK(h, cudaMemsetAsync(cnt, 0, sizeof(int) * 8, st), "cudaMemsetAsync");
     int* npos = cnt + 8;
     int* nneg = cnt + 8 + n_slots;
-    CK(h, launch_tfactor(h->d_T.as<double2>(), n, n_slots, h->d_work.as<double2>(), h->d_CH.as<double2>(),
-                         npos, nneg, cnt, cnt + 2, st),
-       "T factorisation launch");
     int* pos_off = h->d_off.as<int>();
     int* neg_off = pos_off + h->n_atoms;
     int* kpk = neg_off + h->n_atoms;
-    CK(h, launch_layout(npos, nneg, h->d_slot.as<int>(), h->n_atoms, h->n_k, pos_off, neg_off, kpk,
-                        h->d_probs.as<Prob>(), (int)K, st),
+    int* perm = h->d_fac.as<int>();
+    int* outrow = perm + (size_t)n_slots * n;
+    // fork: factorisation on the auxiliary stream
+    CK(h, cudaEventRecord(h->ev[13], st), "cudaEventRecord");
+    CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev[13], 0), "cudaStreamWaitEvent");
+    CK(h, launch_tfactor(h->d_T.as<double2>(), n, n_slots, h->d_work.as<double2>(), h->d_CH.as<double2>(),
+                         perm, outrow, npos, nneg, cnt, cnt + 2, h->aux_stream),
+       "T factorisation launch");
+    CK(h, launch_layout(npos, nneg, h->d_slot.as<int>(), h->n_atoms, nk, pos_off, neg_off, kpk,
+                        h->d_probs.as<Prob>(), (int)K, h->aux_stream),
        "layout launch");
-    CK(h, cudaEventRecord(h->ev[1], st), "cudaEventRecord");
+    CK(h, cudaEventRecord(h->ev[1], h->aux_stream), "cudaEventRecord");
     OpformArgs oa{};
     oa.n_atoms = h->n_atoms;
     oa.n_L = h->n_L;
     oa.n = n;
-    oa.n_k = h->n_k;
+    oa.n_k = nk;
     oa.atom_slot = h->d_slot.as<int>();
     oa.atom_type = h->d_type.as<int>();
     oa.CH = h->d_CH.as<double2>();
+    oa.perm = perm;
+    oa.outrow = outrow;
     oa.npos = npos;
     oa.nneg = nneg;
     oa.pos_off = pos_off;
@@ -686,6 +796,8 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     oa.n_gtiles = (int)(h->gt64.size() / 2);
     oa.goff = h->d_goff.as<int64_t>();
     oa.g_total = h->g_total;
+    oa.h_row0 = 0;
+    oa.s_row0 = h->g_total;
     oa.A = dA;
     oa.B = dB;
     oa.Yc = h->d_Yc.as<double2>();
@@ -699,28 +811,39 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     oa.combo_atoms = dc + 2 * n_combo;
     oa.combo_start = dc + 2 * n_combo + combo_atoms.size();
     oa.n_combo = n_combo;
-    CK(h, launch_opform_H(oa, factored, st), "H operand launch");
+    // S on the caller's stream, beside the factorisation (which holds n_slots SMs)
+    CK(h, cudaEventRecord(h->ev[9], st), "cudaEventRecord");
     CK(h, launch_opform_S(oa, factored, st), "S operand launch");
     CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
-    if (int rc = enqueue_contraction(h, probs, st)) return rc;
-    for (int i = 0; i < 2 * h->n_k; ++i)
+    if (int rc = enqueue_contraction(h, hS, std::max(1, h->num_sms - n_slots), st, 3, 4)) return rc;
+    // join, then H
+    CK(h, cudaStreamWaitEvent(st, h->ev[1], 0), "cudaStreamWaitEvent");
+    CK(h, cudaEventRecord(h->ev[8], st), "cudaEventRecord");
+    CK(h, launch_opform_H(oa, factored, st), "H operand launch");
+    CK(h, cudaEventRecord(h->ev[10], st), "cudaEventRecord");
+    if (int rc = enqueue_contraction(h, hH, h->num_sms, st, 11, 12)) return rc;
+    for (int i = 0; i < 2 * nk; ++i)
       if (op.host[i]) CK(h, cudaMemcpyAsync(op.host[i], op.dev[i], op.bytes[i], cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
     CK(h, cudaEventRecord(h->ev[5], st), "cudaEventRecord");
     return FLAPW_OK;
   };
 
-  if (factored && !h->prep_valid) {
-    if (int rc = prepare_prep(h, user_st)) return rc;
-  }
   h->ev_recorded = true;
+  h->ev_engine = false;
   h->last_stream = user_st;
-  if (!h->opt.use_graph) return enqueue(user_st);
+  if (!h->opt.use_graph) {
+    if (int rc = enqueue(user_st)) return rc;
+    if (h->opt.autotune && h->opt.precision == FLAPW_PREC_EMU && h->tuned_key != h->rows)
+      return autotune_tiles(h, probs, nk, h->rows, n_slots, user_st);
+    return FLAPW_OK;
+  }
 
-  // graph replay keyed on everything the captured sequence bakes in
+  // graph replay, keyed on everything the captured sequence bakes in
   std::vector<uintptr_t> key{(uintptr_t)A, (uintptr_t)B, (uintptr_t)n_slots, (uintptr_t)h->opt.precision,
                              (uintptr_t)layout, (uintptr_t)h->opt.operands, (uintptr_t)slices_of(h),
-                             (uintptr_t)h->d_Z.p, (uintptr_t)h->d_SL.p, (uintptr_t)h->pin_in.p};
-  for (int k = 0; k < h->n_k; ++k) {
+                             (uintptr_t)h->d_Z.p, (uintptr_t)h->d_SL.p, (uintptr_t)h->pin_in.p,
+                             (uintptr_t)h->d_T.p, (uintptr_t)h->d_stageOut.p, (uintptr_t)h->d_emu_tiles.p};
+  for (int k = 0; k < nk; ++k) {
     key.push_back((uintptr_t)H[k]);
     key.push_back((uintptr_t)S[k]);
   }
@@ -729,10 +852,6 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       cudaGraphExecDestroy(h->gexec);
       h->gexec = nullptr;
     }
-    // make sure every workspace exists before capture (no allocation inside)
-    if (h->opt.precision == FLAPW_PREC_EMU)
-      CK(h, h->d_SL.ensure((size_t)slices_of(h) * 2 * h->rows * h->k_alloc * 2), "slice workspace");
-    key[8] = (uintptr_t)h->d_SL.p;
     CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
     const int rc = enqueue(h->cap_stream);
     cudaGraph_t g = nullptr;
@@ -755,6 +874,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
 
 int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const int* sigma,
                void* H, int64_t ldh, void* stream) {
+  (void)cudaGetLastError();  // a stale error of unrelated code must not fail our launch checks
   if (!h || !Z || !H) return fail(h, FLAPW_ERR_ARG, "NULL argument");
   if (K < 1 || N < 1 || ldz < K) return fail(h, FLAPW_ERR_ARG, "need K >= 1, N >= 1, ldz >= K");
   if (K >= (1 << 17)) return fail(h, FLAPW_ERR_UNSUPPORTED, "K must be below 131072");
@@ -763,9 +883,9 @@ int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const i
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   std::vector<int> pos, neg;
   for (int k = 0; k < K; ++k) {
-    const int s = sigma ? sigma[k] : 1;
-    if (s != 1 && s != -1) return fail(h, FLAPW_ERR_ARG, "sigma entries must be +1 or -1");
-    (s > 0 ? pos : neg).push_back(k);
+    const int sg = sigma ? sigma[k] : 1;
+    if (sg != 1 && sg != -1) return fail(h, FLAPW_ERR_ARG, "sigma entries must be +1 or -1");
+    (sg > 0 ? pos : neg).push_back(k);
   }
   const int64_t kp_pad = round_up((int64_t)pos.size(), kChunk);
   const int64_t k_alloc = std::max<int64_t>(kp_pad + round_up((int64_t)neg.size(), kChunk), kChunk);
@@ -779,6 +899,7 @@ int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const i
     CK(h, h->d_stageOut.ensure(ob), "staging");
     dH = h->d_stageOut.as<double2>();
   }
+  if (h->last_stream) CK(h, cudaStreamSynchronize(h->last_stream), "cudaStreamSynchronize");
   std::vector<Prob> probs{Prob{0, N, (int)pos.size(), (int)neg.size(), h->opt.layout, 0,
                                h->opt.layout == FLAPW_LAYOUT_LOWER_FULL ? ldh : N, dH}};
   h->rows = N;
@@ -786,25 +907,33 @@ int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const i
   if (upload(h, h->d_kmap, kmap) || upload(h, h->d_probs, probs)) return FLAPW_ERR_CUDA;
   std::vector<int> rp(N, 0);
   if (upload(h, h->d_rowprob, rp)) return FLAPW_ERR_CUDA;
-  h->tiles_rows_key = -1;  // force a rebuild
-  if (int rc = ensure_tiles(h, probs, -2 - (int64_t)N)) return rc;
-  h->tiles_rows_key = -1;  // the next build_HS rebuilds its own
+  Half hf, none;
+  h->tiles_rows_key = -1;
+  if (int rc = ensure_tiles(h, probs, 1, -2 - (int64_t)N, &hf, &none)) return rc;
+  h->tiles_rows_key = -1;  // a later build_HS rebuilds its own lists
+  hf.row0 = 0;
+  hf.nrows = N;
   CK(h, h->d_Z.ensure((size_t)N * k_alloc * 16), "operand workspace");
   CK(h, h->d_rexp.ensure((size_t)N * 4), "workspace");
   CK(h, h->d_cnt.ensure(sizeof(int) * 16), "workspace");
+  if (int rc = ensure_slices(h)) return rc;
   CK(h, cudaMemsetAsync(h->d_cnt.p, 0, sizeof(int) * 8, st), "cudaMemsetAsync");
   CK(h, cudaEventRecord(h->ev[0], st), "cudaEventRecord");
-  CK(h, cudaEventRecord(h->ev[1], st), "cudaEventRecord");
   CK(h, launch_gather_Z(static_cast<const double2*>(Z), ldz, K, N, h->d_kmap.as<int>(), k_alloc,
                         h->d_Z.as<double2>(), st),
      "gather launch");
   CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
-  if (int rc = enqueue_contraction(h, probs, st)) return rc;
+  if (int rc = enqueue_contraction(h, hf, h->num_sms, st, 3, 4)) return rc;
   if (!devH) CK(h, cudaMemcpyAsync(H, dH, ob, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
   CK(h, cudaEventRecord(h->ev[5], st), "cudaEventRecord");
   h->ev_recorded = true;
+  h->ev_engine = true;
   h->last_stream = st;
   h->gkey.clear();
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
   return FLAPW_OK;
 }
 
@@ -840,11 +969,17 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
   };
   flapw_stats s = h->stats;
   if (h->ev_ab) s.ms_ab = el(6, 7);
-  if (h->ev_recorded) {
-    s.ms_factor = el(0, 1);
-    s.ms_operands = el(1, 2);
+  if (h->ev_recorded && h->ev_engine) {
+    s.ms_factor = 0.0;
+    s.ms_operands = el(0, 2);
     s.ms_slice = (h->opt.precision == FLAPW_PREC_EMU) ? el(2, 3) : 0.0;
     s.ms_contract = el(3, 4);
+    s.ms_hs_total = el(0, 5);
+  } else if (h->ev_recorded) {
+    s.ms_factor = el(0, 1);
+    s.ms_operands = el(9, 2) + el(8, 10);
+    s.ms_slice = (h->opt.precision == FLAPW_PREC_EMU) ? el(2, 3) + el(10, 11) : 0.0;
+    s.ms_contract = el(3, 4) + el(11, 12);
     s.ms_hs_total = el(0, 5);
   }
   s.n_slices = slices_of(h);
@@ -859,7 +994,9 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
     }
     s.flops_herk = 16.0 * h->n_atoms * h->n_L * ng2;
   }
-  if (h->d_cnt.p && h->d_off.p && h->ev_recorded && !h->engine_only && cudaEventQuery(h->ev[5]) == cudaSuccess) {
+  const bool done = h->ev_recorded && cudaEventQuery(h->ev[5]) == cudaSuccess;
+  (void)cudaGetLastError();
+  if (h->d_cnt.p && h->d_off.p && done && !h->engine_only) {
     int c[8];
     int kpk[3] = {0, 0, 0};
     if (cudaMemcpy(c, h->d_cnt.p, sizeof(c), cudaMemcpyDeviceToHost) == cudaSuccess &&
@@ -894,10 +1031,26 @@ int flapw_get_factor(flapw_handle h, int slot, double* CH, int* n_pos, int* n_ne
   if (slot < 0 || slot >= h->last_n_slots) return fail(h, FLAPW_ERR_ARG, "slot out of range");
   const int n = 2 * h->n_L;
   CK(h, cudaStreamSynchronize(h->last_stream), "cudaStreamSynchronize");
-  CK(h, cudaMemcpy(CH, h->d_CH.as<double2>() + (size_t)slot * n * n, (size_t)n * n * 16, cudaMemcpyDeviceToHost), "cudaMemcpy");
+  CK(h, cudaStreamSynchronize(h->aux_stream), "cudaStreamSynchronize");
+  std::vector<double2> M((size_t)n * n);
+  std::vector<int> perm(n), outrow(n);
+  CK(h, cudaMemcpy(M.data(), h->d_CH.as<double2>() + (size_t)slot * n * n, (size_t)n * n * 16, cudaMemcpyDeviceToHost), "cudaMemcpy");
+  const int* fac = h->d_fac.as<int>();
+  CK(h, cudaMemcpy(perm.data(), fac + (size_t)slot * n, n * 4, cudaMemcpyDeviceToHost), "cudaMemcpy");
+  CK(h, cudaMemcpy(outrow.data(), fac + (size_t)h->last_n_slots * n + (size_t)slot * n, n * 4, cudaMemcpyDeviceToHost), "cudaMemcpy");
   int* cnt = h->d_cnt.as<int>();
   CK(h, cudaMemcpy(n_pos, cnt + 8 + slot, 4, cudaMemcpyDeviceToHost), "cudaMemcpy");
   CK(h, cudaMemcpy(n_neg, cnt + 8 + h->last_n_slots + slot, 4, cudaMemcpyDeviceToHost), "cudaMemcpy");
+  // C^H = M P^T, rows moved to their sigma-grouped places
+  std::memset(CH, 0, sizeof(double) * 2 * (size_t)n * n);
+  for (int r = 0; r < n; ++r) {
+    if (outrow[r] < 0) continue;
+    for (int i = 0; i < n; ++i) {
+      const size_t o = ((size_t)outrow[r] * n + perm[i]) * 2;
+      CH[o] = M[(size_t)r * n + i].x;
+      CH[o + 1] = M[(size_t)r * n + i].y;
+    }
+  }
   return FLAPW_OK;
 }
 
@@ -907,7 +1060,9 @@ const char* flapw_last_error(flapw_handle h) {
 
 int flapw_destroy(flapw_handle h) {
   if (!h) return fail(nullptr, FLAPW_ERR_ARG, "NULL handle");
-  if (h->last_stream) cudaStreamSynchronize(h->last_stream);
+  cudaStreamSynchronize(h->last_stream);
+  if (h->aux_stream) cudaStreamSynchronize(h->aux_stream);
+  (void)cudaGetLastError();
   delete h;
   return FLAPW_OK;
 }

@@ -81,9 +81,11 @@ cudaError_t launch_ab_assemble_tiles(const Geom& geo, const int* gtiles, int n_g
                                      const double* bl, const double2* ph, double2* A, double2* B,
                                      cudaStream_t st);
 
-// Bunch-Kaufman LDL^H of each T block and C^H = |L|^{1/2} Q^H L^H P^T.
+// Bunch-Kaufman LDL^H of each T block: M = |Lambda|^{1/2} Q^H L^H (pivoted
+// order), the pivot permutation and each row's place in the sigma-grouped operand.
 cudaError_t launch_tfactor(const double2* T, int n, int n_slots, double2* work, double2* CH,
-                           int* npos, int* nneg, int* npiv2, int* err, cudaStream_t st);
+                           int* perm, int* outrow, int* npos, int* nneg, int* npiv2, int* err,
+                           cudaStream_t st);
 
 // Atom offsets in the sigma-grouped K order and chunk counts of the H problems.
 cudaError_t launch_layout(const int* npos, const int* nneg, const int* atom_slot, int n_atoms,
@@ -94,7 +96,9 @@ struct OpformArgs {
   int n_atoms, n_L, n, n_k;
   const int* atom_slot;
   const int* atom_type;
-  const double2* CH;    // [slot][n][n]
+  const double2* CH;    // [slot][n][n] M in pivoted order (block upper triangular)
+  const int* perm;      // [slot][n] W row feeding pivoted column c
+  const int* outrow;    // [slot][n] sigma-grouped position of row r, -1 if dropped
   const int* npos;      // [slot]
   const int* nneg;      // [slot]
   const int* pos_off;   // [atom]
@@ -108,6 +112,8 @@ struct OpformArgs {
   int n_gtiles;
   const int64_t* goff;  // [n_k+1]
   int64_t g_total;      // plane waves over all k-points
+  int64_t h_row0;       // operand row of the first H plane wave (k-point 0)
+  int64_t s_row0;       // operand row of the first S plane wave
   // from A/B
   const double2* A;
   const double2* B;
@@ -132,9 +138,10 @@ cudaError_t launch_gather_Z(const double2* Zin, int64_t ldz, int K, int N, const
                             int64_t k_alloc, double2* Z, cudaStream_t st);
 
 // FP64 -> integer slices (fp16 carriers) with per-row power-of-two scaling.
-cudaError_t launch_slicer(const double2* Z, int64_t k_alloc, const Prob* probs, int n_prob,
-                          const int* row_prob, int64_t rows, int n_slices, __half* SL,
-                          int* rexp, cudaStream_t st);
+// Rows [row0, row0 + nrows) of the operand; `rows` is the total row count.
+cudaError_t launch_slicer(const double2* Z, int64_t k_alloc, const Prob* probs,
+                          const int* row_prob, int64_t rows, int64_t row0, int64_t nrows,
+                          int n_slices, __half* SL, int* rexp, cudaStream_t st);
 
 // Contractions.
 cudaError_t launch_herk_f64(const double2* Z, int64_t k_alloc, const Prob* probs,

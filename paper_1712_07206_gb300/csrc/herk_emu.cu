@@ -228,30 +228,34 @@ __global__ void __launch_bounds__(kThreads, 1)
         const EmuTile T = tiles[tile];
         const Prob P = probs[T.prob];
         const Units U = units_of(P);
-        const int nch = U.kpc + U.knc;
+        const int nu = U.count();
         const int rowA = P.row_base + T.ib * 128, rowB = P.row_base + T.jb * 64;
-        for (int pt = 0; pt < n_slices && ok; ++pt)
-        for (int si = 0; si <= pt && ok; ++si) {
-          const int sj = pt - si;
-          for (int c = 0; c < nch; ++c) {
-            const int stage = it % kStages;
-            const uint32_t round = it / kStages;
-            if (!mbar_wait(empty_bar(stage), (round & 1u) ^ 1u, abort_flag)) {
-              ok = false;
-              break;
+        for (int u = 0; u < nu && ok; ++u) {
+          int c0, c1, neg;
+          U.get(u, c0, c1, neg);
+          for (int pt = 0; pt < n_slices && ok; ++pt)
+            for (int si = 0; si <= pt && ok; ++si) {
+              const int sj = pt - si;
+              for (int c = c0; c < c1; ++c) {
+                const int stage = it % kStages;
+                const uint32_t round = it / kStages;
+                if (!mbar_wait(empty_bar(stage), (round & 1u) ^ 1u, abort_flag)) {
+                  ok = false;
+                  break;
+                }
+                const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
+                const uint32_t fb = full_bar(stage);
+                mbar_expect_tx(fb, kStageBytes);
+                const int kc = c * kChunk;
+                tma_load_4d(sbase, &tmap, fb, kc, rowA, 0, si);
+                tma_load_4d(sbase + kHalfTile, &tmap, fb, kc, rowA + 64, 0, si);
+                tma_load_4d(sbase + kTileA, &tmap, fb, kc, rowA, 1, si);
+                tma_load_4d(sbase + kTileA + kHalfTile, &tmap, fb, kc, rowA + 64, 1, si);
+                tma_load_4d(sbase + 2 * kTileA, &tmap, fb, kc, rowB, 0, sj);
+                tma_load_4d(sbase + 2 * kTileA + kHalfTile, &tmap, fb, kc, rowB, 1, sj);
+                ++it;
+              }
             }
-            const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
-            const uint32_t fb = full_bar(stage);
-            mbar_expect_tx(fb, kStageBytes);
-            const int kc = c * kChunk;
-            tma_load_4d(sbase, &tmap, fb, kc, rowA, 0, si);
-            tma_load_4d(sbase + kHalfTile, &tmap, fb, kc, rowA + 64, 0, si);
-            tma_load_4d(sbase + kTileA, &tmap, fb, kc, rowA, 1, si);
-            tma_load_4d(sbase + kTileA + kHalfTile, &tmap, fb, kc, rowA + 64, 1, si);
-            tma_load_4d(sbase + 2 * kTileA, &tmap, fb, kc, rowB, 0, sj);
-            tma_load_4d(sbase + 2 * kTileA + kHalfTile, &tmap, fb, kc, rowB, 1, sj);
-            ++it;
-          }
         }
       }
       if (!ok) {
@@ -275,10 +279,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const Units U = units_of(P);
         const int nu = U.count();
         const int npairs = n_slices * (n_slices + 1) / 2;
-        for (int p = 0; p < npairs && ok; ++p) {
-          for (int u = 0; u < nu && ok; ++u) {
-            int c0, c1, neg;
-            U.get(u, c0, c1, neg);
+        for (int u = 0; u < nu && ok; ++u) {
+          int c0, c1, neg;
+          U.get(u, c0, c1, neg);
+          for (int p = 0; p < npairs && ok; ++p) {
             const int buf = acc_it & 1;
             const uint32_t use = acc_it >> 1;
             if (!mbar_wait(tempty_bar(buf), (use & 1u) ^ 1u, abort_flag)) {
@@ -336,12 +340,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       long long acc[64];
 #pragma unroll
       for (int n = 0; n < 64; ++n) acc[n] = 0;
-      for (int pt = 0; pt < n_slices && ok; ++pt)
-      for (int pi = 0; pi <= pt && ok; ++pi) {
-        const int sh = kFixedFrac - kSliceBits * (pt + 2);
-        for (int u = 0; u < nu; ++u) {
-          int c0, c1, neg;
-          U.get(u, c0, c1, neg);
+      for (int u = 0; u < nu && ok; ++u) {
+        int c0, c1, neg;
+        U.get(u, c0, c1, neg);
+        for (int pt = 0; pt < n_slices && ok; ++pt)
+        for (int pi = 0; pi <= pt && ok; ++pi) {
+          const int sh = kFixedFrac - kSliceBits * (pt + 2);
           const int buf = acc_it & 1;
           const uint32_t use = acc_it >> 1;
           if (!mbar_wait(tfull_bar(buf), use & 1u, abort_flag)) {
@@ -349,6 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
+          __syncwarp();  // tcgen05.ld is warp-collective
           const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * 256u;
           // Re: acc1[0:64] + acc2[64:128];  Im: acc1[64:128] - acc2[0:64]
           const uint32_t col1 = h ? 64u : 0u, col2 = h ? 128u : 192u;
@@ -403,6 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
+    __syncwarp();
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
                  "r"(kTmemCols)

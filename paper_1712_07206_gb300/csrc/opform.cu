@@ -11,7 +11,10 @@
 // sigma = -1 rows (offset neg_off[a]).
 //
 // FP64 SIMT: a 32 (C^H rows) x 64 (plane waves) tile per CTA, the 2N_L-long
-// reduction staged through shared memory 16 at a time.
+// reduction staged through shared memory 16 at a time.  C^H = M P^T with M
+// block upper triangular in pivoted order: the W rows are gathered through
+// the permutation and the reduction starts at the tile's first nonzero column,
+// which halves the FP64 work of a dense product.
 //
 // The factored variant uses A_a = diag(e^{iK.tau_a}) A_t (A depends on the
 // atom only through its structure-factor phase): Z_{slot,t} = C^H [A_t; B_t]
@@ -77,7 +80,9 @@ __global__ void __launch_bounds__(256) opform_h_kernel(OpformArgs p, int64_t G) 
   double2 acc[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) acc[e] = make_double2(0.0, 0.0);
-  for (int c0 = 0; c0 < n; c0 += kCT) {
+  const int* perm = p.perm + (int64_t)slot * n;
+  const int c_begin = (r0 > 0 ? r0 - 1 : 0) / kCT * kCT;  // M[r][c] = 0 for c < r - 1
+  for (int c0 = c_begin; c0 < n; c0 += kCT) {
     for (int idx = tid; idx < kCT * kRT; idx += 256) {
       const int rr = idx / kCT, cc = idx % kCT;
       const int r = r0 + rr, c = c0 + cc;
@@ -88,8 +93,9 @@ __global__ void __launch_bounds__(256) opform_h_kernel(OpformArgs p, int64_t G) 
       const int c = c0 + cc, g = g0 + gg;
       double2 w = make_double2(0.0, 0.0);
       if (c < n && g < ng) {
-        if (kFactored) w = w_type(p, type, c, p.goff[k] + g, G);
-        else w = w_from_ab(p, a_single, c, k, g, ng);
+        const int src = perm[c];
+        if (kFactored) w = w_type(p, type, src, p.goff[k] + g, G);
+        else w = w_from_ab(p, a_single, src, k, g, ng);
       }
       ws[cc][gg] = w;
     }
@@ -102,10 +108,11 @@ __global__ void __launch_bounds__(256) opform_h_kernel(OpformArgs p, int64_t G) 
     }
     __syncthreads();
   }
-  const int r = r0 + rl;
+  if (r0 + rl >= n) return;
+  const int r = p.outrow[(int64_t)slot * n + r0 + rl];  // sigma-grouped position
   const int np = p.npos[slot];
-  if (r >= np + p.nneg[slot]) return;  // zero rows of C^H (dropped pivots) are not stored
-  const int64_t row0 = 2 * p.goff[k];  // H problem of k-point k
+  if (r < 0) return;  // zero pivot: the row carries nothing
+  const int64_t row0 = p.h_row0 + p.goff[k];
   if (kFactored) {
     for (int ai = p.combo_start[blockIdx.z]; ai < p.combo_start[blockIdx.z + 1]; ++ai) {
       const int a = p.combo_atoms[ai];
@@ -168,7 +175,7 @@ __global__ void __launch_bounds__(256) opform_s_kernel(OpformArgs p, int64_t G) 
     tile[cc][gg] = w;
   }
   __syncthreads();
-  const int64_t row0 = 2 * p.goff[k] + ng;  // S problem of k-point k
+  const int64_t row0 = p.s_row0 + p.goff[k];
   for (int idx = threadIdx.x; idx < kRT * kGT; idx += 256) {
     const int gg = idx / kRT, cc = idx % kRT;
     const int c = c0 + cc, g = g0 + gg;

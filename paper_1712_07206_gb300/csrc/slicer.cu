@@ -45,9 +45,10 @@ template <int NS>
 __global__ void __launch_bounds__(256) slicer_kernel(const double2* __restrict__ Z, int64_t k_alloc,
                                                      const Prob* __restrict__ probs,
                                                      const int* __restrict__ row_prob, int64_t rows,
-                                                     __half* __restrict__ SL, int* __restrict__ rexp) {
+                                                     int64_t row0, __half* __restrict__ SL,
+                                                     int* __restrict__ rexp) {
   __shared__ unsigned long long red[8];
-  const int64_t row = blockIdx.x;
+  const int64_t row = row0 + blockIdx.x;
   const Prob P = probs[row_prob[row]];
   const int64_t kp = P.kp, kn = P.kn;
   const int64_t kp_pad = (kp + kChunk - 1) / kChunk * kChunk;
@@ -113,18 +114,22 @@ __global__ void __launch_bounds__(256) slicer_kernel(const double2* __restrict__
 
 }  // namespace
 
-cudaError_t launch_slicer(const double2* Z, int64_t k_alloc, const Prob* probs, int n_prob,
-                          const int* row_prob, int64_t rows, int n_slices, __half* SL,
-                          int* rexp, cudaStream_t st) {
-  (void)n_prob;
-  if (rows == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)rows;
+cudaError_t launch_slicer(const double2* Z, int64_t k_alloc, const Prob* probs,
+                          const int* row_prob, int64_t rows, int64_t row0, int64_t nrows,
+                          int n_slices, __half* SL, int* rexp, cudaStream_t st) {
+  if (nrows == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)nrows;
   switch (n_slices) {
-    case 4: slicer_kernel<4><<<grid, 256, 0, st>>>(Z, k_alloc, probs, row_prob, rows, SL, rexp); break;
-    case 5: slicer_kernel<5><<<grid, 256, 0, st>>>(Z, k_alloc, probs, row_prob, rows, SL, rexp); break;
-    case 6: slicer_kernel<6><<<grid, 256, 0, st>>>(Z, k_alloc, probs, row_prob, rows, SL, rexp); break;
-    case 7: slicer_kernel<7><<<grid, 256, 0, st>>>(Z, k_alloc, probs, row_prob, rows, SL, rexp); break;
-    case 8: slicer_kernel<8><<<grid, 256, 0, st>>>(Z, k_alloc, probs, row_prob, rows, SL, rexp); break;
+#define FLAPW_SLICER_CASE(NS)                                                                    \
+  case NS:                                                                                       \
+    slicer_kernel<NS><<<grid, 256, 0, st>>>(Z, k_alloc, probs, row_prob, rows, row0, SL, rexp); \
+    break;
+    FLAPW_SLICER_CASE(4)
+    FLAPW_SLICER_CASE(5)
+    FLAPW_SLICER_CASE(6)
+    FLAPW_SLICER_CASE(7)
+    FLAPW_SLICER_CASE(8)
+#undef FLAPW_SLICER_CASE
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -7,9 +7,13 @@
 // T^AA's Cholesky "may fail"), so instead of plain Cholesky the kernel runs
 // the Bunch-Kaufman diagonal-pivoting LDL^H (1x1 and 2x2 pivots) in FP64:
 //     P^T T P = L D L^H,
-// splits every 2x2 block of D as Q Lambda Q^H, and returns
-//     C^H = |Lambda|^{1/2} Q^H L^H P^T,   sigma = sign(Lambda),
-// with the rows of C^H reordered sigma = +1 first, then -1 (zero pivots drop).
+// splits every 2x2 block of D as Q Lambda Q^H, and returns, in pivoted order,
+//     M = |Lambda|^{1/2} Q^H L^H,   sigma = sign(Lambda),
+// so that C^H = M P^T: the operand rows are M times the W rows gathered by
+// the permutation.  M is block upper triangular (zero left of each pivot
+// block), which the operand formation exploits.  Each row's place in the
+// sigma-grouped operand (sigma = +1 rows first, then -1; zero pivots drop)
+// is returned in `outrow`.
 //
 // One CTA per T slot, the matrix in global memory (L2 resident), lower
 // triangle only.  The work is tiny next to the contraction; it is latency-
@@ -64,6 +68,7 @@ __device__ void block_argmax(double v, int idx, double* s_val, int* s_idx, doubl
 
 __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, int n,
                                                              double2* work, double2* CH,
+                                                             int* perm_out, int* outrow_out,
                                                              int* npos, int* nneg, int* npiv2,
                                                              int* err) {
   const int slot = blockIdx.x;
@@ -72,7 +77,7 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
   double2* C = CH + (int64_t)slot * n * n;
   const int tid = threadIdx.x, nt = blockDim.x;
 
-  __shared__ int perm[kMaxN], pinv[kMaxN], blk[kMaxN], outrow[kMaxN];
+  __shared__ int perm[kMaxN], blk[kMaxN], outrow[kMaxN];
   __shared__ double lam[kMaxN];
   __shared__ double2 qv[kMaxN][2];
   __shared__ double red_v[32];
@@ -261,7 +266,6 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
     __syncthreads();
     k += kstep;
   }
-  for (int i = tid; i < n; i += nt) pinv[perm[i]] = i;
   if (tid == 0) {
     int np = 0, nn = 0;
     for (int r = 0; r < n; ++r)
@@ -279,12 +283,14 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
     if (s_bad) atomicExch(err, FLAPW_ERR_FACTOR);
   }
   __syncthreads();
-  // C^H[r][c] = sqrt|lam_r| sum_{j in block(r)} conj(Q[j][r]) (L^H P^T)[j][c],
-  // (L^H P^T)[j][c] = conj(L[pinv(c)][j]) with unit diagonal, zero above.
+  for (int i = tid; i < n; i += nt) {
+    perm_out[slot * n + i] = perm[i];
+    outrow_out[slot * n + i] = outrow[i];
+  }
+  // M[r][i] = sqrt|lam_r| sum_{j in block(r)} conj(Q[j][r]) (L^H)[j][i],
+  // (L^H)[j][i] = conj(L[i][j]) with unit diagonal and zero for i < j.
   for (int idx = tid; idx < n * n; idx += nt) {
-    const int r = idx / n, c = idx % n;
-    if (outrow[r] < 0) continue;
-    const int i = pinv[c];
+    const int r = idx / n, i = idx % n;
     const int b0 = (blk[r] == 0) ? r - 1 : r;  // first row of r's block
     const int bs = (blk[b0] == 2) ? 2 : 1;
     double2 acc = make_double2(0.0, 0.0);
@@ -294,14 +300,13 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
       if (i == j) lv = make_double2(1.0, 0.0);
       else if (i > b0 + bs - 1) lv = cconj(A[(int64_t)i * n + j]);
       else lv = make_double2(0.0, 0.0);
-      // Q[e][r - b0] for 2x2; 1 for 1x1
-      const double2 q = (bs == 2) ? qv[b0 + (r - b0)][e] : make_double2(1.0, 0.0);
+      const double2 q = (bs == 2) ? qv[r][e] : make_double2(1.0, 0.0);
       const double2 t = cmul(cconj(q), lv);
       acc.x += t.x;
       acc.y += t.y;
     }
-    const double s = sqrt(fabs(lam[r]));
-    C[(int64_t)outrow[r] * n + c] = make_double2(s * acc.x, s * acc.y);
+    const double sq = sqrt(fabs(lam[r]));
+    C[(int64_t)r * n + i] = make_double2(sq * acc.x, sq * acc.y);
   }
 }
 
@@ -320,9 +325,9 @@ __global__ void layout_kernel(const int* npos, const int* nneg, const int* atom_
   kpk[0] = kp_pad;
   kpk[1] = p;
   kpk[2] = q;
-  for (int k = 0; k < n_k; ++k) {
-    probs[2 * k].kp = p;
-    probs[2 * k].kn = q;
+  for (int k = 0; k < n_k; ++k) {  // problems [0, n_k) are the H problems
+    probs[k].kp = p;
+    probs[k].kn = q;
   }
   (void)k_total;
 }
@@ -330,9 +335,11 @@ __global__ void layout_kernel(const int* npos, const int* nneg, const int* atom_
 }  // namespace
 
 cudaError_t launch_tfactor(const double2* T, int n, int n_slots, double2* work, double2* CH,
-                           int* npos, int* nneg, int* npiv2, int* err, cudaStream_t st) {
+                           int* perm, int* outrow, int* npos, int* nneg, int* npiv2, int* err,
+                           cudaStream_t st) {
   if (n > kMaxN) return cudaErrorInvalidValue;
-  tfactor_kernel<<<n_slots, kTfThreads, 0, st>>>(T, n, work, CH, npos, nneg, npiv2, err);
+  tfactor_kernel<<<n_slots, kTfThreads, 0, st>>>(T, n, work, CH, perm, outrow, npos, nneg, npiv2,
+                                                 err);
   return cudaGetLastError();
 }
 

@@ -190,3 +190,82 @@ def test_hs_config2_sampled_columns(precision, tol):
     eh = np.linalg.norm(Hg - Ho) / np.linalg.norm(Ho)
     es = np.linalg.norm(Sg - So) / np.linalg.norm(So)
     assert eh <= tol and es <= tol, (eh, es)
+
+
+# --------------------------------------------- options: autotune, graph, host buffers
+
+def test_autotune_keeps_results_and_picks_an_order():
+    p = inputs.config1()
+    opt = fl.default_options(precision=fl.PREC_EMU)
+    opt.autotune = 1
+    h = fl.from_problem(p, opt)
+    _, A, B = run_ab(p, h)
+    ng = h.num_g(0)
+    H, S = alloc_out(ng, 0), alloc_out(ng, 0)
+    h.build_HS(p.T, p.atom_slot, p.U, A, B, [H], [S])
+    h.sync()
+    st = h.stats()
+    assert 0 <= st["tile_order"] <= 4
+    Ho, So = oracle_hs(p)
+    assert herm_relerr(lower_to_full(H, ng, 0), Ho) <= TOL_EMU
+    assert herm_relerr(lower_to_full(S, ng, 0), So) <= TOL_EMU
+
+
+@pytest.mark.parametrize("precision", [fl.PREC_FP64, fl.PREC_EMU])
+def test_graph_replay_matches(precision):
+    p = inputs.small(17, n_atoms=2, n_types=2, lmax=3, n_target=(210, 150))
+    opt = fl.default_options(precision=precision, use_graph=1)
+    h = fl.from_problem(p, opt)
+    _, A, B = run_ab(p, h)
+    Hs = [alloc_out(h.num_g(k), 0) for k in range(p.n_k)]
+    Ss = [alloc_out(h.num_g(k), 0) for k in range(p.n_k)]
+    for rep in range(3):
+        for X in Hs + Ss:
+            X.zero_()
+        h.build_HS(p.T, p.atom_slot, p.U, A, B, Hs, Ss)
+        h.sync()
+    assert h.stats()["graph_replays"] >= 2
+    tol = TOL_EMU if precision == fl.PREC_EMU else TOL_F64
+    for k in range(p.n_k):
+        Ho, So = oracle_hs(p, k)
+        ng = Ho.shape[0]
+        assert herm_relerr(lower_to_full(Hs[k], ng, 0), Ho) <= tol
+        assert herm_relerr(lower_to_full(Ss[k], ng, 0), So) <= tol
+
+
+def test_host_buffers_through_the_abi():
+    torch = torch_cuda()
+    p = inputs.config1()
+    h = fl.from_problem(p, fl.default_options(precision=fl.PREC_EMU))
+    n = h.ab_offset(p.n_k)
+    A = torch.zeros(n, dtype=torch.complex128).pin_memory()
+    B = torch.zeros(n, dtype=torch.complex128).pin_memory()
+    h.build_AB(p.radial, A, B)
+    ng = h.num_g(0)
+    H = np.zeros(ng * ng, dtype=np.complex128)     # pageable host memory
+    S = torch.zeros(ng * ng, dtype=torch.complex128).pin_memory()
+    h.build_HS(p.T, p.atom_slot, p.U, A, B, [H], [S])
+    h.sync()
+    Ao, _ = oracle.build_ab(p, 0, h.gvectors(0))
+    assert np.abs(A.numpy().reshape(p.n_atoms, p.n_L, ng) - Ao).max() <= 1e-13 * np.abs(Ao).max()
+    Ho, So = oracle_hs(p)
+    assert herm_relerr(lower_to_full(H, ng, 0), Ho) <= TOL_EMU
+    assert herm_relerr(lower_to_full(S, ng, 0), So) <= TOL_EMU
+
+
+def test_bad_calls_return_codes_not_faults():
+    p = inputs.config1()
+    h = fl.from_problem(p)
+    with pytest.raises(fl.FlapwError) as e:
+        h.build_HS(p.T, [0, 7], p.U, None, None, [None], [None])
+    assert e.value.code == -1
+    opt = fl.default_options(operands=fl.OPERANDS_FACTORED)
+    h2 = fl.from_problem(p, opt)
+    ng = h2.num_g(0)
+    with pytest.raises(fl.FlapwError) as e:
+        h2.build_HS(p.T, p.atom_slot, p.U, None, None, [alloc_out(ng, 0)], [alloc_out(ng, 0)])
+    assert e.value.code == -6          # factored operands need build_AB's radial data first
+    eng = fl.engine_create()
+    with pytest.raises(fl.FlapwError) as e:
+        eng.num_g(0)
+    assert e.value.code == -6
