@@ -63,14 +63,17 @@ typedef struct flapw_ctx* flapw_handle;
 
 typedef struct flapw_options {
   int precision; /* FLAPW_PREC_EMU (default) or FLAPW_PREC_FP64 */
-  int n_slices;  /* emulation: 7-bit slices per operand entry, 4..9 (0 = default 7) */
+  int n_slices;  /* emulation: 7-bit slices per operand entry, 4..8 (0 = default 7) */
   int layout;    /* FLAPW_LAYOUT_LOWER_FULL (default) or FLAPW_LAYOUT_LOWER_PACKED */
   int operands;  /* FLAPW_OPERANDS_FROM_AB (default) or FLAPW_OPERANDS_FACTORED */
   int use_graph; /* 1: capture build_HS into a CUDA graph and replay it while the
                     arguments repeat (default 0) */
   int autotune;  /* 1: time the contraction's tile-order variants once per shape and
                     keep the fastest (default 0: fixed choice) */
-  int reserved[10];
+  int tile_order; /* 0: library default; k+1 forces tile order k of the emulated
+                     contraction (0 row-major, 1 column-major, 2/3/4 bands of
+                     8/4/16 row blocks), ignored when autotune is on */
+  int reserved[9];
 } flapw_options;
 
 typedef struct flapw_stats {

@@ -40,7 +40,7 @@ class FlapwError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_slices", ctypes.c_int), ("layout", ctypes.c_int),
                 ("operands", ctypes.c_int), ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("reserved", ctypes.c_int * 10)]
+                ("tile_order", ctypes.c_int), ("reserved", ctypes.c_int * 9)]
 
 
 class Stats(ctypes.Structure):

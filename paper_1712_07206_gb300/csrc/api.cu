@@ -17,6 +17,7 @@ using namespace flapw;
 namespace {
 
 std::string g_last_error;  // errors of calls without a handle
+constexpr int kNumTileOrders = 5;  // emulated tile orders, see make_tiles
 
 // Device buffer that grows on demand.
 struct DevBuf {
@@ -119,7 +120,7 @@ struct flapw_ctx {
   PinBuf pin_in, pin_probs;
   int64_t k_alloc = 0, rows = 0;
   int n_emu_tiles = 0, n_f64_tiles = 0, split_emu = 0, split_f64 = 0, tiles_order = -1;
-  int tile_order = 2;            // emulated tile order in use (see make_tiles)
+  int tile_order = 3;            // emulated tile order in use (see make_tiles)
   int64_t tuned_key = -1;        // shape the autotuner last ran on
   int64_t tiles_rows_key = -1;
   CUtensorMap tmap{};
@@ -179,6 +180,8 @@ int check_options(flapw_ctx* h, const flapw_options& o) {
     return fail(h, FLAPW_ERR_ARG, "options.layout is not a FLAPW_LAYOUT_* value");
   if (o.operands != FLAPW_OPERANDS_FROM_AB && o.operands != FLAPW_OPERANDS_FACTORED)
     return fail(h, FLAPW_ERR_ARG, "options.operands is not a FLAPW_OPERANDS_* value");
+  if (o.tile_order < 0 || o.tile_order > kNumTileOrders)
+    return fail(h, FLAPW_ERR_ARG, "options.tile_order must be in 0..5");
   return FLAPW_OK;
 }
 
@@ -208,7 +211,6 @@ int upload(flapw_ctx* h, DevBuf& d, const std::vector<T>& v) {
 //   order 0: row blocks outer, column blocks inner;  1: column blocks outer;
 //   order 2/3/4: grouped raster -- bands of 8/4/16 row blocks, and within a
 //   band column by column, so the concurrent tiles touch a compact set of rows.
-constexpr int kNumTileOrders = 5;
 void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order,
                 std::vector<EmuTile>* emu, std::vector<F64Tile>* f64) {
   for (int p = p0; p < p1; ++p) {
@@ -403,6 +405,7 @@ int flapw_engine_create(const flapw_options* opt, flapw_handle* out) {
   flapw_default_options(&h->opt);
   if (opt) h->opt = *opt;
   if (check_options(nullptr, h->opt)) return FLAPW_ERR_ARG;
+  if (h->opt.tile_order > 0 && !h->opt.autotune) h->tile_order = h->opt.tile_order - 1;
   h->engine_only = true;
   if (int rc = device_setup(h.get())) {
     g_last_error = h->err;
@@ -428,6 +431,7 @@ int flapw_hs_create(const double lattice[9], int n_atoms, const double* pos_frac
   flapw_default_options(&h->opt);
   if (opt) h->opt = *opt;
   if (check_options(nullptr, h->opt)) return FLAPW_ERR_ARG;
+  if (h->opt.tile_order > 0 && !h->opt.autotune) h->tile_order = h->opt.tile_order - 1;
   std::memcpy(h->lat, lattice, sizeof(h->lat));
   double det;
   reciprocal(h->lat, h->rec, &det);
@@ -515,6 +519,7 @@ int flapw_set_options(flapw_handle h, const flapw_options* opt) {
   if (!h || !opt) return fail(h, FLAPW_ERR_ARG, "NULL argument");
   if (int rc = check_options(h, *opt)) return rc;
   h->opt = *opt;
+  if (opt->tile_order > 0 && !opt->autotune) h->tile_order = opt->tile_order - 1;
   return FLAPW_OK;
 }
 
