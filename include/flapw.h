@@ -178,6 +178,29 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
 int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const int* sigma,
                void* H, int64_t ldh, void* stream);
 
+/* The contraction step alone (as flapw_herk, emulated precision) for callers
+ * that must not allocate device memory: code that runs under a fixed device
+ * memory budget or inside a framework whose caching allocator owns the GPU,
+ * where a cudaMalloc from a library can fail, fragment the pool or stall the
+ * device.  This entry point allocates nothing: its workspaces live in one
+ * static device array of 64 MiB that every GPU loading the library holds
+ * until the process exits.  The paper has no counterpart to this call.
+ *   Z: device, complex128, column-major K x N (element (k, g) at g*ldz + k).
+ *   sigma[K] (host): +1/-1 per row, or NULL for all +1.
+ *   H: device, complex128, lower triangle in `layout` (ld = ldh for the full
+ *      layout, ldh >= N).  n_slices 4..8 (0 = 7).  stream: the caller's stream.
+ * Size limit: about 44 bytes per N x K entry (7 slices) plus small tables
+ * must fit in the 64 MiB array, e.g. N = 1024 with K = 1400; larger problems
+ * return FLAPW_ERR_UNSUPPORTED before any work is enqueued.
+ * The first call on each device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Calls share the array and it keeps the last
+ * call's contents; calls whose work overlaps on the GPU race.  Errors are
+ * reported by the return code only (FLAPW_ERR_ARG, FLAPW_ERR_UNSUPPORTED,
+ * FLAPW_ERR_CUDA); a bounded device wait that runs out is not reported. */
+int flapw_herk_noalloc(const void* Z, int64_t ldz, int K, int N, const int* sigma, void* H,
+                       int64_t ldh, int layout, int n_slices, void* stream);
+
 /* Waits for the handle's enqueued work; reports device-side errors. */
 int flapw_sync(flapw_handle h);
 

@@ -17,7 +17,8 @@ import threading
 import numpy as np
 
 __all__ = ["FlapwError", "Options", "Stats", "Handle", "load", "library_path", "build",
-           "default_options", "enumerate_g", "hs_create", "engine_create", "declared_symbols",
+           "default_options", "enumerate_g", "hs_create", "engine_create", "herk_noalloc",
+           "declared_symbols",
            "PREC_FP64", "PREC_EMU", "LAYOUT_LOWER_FULL", "LAYOUT_LOWER_PACKED",
            "OPERANDS_FROM_AB", "OPERANDS_FACTORED"]
 
@@ -99,6 +100,8 @@ def load():
                                        P(c_void_p), c_void_p]),
             "flapw_herk": (c_int, [h, c_void_p, ctypes.c_int64, c_int, c_int, ip, c_void_p,
                                    ctypes.c_int64, c_void_p]),
+            "flapw_herk_noalloc": (c_int, [c_void_p, ctypes.c_int64, c_int, c_int, ip, c_void_p,
+                                           ctypes.c_int64, c_int, c_int, c_void_p]),
             "flapw_sync": (c_int, [h]),
             "flapw_get_stats": (c_int, [h, P(Stats)]),
             "flapw_get_factor": (c_int, [h, c_int, dp, ip, ip]),
@@ -270,6 +273,15 @@ def hs_create(lattice, pos_frac, atom_type, mt_radius, lmax, k_frac, kmax,
     _check(rc)
     return Handle(raw, n_k=int(kf.shape[0]), n_atoms=int(pos.shape[0]),
                   n_L=(int(lmax) + 1) ** 2, n_types=int(rad.shape[0]), lmax=int(lmax))
+
+
+def herk_noalloc(Z, ldz, K, N, sigma, H, ldh, layout=LAYOUT_LOWER_FULL, n_slices=0, stream=None):
+    """flapw_herk_noalloc: the emulated contraction with no device allocation
+    (workspaces in the library's static 64 MiB device array)."""
+    sig = None if sigma is None else _i32(sigma)
+    _check(load().flapw_herk_noalloc(_addr(Z), int(ldz), int(K), int(N),
+                                     None if sig is None else _ip(sig), _addr(H), int(ldh),
+                                     int(layout), int(n_slices), _stream(stream)))
 
 
 def engine_create(options: Options | None = None) -> Handle:
