@@ -269,3 +269,47 @@ def test_bad_calls_return_codes_not_faults():
     with pytest.raises(fl.FlapwError) as e:
         eng.num_g(0)
     assert e.value.code == -6
+
+
+# ------------------------------------------- full-size workloads, sampled columns
+
+def _sampled_check(p, Hs, Ss, h, layout, ks, tol, n_cols=6, seed=0):
+    rng = np.random.default_rng(seed)
+    for k in ks:
+        n3 = h.gvectors(k)
+        ng = len(n3)
+        cols = np.unique(np.concatenate([[0, ng - 1], rng.integers(0, ng, size=n_cols - 2)]))
+        Ho, So = oracle.hs_columns(p, k, n3, cols)
+        Hg = columns_from_lower(Hs[k], ng, layout, cols)
+        Sg = columns_from_lower(Ss[k], ng, layout, cols)
+        eh = np.linalg.norm(Hg - Ho) / np.linalg.norm(Ho)
+        es = np.linalg.norm(Sg - So) / np.linalg.norm(So)
+        assert eh <= tol and es <= tol, (k, eh, es)
+
+
+@pytest.mark.parametrize("precision,tol", [(fl.PREC_EMU, TOL_EMU), (fl.PREC_FP64, TOL_F64)])
+def test_config3_sampled(precision, tol):
+    p = inputs.config3()
+    h, Hs, Ss, _ = run_hs(p, precision, operands=fl.OPERANDS_FACTORED)
+    _sampled_check(p, Hs, Ss, h, fl.LAYOUT_LOWER_FULL, [0], tol)
+
+
+@pytest.mark.parametrize("precision,tol", [(fl.PREC_EMU, TOL_EMU), (fl.PREC_FP64, TOL_F64)])
+def test_config4_batched_32k_sampled(precision, tol):
+    p = inputs.config4()
+    h, Hs, Ss, _ = run_hs(p, precision, operands=fl.OPERANDS_FACTORED, use_graph=1)
+    ngs = [h.num_g(k) for k in range(p.n_k)]
+    assert min(ngs) >= 2500 and max(ngs) <= 6000 and len(set(ngs)) > 20
+    _sampled_check(p, Hs, Ss, h, fl.LAYOUT_LOWER_FULL, [0, 13, 31], tol, n_cols=4)
+
+
+def test_config5_packed_sampled():
+    torch = torch_cuda()
+    p = inputs.config5()
+    h, Hs, Ss, _ = run_hs(p, fl.PREC_EMU, layout=fl.LAYOUT_LOWER_PACKED,
+                          operands=fl.OPERANDS_FACTORED)
+    ng = h.num_g(0)
+    assert Hs[0].numel() == ng * (ng + 1) // 2
+    _sampled_check(p, Hs, Ss, h, fl.LAYOUT_LOWER_PACKED, [0], TOL_EMU, n_cols=4)
+    del Hs, Ss
+    torch.cuda.empty_cache()
