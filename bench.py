@@ -119,7 +119,8 @@ def run_ours(args):
     p = workload(args.config)
     operands = fl.OPERANDS_FACTORED if args.operands == "factored" else fl.OPERANDS_FROM_AB
     layout = fl.LAYOUT_LOWER_PACKED if p.layout == "packed" else fl.LAYOUT_LOWER_FULL
-    opt = fl.default_options(precision=fl.PREC_EMU, layout=layout, operands=operands, n_slices=args.slices)
+    opt = fl.default_options(precision=fl.PREC_EMU, layout=layout, operands=operands, n_slices=args.slices,
+                             tile_order=args.tile_order)
     h = fl.from_problem(p, opt)
     ngs = [h.num_g(k) for k in range(p.n_k)]
     flops = hs_flops(p, ngs)
@@ -178,6 +179,8 @@ def run_ours(args):
     st = h.stats()
     k_ms = float(np.mean(kms))
     bf16_burst, bf16_sus, hbm, src = peaks()
+    # a contraction of a second or more runs under the power cap: sustained peak
+    peak, peak_kind = (bf16_sus, "sustained") if k_ms >= 1000.0 else (bf16_burst, "burst")
     achieved = st["flops_tensor"] / (k_ms * 1e-3) / 1e12
     n_pairs = args.slices * (args.slices + 1) // 2
     alg_tensor = n_pairs * 4.0 * st["k_total"] * float(np.sum(np.asarray(ngs, float) ** 2)) * 2
@@ -234,11 +237,11 @@ def run_ours(args):
             "ms_per_step": round(f64_ms, 3), "steps": args.fp64_steps},
         "speedup_emu_vs_fp64": None if f64_ms is None else round(f64_ms / ms, 2),
         "stages_ms": stage,
-        "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": bf16_burst,
-                     "unit": "TFLOP/s", "frac": round(achieved / bf16_burst, 4), "traffic": args.traffic,
-                     "kernel": "herk_emu_kernel", "kernel_ms": round(k_ms, 4),
+        "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": args.traffic,
+                     "kernel": "herk_emu_kernel (S and H launches)", "kernel_ms": round(k_ms, 4),
                      "achieved_algorithmic": round(achieved_alg, 2),
-                     "peak_source": f"{src} bf16 burst x 1.0 (fp16 = bf16 nominal rate)"},
+                     "peak_source": f"{src} bf16 {peak_kind} x 1.0 (fp16 = bf16 nominal rate)"},
         "e2e": e2e,
         "gpu_launches": 8 * args.steps,
         "clocks": clk,
@@ -328,6 +331,8 @@ def main():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--operands", choices=["factored", "from_ab"], default="factored")
     ap.add_argument("--slices", type=int, default=7)
+    ap.add_argument("--tile-order", type=int, default=0,
+                    help="0: library default; k+1 forces emulated tile order k")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
