@@ -119,6 +119,7 @@ struct flapw_ctx {
       d_emu_tiles, d_f64_tiles, d_combo, d_kmap, d_stageA, d_stageB, d_stageOut;
   PinBuf pin_in, pin_probs;
   int64_t k_alloc = 0, rows = 0;
+  int64_t k_terms = 0;           // most products summed into one output element
   int n_emu_tiles = 0, n_f64_tiles = 0, split_emu = 0, split_f64 = 0, tiles_order = -1;
   int tile_order = 3;            // emulated tile order in use (see make_tiles)
   int64_t tuned_key = -1;        // shape the autotuner last ran on
@@ -273,7 +274,8 @@ int enqueue_contraction(flapw_ctx* h, const Half& hf, int max_grid, cudaStream_t
     CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
     const int grid = std::max(1, std::min(hf.emu_nt, max_grid));
     CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf.emu_t0,
-                          hf.emu_nt, h->d_rexp.as<int>(), s, h->d_cnt.as<int>() + 2, grid, st),
+                          hf.emu_nt, h->d_rexp.as<int>(), s, fixed_frac_bits(h->k_terms),
+                          h->d_cnt.as<int>() + 2, grid, st),
        "emulated contraction launch");
   } else {
     CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
@@ -351,7 +353,8 @@ int autotune_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, in
       for (const Half* hf : {&b, &a}) {
         const int grid = std::max(1, std::min(hf->emu_nt, h->num_sms));
         CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf->emu_t0,
-                              hf->emu_nt, h->d_rexp.as<int>(), s, h->d_cnt.as<int>() + 2, grid, st),
+                              hf->emu_nt, h->d_rexp.as<int>(), s, fixed_frac_bits(h->k_terms),
+                              h->d_cnt.as<int>() + 2, grid, st),
            "emulated contraction launch");
       }
       CK(h, cudaEventRecord(h->ev[15], st), "cudaEventRecord");
@@ -700,6 +703,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   }
   h->rows = 2 * h->g_total;
   h->k_alloc = round_up(K, kChunk) + kChunk;
+  h->k_terms = K;
   CK(h, h->d_T.ensure(t_bytes), "workspace");
   CK(h, h->d_work.ensure(t_bytes), "workspace");
   CK(h, h->d_CH.ensure(t_bytes), "workspace");
@@ -909,6 +913,7 @@ int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const i
                                h->opt.layout == FLAPW_LAYOUT_LOWER_FULL ? ldh : N, dH}};
   h->rows = N;
   h->k_alloc = k_alloc;
+  h->k_terms = K;
   if (upload(h, h->d_kmap, kmap) || upload(h, h->d_probs, probs)) return FLAPW_ERR_CUDA;
   std::vector<int> rp(N, 0);
   if (upload(h, h->d_rowprob, rp)) return FLAPW_ERR_CUDA;

@@ -17,8 +17,8 @@ constexpr int kMaxLmax = 12;
 constexpr int kMaxNL = (kMaxLmax + 1) * (kMaxLmax + 1);
 constexpr int kChunk = 64;        // columns of K per pipeline step (one 128-byte fp16 row)
 constexpr int kSliceBits = 7;     // magnitude bits per emulation slice
-constexpr int kFixedFrac = 45;    // fractional bits of the 64-bit fixed-point accumulators
-constexpr int kUnitChunks = 16;   // K chunks per exact FP32 accumulation (16*64 = 1024 terms)
+constexpr int kUnitChunks = 64;   // K chunks per unit: the longest exact FP32 accumulation
+                                  // (4096 terms, digit products <= 2^12)
 
 // One lower-triangle contraction problem: H or S of one k-point.
 struct Prob {
@@ -146,9 +146,13 @@ cudaError_t launch_slicer(const double2* Z, int64_t k_alloc, const Prob* probs,
 // Contractions.
 cudaError_t launch_herk_f64(const double2* Z, int64_t k_alloc, const Prob* probs,
                             const F64Tile* tiles, int n_tiles, cudaStream_t st);
+// Fractional bits of the contraction's 64-bit fixed-point accumulators for
+// sums of at most k_terms complex products (each < 2 in magnitude after the
+// per-row scaling): 61 - ceil(log2 k_terms), clamped to [40, 50].
+int fixed_frac_bits(int64_t k_terms);
 cudaError_t launch_herk_emu(const CUtensorMap& tmap, const Prob* probs, const EmuTile* tiles,
-                            int n_tiles, const int* rexp, int n_slices, int* err, int grid,
-                            cudaStream_t st);
+                            int n_tiles, const int* rexp, int n_slices, int frac, int* err,
+                            int grid, cudaStream_t st);
 size_t herk_emu_smem_bytes();
 
 // Tensor map for the slice array [slice][plane][row][k] (fp16).

@@ -6,12 +6,16 @@
 // Then X_{G'G} = 2^{e_G' + e_G} sum_{t} 128^{-t} sum_{i+j=t} D_i(G')^H D_j(G),
 // and the truncated sum keeps the s(s+1)/2 slice pairs with i + j <= s + 1
 // (Ozaki-style split-precision product).  Each slice product is computed
-// EXACTLY: digit products are <= 2^14 and a TMEM FP32 accumulator sums at most
-// 1024 of them between drains (|sum| <= 2^24).  Every drain converts the FP32
+// EXACTLY: a TMEM FP32 accumulator is drained before its sum can pass 2^24 --
+// after 1024 terms for the pair (0,0) (digit products <= 2^14), 2048 for the
+// pairs (0,j), (i,0) (<= 2^13) and 4096 for the rest (<= 2^12).  Every drain converts the FP32
 // partial sums to integers and adds them, shifted by the level of the slice
-// pair, into 64-bit fixed-point accumulators held in registers (45 fractional
-// bits), so the cross-slice, cross-atom accumulation is exact integer
-// arithmetic; FP64 is used once per output element at the end.
+// pair, into 64-bit fixed-point accumulators held in registers (F fractional
+// bits, F = 61 - ceil(log2 K): with max(|Re|,|Im|) < 1 per entry a sum of K
+// products stays below 2K, which then fits in 62 bits), so the
+// cross-slice, cross-atom accumulation is integer arithmetic rounded only
+// where a level's weight falls below 2^-F; FP64 is used once per output
+// element at the end.
 //
 // CTA tile: 128 rows (G') x 64 columns (G) of complex output.  Per 64-wide K
 // chunk the producer loads, with TMA and 128-byte swizzle:
@@ -167,6 +171,12 @@ struct Units {
   }
 };
 
+// Chunks (64 terms each) a TMEM accumulator may sum exactly for slice pair
+// (i, j): the leading digit is up to 128 in magnitude, later digits up to 64.
+__device__ __forceinline__ int pair_span(int i, int j) {
+  return (i == 0 && j == 0) ? kUnitChunks / 4 : (i == 0 || j == 0) ? kUnitChunks / 2 : kUnitChunks;
+}
+
 __device__ __forceinline__ Units units_of(const Prob& P) {
   Units u;
   u.kpc = (P.kp + kChunk - 1) / kChunk;
@@ -177,7 +187,7 @@ __device__ __forceinline__ Units units_of(const Prob& P) {
 __global__ void __launch_bounds__(kThreads, 1)
     herk_emu_kernel(const __grid_constant__ CUtensorMap tmap, const Prob* __restrict__ probs,
                     const EmuTile* __restrict__ tiles, int n_tiles, const int* __restrict__ rexp,
-                    int n_slices, int* __restrict__ err) {
+                    int n_slices, int frac, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
@@ -278,42 +288,46 @@ __global__ void __launch_bounds__(kThreads, 1)
         const Prob P = probs[T.prob];
         const Units U = units_of(P);
         const int nu = U.count();
-        const int npairs = n_slices * (n_slices + 1) / 2;
         for (int u = 0; u < nu && ok; ++u) {
           int c0, c1, neg;
           U.get(u, c0, c1, neg);
-          for (int p = 0; p < npairs && ok; ++p) {
-            const int buf = acc_it & 1;
-            const uint32_t use = acc_it >> 1;
-            if (!mbar_wait(tempty_bar(buf), (use & 1u) ^ 1u, abort_flag)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t d1 = tmem_base + (uint32_t)buf * 256u;
-            const uint32_t d2 = d1 + 128u;
-            for (int c = c0; c < c1; ++c) {
-              const int stage = it % kStages;
-              if (!mbar_wait(full_bar(stage), (it / kStages) & 1u, abort_flag)) {
+          for (int pt = 0; pt < n_slices && ok; ++pt)
+          for (int pi = 0; pi <= pt && ok; ++pi) {
+            const int span = pair_span(pi, pt - pi);
+            for (int s0 = c0; s0 < c1 && ok; s0 += span) {
+              const int s1 = min(c1, s0 + span);
+              const int buf = acc_it & 1;
+              const uint32_t use = acc_it >> 1;
+              if (!mbar_wait(tempty_bar(buf), (use & 1u) ^ 1u, abort_flag)) {
                 ok = false;
                 break;
               }
               tc_fence_after();
-              const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
-              const uint64_t dar = sdesc(sbase), dai = sdesc(sbase + kTileA),
-                             db = sdesc(sbase + 2 * kTileA);
+              const uint32_t d1 = tmem_base + (uint32_t)buf * 256u;
+              const uint32_t d2 = d1 + 128u;
+              for (int c = s0; c < s1; ++c) {
+                const int stage = it % kStages;
+                if (!mbar_wait(full_bar(stage), (it / kStages) & 1u, abort_flag)) {
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+                const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
+                const uint64_t dar = sdesc(sbase), dai = sdesc(sbase + kTileA),
+                               db = sdesc(sbase + 2 * kTileA);
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk) {
-                const uint32_t acc = (c > c0 || kk > 0) ? 1u : 0u;
-                umma(d1, dar + 2 * kk, db + 2 * kk, acc);
-                umma(d2, dai + 2 * kk, db + 2 * kk, acc);
+                for (int kk = 0; kk < 4; ++kk) {
+                  const uint32_t acc = (c > s0 || kk > 0) ? 1u : 0u;
+                  umma(d1, dar + 2 * kk, db + 2 * kk, acc);
+                  umma(d2, dai + 2 * kk, db + 2 * kk, acc);
+                }
+                umma_commit(empty_bar(stage));
+                ++it;
               }
-              umma_commit(empty_bar(stage));
-              ++it;
+              if (!ok) break;
+              umma_commit(tfull_bar(buf));
+              ++acc_it;
             }
-            if (!ok) break;
-            umma_commit(tfull_bar(buf));
-            ++acc_it;
           }
         }
       }
@@ -344,8 +358,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         int c0, c1, neg;
         U.get(u, c0, c1, neg);
         for (int pt = 0; pt < n_slices && ok; ++pt)
-        for (int pi = 0; pi <= pt && ok; ++pi) {
-          const int sh = kFixedFrac - kSliceBits * (pt + 2);
+        for (int pi = 0; pi <= pt && ok; ++pi)
+        for (int s0 = c0; s0 < c1 && ok; s0 += pair_span(pi, pt - pi)) {
+          const int sh = frac - kSliceBits * (pt + 2);
           const int buf = acc_it & 1;
           const uint32_t use = acc_it >> 1;
           if (!mbar_wait(tfull_bar(buf), use & 1u, abort_flag)) {
@@ -391,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int n = 0; n < 64; ++n) {
           const int64_t gc = (int64_t)T.jb * 64 + n;
           if (gc < ng && gc <= gr) {
-            const int ex = er + rexp[P.row_base + gc] - kFixedFrac;
+            const int ex = er + rexp[P.row_base + gc] - frac;
             const double scale = __longlong_as_double((long long)(ex + 1023) << 52);
             const double val = (double)acc[n] * scale;
             const int64_t o = (P.layout == FLAPW_LAYOUT_LOWER_PACKED)
@@ -420,11 +435,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 size_t herk_emu_smem_bytes() { return kStages * kStageBytes + 1024 + 256; }
 
+int fixed_frac_bits(int64_t k_terms) {
+  int lg = 0;
+  while (lg < 62 && ((int64_t)1 << lg) < k_terms) ++lg;
+  const int f = 61 - lg;  // |sum| < 2K 2^F <= 2^62
+  return f < 40 ? 40 : (f > 50 ? 50 : f);  // <= 50: one (0,0) drain, < 2^25 2^(F-14), fits too
+}
+
 cudaError_t launch_herk_emu(const CUtensorMap& tmap, const Prob* probs, const EmuTile* tiles,
-                            int n_tiles, const int* rexp, int n_slices, int* err, int grid,
-                            cudaStream_t st) {
+                            int n_tiles, const int* rexp, int n_slices, int frac, int* err,
+                            int grid, cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
-  if (n_slices < 1 || n_slices > kMaxS) return cudaErrorInvalidValue;
+  if (n_slices < 1 || n_slices > kMaxS || frac < 40 || frac > 50) return cudaErrorInvalidValue;
   static bool attr = false;
   const size_t smem = herk_emu_smem_bytes();
   if (!attr) {
@@ -433,7 +455,8 @@ cudaError_t launch_herk_emu(const CUtensorMap& tmap, const Prob* probs, const Em
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  herk_emu_kernel<<<grid, kThreads, smem, st>>>(tmap, probs, tiles, n_tiles, rexp, n_slices, err);
+  herk_emu_kernel<<<grid, kThreads, smem, st>>>(tmap, probs, tiles, n_tiles, rexp, n_slices, frac,
+                                                err);
   return cudaGetLastError();
 }
 

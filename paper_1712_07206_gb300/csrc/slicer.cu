@@ -5,8 +5,9 @@
 // rounded to the fixed-point integer X = round(x 2^{7s - e}) (|X| <= 2^{7s})
 // and written as s balanced base-128 digits
 //     X = sum_{i=0}^{s-1} d_i 128^{s-1-i},  |d_0| <= 128,  |d_i| <= 64 (i > 0),
-// each carried exactly by an fp16 value.  Products of two digits are at most
-// 2^14, so 1024 of them sum exactly in FP32.  Everything here is integer bit
+// each carried exactly by an fp16 value.  A product of two leading digits is
+// at most 2^14, of a leading and a later digit 2^13, of two later digits
+// 2^12, so 1024, 2048 and 4096 of them respectively sum exactly in FP32.  Everything here is integer bit
 // manipulation of the IEEE-754 encoding: FP64 arithmetic is scarce on this
 // part.  The rounding of X is the only approximation (|x - X 2^{e-7s}| <=
 // 2^{e-7s-1}).

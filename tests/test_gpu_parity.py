@@ -152,12 +152,12 @@ def test_herk_step_vs_numpy(precision, K, N):
     assert herm_relerr(lower_to_full(H, N, 0), R) <= tol
 
 
-@pytest.mark.parametrize("K", [64, 1023, 1024, 1025, 3000])
+@pytest.mark.parametrize("K", [64, 1024, 1025, 2049, 4096, 4097, 9000])
 def test_herk_integer_data_bit_exact(K):
-    """Entries m/128 with |m| <= 127: one slice carries them exactly, so the
-    emulated product must equal the exact (integer-valued) sum bit for bit,
-    with every partial sum at its largest (exactness of the FP32 tensor-core
-    accumulation over 1024 terms and of the integer drain)."""
+    """Entries m/128 with |m| <= 127: the leading slice carries them exactly,
+    so the emulated product must equal the exact (integer-valued) sum bit for
+    bit, with leading digits near their largest (exactness of the FP32
+    tensor-core accumulation over 1024 terms of up to 2^14 and of the drain)."""
     torch = torch_cuda()
     N = 192
     rng = np.random.default_rng(K)
