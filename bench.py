@@ -38,6 +38,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float) -> float:
+    """Largest value over the ranks of the default process group (x itself
+    when there is none); NCCL reduces on the GPU, gloo on the CPU."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    if dist.get_backend() == "nccl":
+        dev = torch.device("cuda", torch.cuda.current_device())
+    else:
+        dev = torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -168,12 +184,7 @@ def run_ours(args):
     step_ms, _ = timed(args.steps)
     t_wall = time.time() - t_wall
     clk = clocks.stop()
-    ms = float(np.mean(step_ms))
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(step_ms)))
     # contraction kernel duration, from the library's own events on the launching stream
     _, kms = timed(3, collect_kernel=True)
     st = h.stats()
@@ -356,7 +367,7 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cols", type=int, default=48)
-    ap.add_argument("--ref-cols", type=int, default=8)
+    ap.add_argument("--ref-cols", type=int, default=32)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per contraction launch from an ncu capture")
     args = ap.parse_args()
