@@ -4,35 +4,39 @@
 // The operand is given as s integer slices per entry (see slicer.cu):
 //     Z = 2^{e_row} sum_i d_i 128^{-(i+1)}   (Re and Im planes separately).
 // Then X_{G'G} = 2^{e_G' + e_G} sum_{t} 128^{-t} sum_{i+j=t} D_i(G')^H D_j(G),
-// and the truncated sum keeps the s(s+1)/2 slice pairs with i + j <= s + 1
+// and the truncated sum keeps the s(s+1)/2 slice pairs with i + j <= s - 1
 // (Ozaki-style split-precision product).  Each slice product is computed
 // EXACTLY: a TMEM FP32 accumulator is drained before its sum can pass 2^24 --
 // after 1024 terms for the pair (0,0) (digit products <= 2^14), 2048 for the
-// pairs (0,j), (i,0) (<= 2^13) and 4096 for the rest (<= 2^12).  Every drain converts the FP32
-// partial sums to integers and adds them, shifted by the level of the slice
-// pair, into 64-bit fixed-point accumulators held in registers (F fractional
-// bits, F = 61 - ceil(log2 K): with max(|Re|,|Im|) < 1 per entry a sum of K
-// products stays below 2K, which then fits in 62 bits), so the
-// cross-slice, cross-atom accumulation is integer arithmetic rounded only
-// where a level's weight falls below 2^-F; FP64 is used once per output
+// pairs (0,j), (i,0) (<= 2^13) and at most kPassChunks*64 for the rest.  Every
+// drain converts the FP32 partial sums to integers and adds them, shifted by
+// the level of the slice pair, into 64-bit fixed-point accumulators held in
+// registers (F fractional bits, F = 61 - ceil(log2 K): with max(|Re|,|Im|) < 1
+// per entry a sum of K products stays below 2K, which then fits in 62 bits),
+// so the cross-slice, cross-atom accumulation is integer arithmetic rounded
+// only where a level's weight falls below 2^-F; FP64 is used once per output
 // element at the end.
 //
-// CTA tile: 128 rows (G') x 64 columns (G) of complex output.  Per 64-wide K
-// chunk the producer loads, with TMA and 128-byte swizzle:
-//     A_R = Re slice i, rows G' (128x64 fp16)    A_I = Im slice i, rows G'
-//     B   = [Re slice j, rows G (64x64); Im slice j, rows G (64x64)]
-// and the MMA warp issues two M=128, N=128, K=16 MMAs per 16 columns:
-//     acc1 = A_R B = [RR | RI],   acc2 = A_I B = [IR | II]
-// so  Re X = RR + II,  Im X = RI - IR  (assembled in the drain).  Rows with
-// sigma = -1 form their own K units, subtracted in the drain.
+// CTA tile: 128 rows (G') x 64 columns (G) of complex output.  Slice pairs
+// are taken in groups (i; j, j+1) sharing the row slice i: per 64-wide K chunk
+// the producer loads, with TMA and 128-byte swizzle, one plane of slice i for
+// the tile's rows (A: 128 x 64 fp16) and B = [Re_j; Im_j; Re_{j+1}; Im_{j+1}]
+// for the tile's columns (4 x 64 rows), and the MMA warp issues one
+// M=128, N=256, K=16 MMA per 16 columns.  Each K sub-span runs twice: an R pass
+// (A = Re_i) into accumulator acc_R = [RR_j | RI_j | RR_j+1 | RI_j+1] and an I
+// pass (A = Im_i) into acc_I = [IR_j | II_j | IR_j+1 | II_j+1]; the drains add
+//     Re += RR (R pass), Re += II (I pass), Im += RI (R pass), Im -= IR (I pass)
+// so the two 256-column accumulators also double-buffer each other: the drain
+// of one pass overlaps the MMAs of the next.  N=256 halves the shared-memory
+// operand reads per MMA flop of a 128-wide B (the N=128 form ran the tensor
+// pipe at ~64 %).  Rows with sigma = -1 form their own K units, subtracted.
 //
 // Warp roles: warp 0 TMA producer, warp 1 TMEM allocator + MMA issuer,
 // warps 2..9 drain/epilogue (warp w reads TMEM lanes 32*(w%4)..+31; warps
-// 2-5 assemble Re, 6-9 Im).  TMEM: two 256-column buffers (acc1 | acc2) so the
-// drain of one K unit overlaps the MMAs of the next.  Persistent CTAs walk
-// the lower-triangle tile list.  Every wait is bounded by a wall-clock limit;
-// on expiry the CTA records an error, lets its in-flight copies and MMAs
-// complete, frees TMEM and exits.
+// 2-5 own Re, 6-9 own Im).  Persistent CTAs walk the lower-triangle tile
+// list.  Every wait is bounded by a wall-clock limit; on expiry the CTA
+// records an error, lets its in-flight copies and MMAs complete, frees TMEM
+// and exits.
 #include <cstdint>
 
 #include "flapw_internal.h"
@@ -44,14 +48,17 @@ constexpr int kStages = 4;
 constexpr int kThreads = 320;
 constexpr uint32_t kHalfTile = 64 * 128;                 // 64 rows x 128 B
 constexpr uint32_t kTileA = 2 * kHalfTile;               // 128 rows
-constexpr uint32_t kStageBytes = 3 * kTileA;             // A_R, A_I, B
+constexpr uint32_t kStageBytes = 3 * kTileA;             // A (128 rows) + B (256 rows)
 constexpr uint32_t kTmemCols = 512;
 constexpr unsigned long long kWaitNs = 4000000000ull;    // 4 s
 constexpr int kMaxS = 8;
+constexpr int kPassChunks = 32;                          // longest K sub-span of a pass
 
-// instruction descriptor: D = F32, A = B = F16, K-major both, N = 128, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((128u >> 3) << 17) |
-                            ((128u >> 4) << 24);
+// instruction descriptors: D = F32, A = B = F16, K-major both, M = 128, N = 256 / 128
+constexpr uint32_t kIdesc256 = (1u << 4) | (0u << 7) | (0u << 10) | ((256u >> 3) << 17) |
+                               ((128u >> 4) << 24);
+constexpr uint32_t kIdesc128 = (1u << 4) | (0u << 7) | (0u << 10) | ((128u >> 3) << 17) |
+                               ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -119,11 +126,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accum) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile(
@@ -184,6 +192,64 @@ __device__ __forceinline__ Units units_of(const Prob& P) {
   return u;
 }
 
+// The drain steps of one tile, in the order every role walks them: for each
+// K unit (sign-homogeneous, <= kUnitChunks chunks), for each slice group
+// (i; j, j+1) with i + j + 1 <= s - 1, for each sub-span of the unit, an R
+// pass then an I pass.  A sub-span is as long as both pairs of the group may
+// accumulate exactly (and at most kPassChunks).
+struct Sched {
+  Units U;
+  int s, nu;
+  int u, c0, c1, neg;
+  int i, j, two, span;
+  int s0, s1, pass;
+
+  __device__ void set_group() {
+    two = (j + 1 <= s - 1 - i) ? 1 : 0;
+    span = pair_span(i, j);
+    if (two) span = min(span, pair_span(i, j + 1));
+    span = min(span, kPassChunks);
+    s0 = c0;
+    s1 = min(c1, s0 + span);
+  }
+  __device__ bool begin(const Units& units, int n_slices) {
+    U = units;
+    s = n_slices;
+    nu = U.count();
+    u = 0;
+    if (nu == 0) return false;
+    U.get(0, c0, c1, neg);
+    i = 0;
+    j = 0;
+    pass = 0;
+    set_group();
+    return true;
+  }
+  __device__ bool next() {
+    if (pass == 0) {
+      pass = 1;
+      return true;
+    }
+    pass = 0;
+    s0 += span;
+    if (s0 < c1) {
+      s1 = min(c1, s0 + span);
+      return true;
+    }
+    j += 2;
+    if (j > s - 1 - i) {
+      j = 0;
+      if (++i >= s) {
+        i = 0;
+        if (++u >= nu) return false;
+        U.get(u, c0, c1, neg);
+      }
+    }
+    set_group();
+    return true;
+  }
+};
+
 __global__ void __launch_bounds__(kThreads, 1)
     herk_emu_kernel(const __grid_constant__ CUtensorMap tmap, const Prob* __restrict__ probs,
                     const EmuTile* __restrict__ tiles, int n_tiles, const int* __restrict__ rexp,
@@ -237,35 +303,32 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
         const EmuTile T = tiles[tile];
         const Prob P = probs[T.prob];
-        const Units U = units_of(P);
-        const int nu = U.count();
         const int rowA = P.row_base + T.ib * 128, rowB = P.row_base + T.jb * 64;
-        for (int u = 0; u < nu && ok; ++u) {
-          int c0, c1, neg;
-          U.get(u, c0, c1, neg);
-          for (int pt = 0; pt < n_slices && ok; ++pt)
-            for (int si = 0; si <= pt && ok; ++si) {
-              const int sj = pt - si;
-              for (int c = c0; c < c1; ++c) {
-                const int stage = it % kStages;
-                const uint32_t round = it / kStages;
-                if (!mbar_wait(empty_bar(stage), (round & 1u) ^ 1u, abort_flag)) {
-                  ok = false;
-                  break;
-                }
-                const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
-                const uint32_t fb = full_bar(stage);
-                mbar_expect_tx(fb, kStageBytes);
-                const int kc = c * kChunk;
-                tma_load_4d(sbase, &tmap, fb, kc, rowA, 0, si);
-                tma_load_4d(sbase + kHalfTile, &tmap, fb, kc, rowA + 64, 0, si);
-                tma_load_4d(sbase + kTileA, &tmap, fb, kc, rowA, 1, si);
-                tma_load_4d(sbase + kTileA + kHalfTile, &tmap, fb, kc, rowA + 64, 1, si);
-                tma_load_4d(sbase + 2 * kTileA, &tmap, fb, kc, rowB, 0, sj);
-                tma_load_4d(sbase + 2 * kTileA + kHalfTile, &tmap, fb, kc, rowB, 1, sj);
-                ++it;
-              }
+        Sched sc;
+        for (bool more = sc.begin(units_of(P), n_slices); more && ok; more = sc.next()) {
+          for (int c = sc.s0; c < sc.s1; ++c) {
+            const int stage = it % kStages;
+            const uint32_t round = it / kStages;
+            if (!mbar_wait(empty_bar(stage), (round & 1u) ^ 1u, abort_flag)) {
+              ok = false;
+              break;
             }
+            const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
+            const uint32_t fb = full_bar(stage);
+            mbar_expect_tx(fb, kTileA + (sc.two ? 2u : 1u) * kTileA);
+            const int kc = c * kChunk;
+            // A: plane `pass` of slice i, the tile's 128 rows
+            tma_load_4d(sbase, &tmap, fb, kc, rowA, sc.pass, sc.i);
+            tma_load_4d(sbase + kHalfTile, &tmap, fb, kc, rowA + 64, sc.pass, sc.i);
+            // B: [Re_j; Im_j (; Re_j+1; Im_j+1)], the tile's 64 columns each
+            tma_load_4d(sbase + kTileA, &tmap, fb, kc, rowB, 0, sc.j);
+            tma_load_4d(sbase + kTileA + kHalfTile, &tmap, fb, kc, rowB, 1, sc.j);
+            if (sc.two) {
+              tma_load_4d(sbase + 2 * kTileA, &tmap, fb, kc, rowB, 0, sc.j + 1);
+              tma_load_4d(sbase + 2 * kTileA + kHalfTile, &tmap, fb, kc, rowB, 1, sc.j + 1);
+            }
+            ++it;
+          }
         }
       }
       if (!ok) {
@@ -286,49 +349,35 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
         const EmuTile T = tiles[tile];
         const Prob P = probs[T.prob];
-        const Units U = units_of(P);
-        const int nu = U.count();
-        for (int u = 0; u < nu && ok; ++u) {
-          int c0, c1, neg;
-          U.get(u, c0, c1, neg);
-          for (int pt = 0; pt < n_slices && ok; ++pt)
-          for (int pi = 0; pi <= pt && ok; ++pi) {
-            const int span = pair_span(pi, pt - pi);
-            for (int s0 = c0; s0 < c1 && ok; s0 += span) {
-              const int s1 = min(c1, s0 + span);
-              const int buf = acc_it & 1;
-              const uint32_t use = acc_it >> 1;
-              if (!mbar_wait(tempty_bar(buf), (use & 1u) ^ 1u, abort_flag)) {
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-              const uint32_t d1 = tmem_base + (uint32_t)buf * 256u;
-              const uint32_t d2 = d1 + 128u;
-              for (int c = s0; c < s1; ++c) {
-                const int stage = it % kStages;
-                if (!mbar_wait(full_bar(stage), (it / kStages) & 1u, abort_flag)) {
-                  ok = false;
-                  break;
-                }
-                tc_fence_after();
-                const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
-                const uint64_t dar = sdesc(sbase), dai = sdesc(sbase + kTileA),
-                               db = sdesc(sbase + 2 * kTileA);
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                  const uint32_t acc = (c > s0 || kk > 0) ? 1u : 0u;
-                  umma(d1, dar + 2 * kk, db + 2 * kk, acc);
-                  umma(d2, dai + 2 * kk, db + 2 * kk, acc);
-                }
-                umma_commit(empty_bar(stage));
-                ++it;
-              }
-              if (!ok) break;
-              umma_commit(tfull_bar(buf));
-              ++acc_it;
-            }
+        Sched sc;
+        for (bool more = sc.begin(units_of(P), n_slices); more && ok; more = sc.next()) {
+          const int buf = acc_it & 1;  // equals sc.pass: R passes use acc_R, I passes acc_I
+          const uint32_t use = acc_it >> 1;
+          if (!mbar_wait(tempty_bar(buf), (use & 1u) ^ 1u, abort_flag)) {
+            ok = false;
+            break;
           }
+          tc_fence_after();
+          const uint32_t d = tmem_base + (uint32_t)buf * 256u;
+          const uint32_t idesc = sc.two ? kIdesc256 : kIdesc128;
+          for (int c = sc.s0; c < sc.s1; ++c) {
+            const int stage = it % kStages;
+            if (!mbar_wait(full_bar(stage), (it / kStages) & 1u, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
+            const uint64_t da = sdesc(sbase), db = sdesc(sbase + kTileA);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              umma(d, da + 2 * kk, db + 2 * kk, idesc, (c > sc.s0 || kk > 0) ? 1u : 0u);
+            umma_commit(empty_bar(stage));
+            ++it;
+          }
+          if (!ok) break;
+          umma_commit(tfull_bar(buf));
+          ++acc_it;
         }
       }
       // all MMAs issued so far complete before teardown
@@ -349,51 +398,46 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       const EmuTile T = tiles[tile];
       const Prob P = probs[T.prob];
-      const Units U = units_of(P);
-      const int nu = U.count();
       long long acc[64];
 #pragma unroll
       for (int n = 0; n < 64; ++n) acc[n] = 0;
-      for (int u = 0; u < nu && ok; ++u) {
-        int c0, c1, neg;
-        U.get(u, c0, c1, neg);
-        for (int pt = 0; pt < n_slices && ok; ++pt)
-        for (int pi = 0; pi <= pt && ok; ++pi)
-        for (int s0 = c0; s0 < c1 && ok; s0 += pair_span(pi, pt - pi)) {
-          const int sh = frac - kSliceBits * (pt + 2);
-          const int buf = acc_it & 1;
-          const uint32_t use = acc_it >> 1;
-          if (!mbar_wait(tfull_bar(buf), use & 1u, abort_flag)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          __syncwarp();  // tcgen05.ld is warp-collective
-          const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * 256u;
-          // Re: acc1[0:64] + acc2[64:128];  Im: acc1[64:128] - acc2[0:64]
-          const uint32_t col1 = h ? 64u : 0u, col2 = h ? 128u : 192u;
+      Sched sc;
+      for (bool more = sc.begin(units_of(P), n_slices); more && ok; more = sc.next()) {
+        const int buf = acc_it & 1;
+        const uint32_t use = acc_it >> 1;
+        if (!mbar_wait(tfull_bar(buf), use & 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        __syncwarp();  // tcgen05.ld is warp-collective
+        // R pass: Re += RR (cols 0..63 of a pair block), Im += RI (64..127);
+        // I pass: Re += II (64..127), Im -= IR (0..63).
+        const uint32_t col = (h == 0) ? (sc.pass ? 64u : 0u) : (sc.pass ? 0u : 64u);
+        const bool sub = (sc.neg != 0) != (h == 1 && sc.pass == 1);
+        for (int pq = 0; pq <= sc.two; ++pq) {
+          const int sh = frac - kSliceBits * (sc.i + sc.j + pq + 2);
+          const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * 256u +
+                              (uint32_t)pq * 128u + col;
 #pragma unroll
           for (int cb = 0; cb < 8; ++cb) {
-            uint32_t x1[8], x2[8];
-            tmem_ld8(tb + col1 + 8u * cb, x1);
-            tmem_ld8(tb + col2 + 8u * cb, x2);
+            uint32_t x[8];
+            tmem_ld8(tb + 8u * cb, x);
             tmem_wait_ld();
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-              const int v1 = __float2int_rn(__uint_as_float(x1[e]));
-              const int v2 = __float2int_rn(__uint_as_float(x2[e]));
-              int v = h ? v1 - v2 : v1 + v2;
-              if (neg) v = -v;
+              int v = __float2int_rn(__uint_as_float(x[e]));
+              if (sub) v = -v;
               long long w;
               if (sh >= 0) w = (long long)v * (1ll << sh);
               else w = (long long)((v + (1 << (-sh - 1))) >> (-sh));
               acc[8 * cb + e] += w;
             }
           }
-          tc_fence_before();
-          mbar_arrive(tempty_bar(buf));
-          ++acc_it;
         }
+        tc_fence_before();
+        mbar_arrive(tempty_bar(buf));
+        ++acc_it;
       }
       if (!ok) break;
       // write the lower-triangle part of the tile
