@@ -266,7 +266,9 @@ def run_ours(args):
                      "achieved_algorithmic": round(achieved_alg, 2),
                      "peak_source": f"{src} bf16 {peak_kind} x 1.0 (fp16 = bf16 nominal rate)"},
         "e2e": e2e,
-        "gpu_launches": 8 * args.steps,
+        # per step: ab_prep, ab_assemble, tfactor, layout, opform_S, opform_H,
+        # slicer and the contraction for the S half and for the H half
+        "gpu_launches": 10 * args.steps,
         "clocks": clk,
         "timed_wall_s": round(t_wall, 3),
     }

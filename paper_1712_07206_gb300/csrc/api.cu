@@ -124,7 +124,7 @@ struct flapw_ctx {
   int tile_order = 3;            // emulated tile order in use (see make_tiles)
   int64_t tuned_key = -1;        // shape the autotuner last ran on
   int64_t tiles_rows_key = -1;
-  CUtensorMap tmap{};
+  SliceMaps tmap{};
   void* tmap_base = nullptr;
   int64_t tmap_k = 0, tmap_rows = 0;
   int tmap_s = 0;
@@ -206,18 +206,19 @@ int upload(flapw_ctx* h, DevBuf& d, const std::vector<T>& v) {
   return FLAPW_OK;
 }
 
-// Emulated contraction tiles (128 x 64) and FP64 tiles (64 x 64) of the
-// lower triangles of problems [p0, p1).  The order of the emulated tiles
-// decides which operand rows the ~150 concurrently running tiles share in L2:
+// Emulated contraction tiles (256 x 64, one per CTA pair) and FP64 tiles
+// (64 x 64) of the lower triangles of problems [p0, p1).  The order of the
+// emulated tiles decides which operand rows the ~75 concurrently running
+// tiles share in L2:
 //   order 0: row blocks outer, column blocks inner;  1: column blocks outer;
-//   order 2/3/4: grouped raster -- bands of 8/4/16 row blocks, and within a
+//   order 2/3/4: grouped raster -- bands of 4/2/8 row blocks, and within a
 //   band column by column, so the concurrent tiles touch a compact set of rows.
 void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order,
                 std::vector<EmuTile>* emu, std::vector<F64Tile>* f64) {
   for (int p = p0; p < p1; ++p) {
     const int ng = probs[p].n_g;
-    const int nib = (ng + 127) / 128, njb = (ng + 63) / 64;
-    auto valid = [&](int ib, int jb) { return jb * 64 <= ib * 128 + 127; };
+    const int nib = (ng + 255) / 256, njb = (ng + 63) / 64;
+    auto valid = [&](int ib, int jb) { return jb * 64 <= ib * 256 + 255; };
     if (order == 0) {
       for (int ib = 0; ib < nib; ++ib)
         for (int jb = 0; jb < njb; ++jb)
@@ -227,7 +228,7 @@ void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order,
         for (int ib = 0; ib < nib; ++ib)
           if (valid(ib, jb)) emu->push_back(EmuTile{p, ib, jb, 0});
     } else {
-      const int band = (order == 2) ? 8 : (order == 3) ? 4 : 16;
+      const int band = (order == 2) ? 4 : (order == 3) ? 2 : 8;
       for (int i0 = 0; i0 < nib; i0 += band)
         for (int jb = 0; jb < njb; ++jb)
           for (int ib = i0; ib < std::min(nib, i0 + band); ++ib)
@@ -261,9 +262,10 @@ struct Half {
   int emu_t0, emu_nt, f64_t0, f64_nt;
 };
 
-// Slices (emulated precision) and contracts one half.  Records ev_sl after
-// the slicer and ev_k after the contraction.
-int enqueue_contraction(flapw_ctx* h, const Half& hf, int max_grid, cudaStream_t st, int ev_sl,
+// Slices (emulated precision) and contracts one half beside concurrent work
+// that holds busy_sms SMs.  Records ev_sl after the slicer and ev_k after the
+// contraction.
+int enqueue_contraction(flapw_ctx* h, const Half& hf, int busy_sms, cudaStream_t st, int ev_sl,
                         int ev_k) {
   const int s = slices_of(h);
   const int64_t rows = h->rows;
@@ -272,10 +274,9 @@ int enqueue_contraction(flapw_ctx* h, const Half& hf, int max_grid, cudaStream_t
                         rows, hf.row0, hf.nrows, s, h->d_SL.as<__half>(), h->d_rexp.as<int>(), st),
        "slicer launch");
     CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
-    const int grid = std::max(1, std::min(hf.emu_nt, max_grid));
     CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf.emu_t0,
                           hf.emu_nt, h->d_rexp.as<int>(), s, fixed_frac_bits(h->k_terms),
-                          h->d_cnt.as<int>() + 2, grid, st),
+                          h->d_cnt.as<int>() + 2, busy_sms, st),
        "emulated contraction launch");
   } else {
     CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
@@ -290,12 +291,13 @@ int enqueue_contraction(flapw_ctx* h, const Half& hf, int max_grid, cudaStream_t
 // Slice workspace and its tensor map (host-side; never inside stream capture).
 int ensure_slices(flapw_ctx* h) {
   if (h->opt.precision != FLAPW_PREC_EMU) return FLAPW_OK;
+  CK(h, herk_emu_init(), "contraction kernel setup");
   const int s = slices_of(h);
   CK(h, h->d_SL.ensure((size_t)s * 2 * h->rows * h->k_alloc * 2), "slice workspace");
   if (h->tmap_base != h->d_SL.p || h->tmap_k != h->k_alloc || h->tmap_rows != h->rows ||
       h->tmap_s != s) {
     std::string e;
-    if (!make_slice_tmap(&h->tmap, h->d_SL.p, h->k_alloc, h->rows, s, &e)) return fail(h, FLAPW_ERR_CUDA, e);
+    if (!make_slice_tmaps(&h->tmap, h->d_SL.p, h->k_alloc, h->rows, s, &e)) return fail(h, FLAPW_ERR_CUDA, e);
     h->tmap_base = h->d_SL.p;
     h->tmap_k = h->k_alloc;
     h->tmap_rows = h->rows;
@@ -351,10 +353,9 @@ int autotune_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, in
     for (int rep = 0; rep < 2; ++rep) {
       CK(h, cudaEventRecord(h->ev[14], st), "cudaEventRecord");
       for (const Half* hf : {&b, &a}) {
-        const int grid = std::max(1, std::min(hf->emu_nt, h->num_sms));
         CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf->emu_t0,
                               hf->emu_nt, h->d_rexp.as<int>(), s, fixed_frac_bits(h->k_terms),
-                              h->d_cnt.as<int>() + 2, grid, st),
+                              h->d_cnt.as<int>() + 2, 0, st),
            "emulated contraction launch");
       }
       CK(h, cudaEventRecord(h->ev[15], st), "cudaEventRecord");
@@ -824,13 +825,13 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     CK(h, cudaEventRecord(h->ev[9], st), "cudaEventRecord");
     CK(h, launch_opform_S(oa, factored, st), "S operand launch");
     CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
-    if (int rc = enqueue_contraction(h, hS, std::max(1, h->num_sms - n_slots), st, 3, 4)) return rc;
+    if (int rc = enqueue_contraction(h, hS, n_slots, st, 3, 4)) return rc;
     // join, then H
     CK(h, cudaStreamWaitEvent(st, h->ev[1], 0), "cudaStreamWaitEvent");
     CK(h, cudaEventRecord(h->ev[8], st), "cudaEventRecord");
     CK(h, launch_opform_H(oa, factored, st), "H operand launch");
     CK(h, cudaEventRecord(h->ev[10], st), "cudaEventRecord");
-    if (int rc = enqueue_contraction(h, hH, h->num_sms, st, 11, 12)) return rc;
+    if (int rc = enqueue_contraction(h, hH, 0, st, 11, 12)) return rc;
     for (int i = 0; i < 2 * nk; ++i)
       if (op.host[i]) CK(h, cudaMemcpyAsync(op.host[i], op.dev[i], op.bytes[i], cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
     CK(h, cudaEventRecord(h->ev[5], st), "cudaEventRecord");
@@ -933,7 +934,7 @@ int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const i
                         h->d_Z.as<double2>(), st),
      "gather launch");
   CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
-  if (int rc = enqueue_contraction(h, hf, h->num_sms, st, 3, 4)) return rc;
+  if (int rc = enqueue_contraction(h, hf, 0, st, 3, 4)) return rc;
   if (!devH) CK(h, cudaMemcpyAsync(H, dH, ob, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
   CK(h, cudaEventRecord(h->ev[5], st), "cudaEventRecord");
   h->ev_recorded = true;
@@ -1014,7 +1015,7 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
       s.n_pivot2 = c[0];
       s.n_pos = kpk[1];
       s.n_neg = kpk[2];
-      // tensor flops: per tile, pairs x chunks x 2 MMAs x 4 x (2*128*128*16)
+      // tensor flops: per 256 x 64 tile, slice pairs x chunks x 2 passes x 4 x (2*256*128*16)
       const int S_ = slices_of(h);
       const double pairs = S_ * (S_ + 1) / 2.0;
       const double chH = std::ceil(kpk[1] / 64.0) + std::ceil(kpk[2] / 64.0);
@@ -1022,10 +1023,10 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
       double tf = 0;
       for (int k = 0; k < h->n_k; ++k) {
         const int ng = (int)(h->goff[k + 1] - h->goff[k]);
-        const int nib = (ng + 127) / 128, njb = (ng + 63) / 64;
+        const int nib = (ng + 255) / 256, njb = (ng + 63) / 64;
         double nt = 0;
-        for (int ib = 0; ib < nib; ++ib) nt += std::min(njb, 2 * ib + 2);
-        tf += nt * pairs * (chH + chS) * 2.0 * 4.0 * (2.0 * 128 * 128 * 16);
+        for (int ib = 0; ib < nib; ++ib) nt += std::min(njb, 4 * ib + 4);
+        tf += nt * pairs * (chH + chS) * 2.0 * 4.0 * (2.0 * 256 * 128 * 16);
       }
       s.flops_tensor = tf;
     } else {

@@ -32,10 +32,11 @@ struct Prob {
   double2* out;   // lower triangle, complex128
 };
 
-// Output tile of the emulated contraction: 128 rows (G') x 64 columns (G).
+// Output tile of the emulated contraction: 256 rows (G') x 64 columns (G),
+// computed by a CTA pair.
 struct EmuTile {
   int prob;
-  int ib;  // row block (128)
+  int ib;  // row block (256)
   int jb;  // column block (64)
   int pad;
 };
@@ -150,14 +151,24 @@ cudaError_t launch_herk_f64(const double2* Z, int64_t k_alloc, const Prob* probs
 // sums of at most k_terms complex products (each < 2 in magnitude after the
 // per-row scaling): 61 - ceil(log2 k_terms), clamped to [40, 50].
 int fixed_frac_bits(int64_t k_terms);
-cudaError_t launch_herk_emu(const CUtensorMap& tmap, const Prob* probs, const EmuTile* tiles,
+// Tensor maps of the slice array [slice][plane][row][k] (fp16) for the
+// emulated contraction's operand loads.
+struct SliceMaps {
+  CUtensorMap a;   // 64 k x 128 rows (the MMA's A rows)
+  CUtensorMap b2;  // 64 k x 64 rows x both planes (a B half of a slice pair)
+  CUtensorMap b1;  // 64 k x 64 rows (a B half of a lone slice)
+};
+bool make_slice_tmaps(SliceMaps* maps, void* base, int64_t k_alloc, int64_t rows, int n_slices,
+                      std::string* err);
+// Kernel attributes and the co-resident CTA-pair count of the current device
+// (host side; call outside stream capture before the first launch).
+cudaError_t herk_emu_init();
+// Launches persistent CTA pairs: min(n_tiles, co-resident pairs - busy_sms),
+// where busy_sms is the number of SMs that concurrent work holds.
+cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuTile* tiles,
                             int n_tiles, const int* rexp, int n_slices, int frac, int* err,
-                            int grid, cudaStream_t st);
+                            int busy_sms, cudaStream_t st);
 size_t herk_emu_smem_bytes();
-
-// Tensor map for the slice array [slice][plane][row][k] (fp16).
-bool make_slice_tmap(CUtensorMap* map, void* base, int64_t k_alloc, int64_t rows, int n_slices,
-                     std::string* err);
 
 // ---- host G enumeration ----------------------------------------------------
 int enumerate_g(const double lat[9], const double k[3], double kmax, std::vector<int>* n3);

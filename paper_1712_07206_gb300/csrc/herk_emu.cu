@@ -17,48 +17,61 @@
 // only where a level's weight falls below 2^-F; FP64 is used once per output
 // element at the end.
 //
-// CTA tile: 128 rows (G') x 64 columns (G) of complex output.  Slice pairs
-// are taken in groups (i; j, j+1) sharing the row slice i: per 64-wide K chunk
-// the producer loads, with TMA and 128-byte swizzle, one plane of slice i for
-// the tile's rows (A: 128 x 64 fp16) and B = [Re_j; Im_j; Re_{j+1}; Im_{j+1}]
-// for the tile's columns (4 x 64 rows), and the MMA warp issues one
-// M=128, N=256, K=16 MMA per 16 columns.  Each K sub-span runs twice: an R pass
-// (A = Re_i) into accumulator acc_R = [RR_j | RI_j | RR_j+1 | RI_j+1] and an I
-// pass (A = Im_i) into acc_I = [IR_j | II_j | IR_j+1 | II_j+1]; the drains add
+// The kernel runs on CTA pairs (a 2-CTA cluster, tcgen05 cta_group::2).  A
+// pair owns an output tile of 256 rows (G') x 64 columns (G) of complex
+// output; CTA r of the pair holds rows 128r..128r+127 and their accumulators.
+// Slice pairs are taken in groups (i; j, j+1) sharing the row slice i.  Per
+// 128-wide K stage each CTA loads with TMA (128-byte swizzle), for two 64-wide
+// K chunks, one plane of slice i for its 128 rows (the MMA's A) and its half
+// of B = [Re_j; Im_j | Re_{j+1}; Im_{j+1}] for the tile's 64 columns (CTA 0 the
+// slice j planes, CTA 1 the slice j+1 planes; for a lone slice j, CTA 0 Re_j
+// and CTA 1 Im_j).  One thread of CTA 0 issues M=256, N=256 (or 128), K=16
+// MMAs that read A and B from both CTAs' shared memory and write each CTA's
+// rows into its own TMEM.  Each K sub-span runs twice: an R pass (A = Re_i)
+// into accumulator acc_R = [RR_j | RI_j | RR_j+1 | RI_j+1] and an I pass
+// (A = Im_i) into acc_I = [IR_j | II_j | IR_j+1 | II_j+1]; the drains add
 //     Re += RR (R pass), Re += II (I pass), Im += RI (R pass), Im -= IR (I pass)
 // so the two 256-column accumulators also double-buffer each other: the drain
-// of one pass overlaps the MMAs of the next.  N=256 halves the shared-memory
-// operand reads per MMA flop of a 128-wide B (the N=128 form ran the tensor
-// pipe at ~64 %).  Rows with sigma = -1 form their own K units, subtracted.
+// of one pass overlaps the MMAs of the next.  Against one CTA per tile (M=128)
+// the pair halves the B bytes each SM loads per MMA flop, and 128-wide stages
+// halve the producer/MMA hand-offs per flop; both bound the tensor pipe's
+// occupancy.  Rows with sigma = -1 form their own K units, subtracted.
 //
-// Warp roles: warp 0 TMA producer, warp 1 TMEM allocator + MMA issuer,
-// warps 2..9 drain/epilogue (warp w reads TMEM lanes 32*(w%4)..+31; warps
-// 2-5 own Re, 6-9 own Im).  Persistent CTAs walk the lower-triangle tile
-// list.  Every wait is bounded by a wall-clock limit; on expiry the CTA
-// records an error, lets its in-flight copies and MMAs complete, frees TMEM
-// and exits.
+// Warp roles (both CTAs): warp 0 TMA producer, warp 1 TMEM allocator (and in
+// CTA 0 the MMA issuer), warps 2..9 drain/epilogue (warp w reads TMEM lanes
+// 32*(w%4)..+31; warps 2-5 own Re, 6-9 own Im).  Stage and accumulator
+// barriers live in CTA 0 (full, tempty) or in both CTAs (empty, tfull,
+// signalled by multicast commits).  Persistent pairs walk the tile list.
+// Every wait is bounded by a wall-clock limit; on expiry the CTA records an
+// error, raises the abort flag of both CTAs, lets its in-flight copies and
+// MMAs complete, frees TMEM and exits.
+#include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "flapw_internal.h"
 
 namespace flapw {
 namespace {
 
-constexpr int kStages = 4;
+constexpr int kStages = 3;
 constexpr int kThreads = 320;
-constexpr uint32_t kHalfTile = 64 * 128;                 // 64 rows x 128 B
-constexpr uint32_t kTileA = 2 * kHalfTile;               // 128 rows
-constexpr uint32_t kStageBytes = 3 * kTileA;             // A (128 rows) + B (256 rows)
+constexpr int kStageChunks = 2;                          // 64-wide K chunks per stage
+constexpr uint32_t kTileA = 128 * 128;                   // A: 128 rows x 128 B, one chunk
+constexpr uint32_t kTileB = 128 * 128;                   // this CTA's B half: <= 128 rows
+constexpr uint32_t kOffB = kStageChunks * kTileA;        // B after both A chunks
+constexpr uint32_t kStageBytes = kStageChunks * (kTileA + kTileB);
 constexpr uint32_t kTmemCols = 512;
 constexpr unsigned long long kWaitNs = 4000000000ull;    // 4 s
 constexpr int kMaxS = 8;
 constexpr int kPassChunks = 32;                          // longest K sub-span of a pass
+constexpr int kMaxDevices = 64;
 
-// instruction descriptors: D = F32, A = B = F16, K-major both, M = 128, N = 256 / 128
+// instruction descriptors: D = F32, A = B = F16, K-major both, M = 256, N = 256 / 128
 constexpr uint32_t kIdesc256 = (1u << 4) | (0u << 7) | (0u << 10) | ((256u >> 3) << 17) |
-                               ((128u >> 4) << 24);
+                               ((256u >> 4) << 24);
 constexpr uint32_t kIdesc128 = (1u << 4) | (0u << 7) | (0u << 10) | ((128u >> 3) << 17) |
-                               ((128u >> 4) << 24);
+                               ((256u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -70,6 +83,22 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Address of the same shared-memory object in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
@@ -77,42 +106,63 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+// Arrive on a barrier given by its cluster address (either CTA of the pair).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cbar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cbar)
+               : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
       : "r"(bar), "r"(parity)
       : "memory");
   return ok != 0;
 }
+
+// Abort flags: one per CTA.  A role that gives up raises both CTAs' flags.
+struct Abort {
+  volatile int* local;
+  uint32_t peer;  // cluster address of the other CTA's flag
+  __device__ void raise() const {
+    *local = 1;
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer), "r"(1) : "memory");
+  }
+};
+
 // Bounded wait.  Returns false if the wall-clock limit passed or another role
-// aborted; the first role to time out raises the abort flag.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+// aborted; the first role to time out raises the abort flags.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const Abort& ab) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 63) == 0) {
-      if (*abort_flag) return false;
+      if (*ab.local) return false;
       if (global_ns() - t0 > kWaitNs) {
-        *abort_flag = 1;
+        ab.raise();
         return false;
       }
     }
   }
 }
+// Wait that ignores the abort flags (teardown), still bounded.
+__device__ __forceinline__ void mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kWaitNs) break;
+}
 
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+// TMA tile load into this CTA's shared memory, completion counted on a
+// barrier of either CTA of the pair (cluster address).
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t cbar,
                                             int c0, int c1, int c2, int c3) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      "cp.async.bulk.tensor.4d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(cbar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
       : "memory");
 }
 
@@ -126,16 +176,21 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                     uint32_t accum) {
+// One pair MMA: A rows from both CTAs (128 each), B halves from both CTAs,
+// D rows into each CTA's TMEM at the same address.
+__device__ __forceinline__ void umma_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accum) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accum));
 }
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
+// Arrive on the barrier at this offset in both CTAs once the MMAs issued so
+// far have completed.
+__device__ __forceinline__ void umma_commit_both(uint32_t bar) {
   asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar), "h"((uint16_t)3)
       : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
@@ -151,8 +206,38 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                  "=r"(r[6]), "=r"(r[7])
                : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// tcgen05.wait::ld that also marks the loaded registers as written here, so
+// the compiler cannot read them before the wait.
+__device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&r)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7])
+               :
+               : "memory");
+}
+
+// Adds f(v) for the integer values v of 64 consecutive TMEM columns (this
+// thread's lane) to acc[0..63].  The next 8 columns load while the current 8
+// are converted.
+template <class F>
+__device__ __forceinline__ void drain64(uint32_t tb, long long (&acc)[64], F f) {
+  uint32_t xa[8], xb[8];
+  tmem_ld8(tb, xa);
+  tmem_wait_ld_regs(xa);
+#pragma unroll
+  for (int cb = 0; cb < 8; ++cb) {
+    if (cb & 1) {
+      if (cb < 7) tmem_ld8(tb + 8u * (cb + 1), xa);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[8 * cb + e] += f(__float2int_rn(__uint_as_float(xb[e])));
+      if (cb < 7) tmem_wait_ld_regs(xa);
+    } else {
+      if (cb < 7) tmem_ld8(tb + 8u * (cb + 1), xb);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[8 * cb + e] += f(__float2int_rn(__uint_as_float(xa[e])));
+      if (cb < 7) tmem_wait_ld_regs(xb);
+    }
+  }
 }
 
 // Slice pairs (i, j), 0-based, are visited by level: t = i + j = 0..s-1
@@ -201,16 +286,20 @@ struct Sched {
   Units U;
   int s, nu;
   int u, c0, c1, neg;
-  int i, j, two, span;
+  int i, j, two;
+  int nsub, k;  // sub-spans of the unit for this group, current one
   int s0, s1, pass;
 
+  __device__ int bound(int m) const { return c0 + (int)((long long)m * (c1 - c0) / nsub); }
   __device__ void set_group() {
     two = (j + 1 <= s - 1 - i) ? 1 : 0;
-    span = pair_span(i, j);
+    int span = pair_span(i, j);
     if (two) span = min(span, pair_span(i, j + 1));
     span = min(span, kPassChunks);
+    nsub = (c1 - c0 + span - 1) / span;
+    k = 0;
     s0 = c0;
-    s1 = min(c1, s0 + span);
+    s1 = bound(1);
   }
   __device__ bool begin(const Units& units, int n_slices) {
     U = units;
@@ -231,9 +320,9 @@ struct Sched {
       return true;
     }
     pass = 0;
-    s0 += span;
-    if (s0 < c1) {
-      s1 = min(c1, s0 + span);
+    if (++k < nsub) {
+      s0 = s1;
+      s1 = bound(k + 1);
       return true;
     }
     j += 2;
@@ -251,17 +340,19 @@ struct Sched {
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
-    herk_emu_kernel(const __grid_constant__ CUtensorMap tmap, const Prob* __restrict__ probs,
+    herk_emu_kernel(const __grid_constant__ SliceMaps maps, const Prob* __restrict__ probs,
                     const EmuTile* __restrict__ tiles, int n_tiles, const int* __restrict__ rexp,
                     int n_slices, int frac, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
-  // bars: full[4], empty[4], tfull[2], tempty[2], drain[1]
+  // bars: full[kStages], empty[kStages], tfull[2], tempty[2], drain[1]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* abort_word = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const int pair = blockIdx.x >> 1, n_pairs = gridDim.x >> 1;
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
@@ -276,126 +367,136 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), 256);
+      mbar_init(tempty_bar(b), 16);  // one arrival per drain warp of both CTAs
     }
     mbar_init(drain_bar, 1);
-    *abort_flag = 0;
+    *abort_word = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b2)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b1)) : "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+    // both CTAs of the pair allocate together: the same columns in each TMEM
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
                  "r"(kTmemCols)
                  : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
-  __syncthreads();
+  cluster_sync();  // barriers initialised and TMEM allocated in both CTAs
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  const Abort ab{abort_word, map_to_rank(smem_u32(abort_word), rank ^ 1u)};
 
   if (warp == 0) {
-    // ---------------- TMA producer ----------------
+    // ---------------- TMA producer (both CTAs) ----------------
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      for (int tile = pair; tile < n_tiles && ok; tile += n_pairs) {
         const EmuTile T = tiles[tile];
         const Prob P = probs[T.prob];
-        const int rowA = P.row_base + T.ib * 128, rowB = P.row_base + T.jb * 64;
+        const int rowA = P.row_base + T.ib * 256 + (int)rank * 128, rowB = P.row_base + T.jb * 64;
         Sched sc;
         for (bool more = sc.begin(units_of(P), n_slices); more && ok; more = sc.next()) {
-          for (int c = sc.s0; c < sc.s1; ++c) {
+          const uint32_t b_bytes = sc.two ? kTileB : kTileB / 2;
+          for (int c = sc.s0; c < sc.s1; c += kStageChunks) {
+            const int nv = min(kStageChunks, sc.s1 - c);
             const int stage = it % kStages;
             const uint32_t round = it / kStages;
-            if (!mbar_wait(empty_bar(stage), (round & 1u) ^ 1u, abort_flag)) {
+            if (!mbar_wait(empty_bar(stage), (round & 1u) ^ 1u, ab)) {
               ok = false;
               break;
             }
             const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
             const uint32_t fb = full_bar(stage);
-            mbar_expect_tx(fb, kTileA + (sc.two ? 2u : 1u) * kTileA);
-            const int kc = c * kChunk;
-            // A: plane `pass` of slice i, the tile's 128 rows
-            tma_load_4d(sbase, &tmap, fb, kc, rowA, sc.pass, sc.i);
-            tma_load_4d(sbase + kHalfTile, &tmap, fb, kc, rowA + 64, sc.pass, sc.i);
-            // B: [Re_j; Im_j (; Re_j+1; Im_j+1)], the tile's 64 columns each
-            tma_load_4d(sbase + kTileA, &tmap, fb, kc, rowB, 0, sc.j);
-            tma_load_4d(sbase + kTileA + kHalfTile, &tmap, fb, kc, rowB, 1, sc.j);
-            if (sc.two) {
-              tma_load_4d(sbase + 2 * kTileA, &tmap, fb, kc, rowB, 0, sc.j + 1);
-              tma_load_4d(sbase + 2 * kTileA + kHalfTile, &tmap, fb, kc, rowB, 1, sc.j + 1);
+            // CTA 0's barrier counts the bytes of both CTAs
+            if (rank == 0) mbar_expect_tx(fb, 2u * (uint32_t)nv * (kTileA + b_bytes));
+            const uint32_t cfb = map_to_rank(fb, 0);
+            for (int q = 0; q < nv; ++q) {
+              const int kc = (c + q) * kChunk;
+              // A: plane `pass` of slice i, this CTA's 128 rows
+              tma_load_4d(sbase + q * kTileA, &maps.a, cfb, kc, rowA, sc.pass, sc.i);
+              // B half: slice j + rank, both planes (or plane `rank` of a lone slice j)
+              if (sc.two)
+                tma_load_4d(sbase + kOffB + q * kTileB, &maps.b2, cfb, kc, rowB, 0, sc.j + (int)rank);
+              else
+                tma_load_4d(sbase + kOffB + q * kTileB, &maps.b1, cfb, kc, rowB, (int)rank, sc.j);
             }
             ++it;
           }
         }
       }
       if (!ok) {
-        // let the copies already issued land before the CTA can exit
-        for (uint32_t q = (it > kStages ? it - kStages : 0); q < it; ++q) {
-          const unsigned long long t0 = global_ns();
-          while (!mbar_try_wait(full_bar(q % kStages), (q / kStages) & 1u))
-            if (global_ns() - t0 > kWaitNs) break;
-        }
+        // CTA 0 sees both CTAs' copies land on its barriers; the pair's
+        // closing cluster barrier keeps CTA 1 resident until then
+        if (rank == 0)
+          for (uint32_t q = (it > kStages ? it - kStages : 0); q < it; ++q)
+            mbar_wait_bounded(full_bar(q % kStages), (q / kStages) & 1u);
         atomicExch(err, FLAPW_ERR_TIMEOUT);
       }
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
+    // ---------------- MMA issuer (CTA 0 only) ----------------
+    if (lane == 0 && rank == 0) {
       uint32_t it = 0, acc_it = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      for (int tile = pair; tile < n_tiles && ok; tile += n_pairs) {
         const EmuTile T = tiles[tile];
         const Prob P = probs[T.prob];
         Sched sc;
         for (bool more = sc.begin(units_of(P), n_slices); more && ok; more = sc.next()) {
           const int buf = acc_it & 1;  // equals sc.pass: R passes use acc_R, I passes acc_I
           const uint32_t use = acc_it >> 1;
-          if (!mbar_wait(tempty_bar(buf), (use & 1u) ^ 1u, abort_flag)) {
+          if (!mbar_wait(tempty_bar(buf), (use & 1u) ^ 1u, ab)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t d = tmem_base + (uint32_t)buf * 256u;
           const uint32_t idesc = sc.two ? kIdesc256 : kIdesc128;
-          for (int c = sc.s0; c < sc.s1; ++c) {
+          for (int c = sc.s0; c < sc.s1; c += kStageChunks) {
+            const int nv = min(kStageChunks, sc.s1 - c);
             const int stage = it % kStages;
-            if (!mbar_wait(full_bar(stage), (it / kStages) & 1u, abort_flag)) {
+            if (!mbar_wait(full_bar(stage), (it / kStages) & 1u, ab)) {
               ok = false;
               break;
             }
             tc_fence_after();
             const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
-            const uint64_t da = sdesc(sbase), db = sdesc(sbase + kTileA);
+            for (int q = 0; q < nv; ++q) {
+              const uint64_t da = sdesc(sbase + q * kTileA), db = sdesc(sbase + kOffB + q * kTileB);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              umma(d, da + 2 * kk, db + 2 * kk, idesc, (c > sc.s0 || kk > 0) ? 1u : 0u);
-            umma_commit(empty_bar(stage));
+              for (int kk = 0; kk < 4; ++kk)
+                umma_pair(d, da + 2 * kk, db + 2 * kk, idesc, (c > sc.s0 || q > 0 || kk > 0) ? 1u : 0u);
+            }
+            umma_commit_both(empty_bar(stage));
             ++it;
           }
           if (!ok) break;
-          umma_commit(tfull_bar(buf));
+          umma_commit_both(tfull_bar(buf));
           ++acc_it;
         }
       }
-      // all MMAs issued so far complete before teardown
-      umma_commit(drain_bar);
-      const unsigned long long t0 = global_ns();
-      while (!mbar_try_wait(drain_bar, 0))
-        if (global_ns() - t0 > kWaitNs) break;
+      // all MMAs issued so far complete before teardown (both CTAs learn it)
+      umma_commit_both(drain_bar);
+      mbar_wait_bounded(drain_bar, 0);
       if (!ok) atomicExch(err, FLAPW_ERR_TIMEOUT);
+    } else if (lane == 0) {
+      // CTA 1: its TMEM is written until CTA 0's last MMA completes
+      mbar_wait_bounded(drain_bar, 0);
     }
   } else {
-    // ---------------- drain + epilogue (256 threads) ----------------
+    // ---------------- drain + epilogue (256 threads per CTA) ----------------
     const int ew = warp - 2;
     const int q = warp & 3;       // TMEM lane quadrant this warp may access
     const int h = ew >> 2;        // 0: Re, 1: Im
-    const int m = q * 32 + lane;  // row within the tile
+    const int m = q * 32 + lane;  // row within this CTA's 128 rows
     uint32_t acc_it = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    for (int tile = pair; tile < n_tiles && ok; tile += n_pairs) {
       const EmuTile T = tiles[tile];
       const Prob P = probs[T.prob];
       long long acc[64];
@@ -405,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (bool more = sc.begin(units_of(P), n_slices); more && ok; more = sc.next()) {
         const int buf = acc_it & 1;
         const uint32_t use = acc_it >> 1;
-        if (!mbar_wait(tfull_bar(buf), use & 1u, abort_flag)) {
+        if (!mbar_wait(tfull_bar(buf), use & 1u, ab)) {
           ok = false;
           break;
         }
@@ -419,30 +520,28 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int sh = frac - kSliceBits * (sc.i + sc.j + pq + 2);
           const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * 256u +
                               (uint32_t)pq * 128u + col;
-#pragma unroll
-          for (int cb = 0; cb < 8; ++cb) {
-            uint32_t x[8];
-            tmem_ld8(tb + 8u * cb, x);
-            tmem_wait_ld();
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              int v = __float2int_rn(__uint_as_float(x[e]));
-              if (sub) v = -v;
-              long long w;
-              if (sh >= 0) w = (long long)v * (1ll << sh);
-              else w = (long long)((v + (1 << (-sh - 1))) >> (-sh));
-              acc[8 * cb + e] += w;
-            }
+          if (sh >= 0) {
+            // +-v 2^sh as one 32 x 32 -> 64-bit multiply-add; a shift past 30
+            // is applied to v first (|v| <= 2^24 and sh - 30 <= 6)
+            const int pre = sh > 30 ? sh - 30 : 0;
+            const int mul = sub ? -(1 << (sh - pre)) : (1 << (sh - pre));
+            if (pre == 0) drain64(tb, acc, [=](int v) { return (long long)v * mul; });
+            else drain64(tb, acc, [=](int v) { return (long long)(v << pre) * mul; });
+          } else {
+            // below the fixed point: round the signed value half up
+            const int rs = -sh, half = 1 << (-sh - 1);
+            drain64(tb, acc, [=](int v) { return (long long)(((sub ? -v : v) + half) >> rs); });
           }
         }
         tc_fence_before();
-        mbar_arrive(tempty_bar(buf));
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(map_to_rank(tempty_bar(buf), 0));
         ++acc_it;
       }
       if (!ok) break;
-      // write the lower-triangle part of the tile
+      // write the lower-triangle part of this CTA's rows of the tile
       const int64_t ng = P.n_g;
-      const int64_t gr = (int64_t)T.ib * 128 + m;
+      const int64_t gr = (int64_t)T.ib * 256 + (int64_t)rank * 128 + m;
       if (gr < ng) {
         const int er = rexp[P.row_base + gr];
         double* outd = reinterpret_cast<double*>(P.out);
@@ -464,16 +563,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (!ok) atomicExch(err, FLAPW_ERR_TIMEOUT);
   }
 
+  // neither CTA leaves while the other may still touch its shared memory
   tc_fence_before();
-  __syncthreads();
+  cluster_sync();
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
                  "r"(kTmemCols)
                  : "memory");
   }
 }
+
+struct DevState {
+  bool ready = false;
+  int max_pairs = 0;
+};
+std::mutex g_state_mutex;
+DevState g_state[kMaxDevices];
 
 }  // namespace
 
@@ -486,27 +593,74 @@ int fixed_frac_bits(int64_t k_terms) {
   return f < 40 ? 40 : (f > 50 ? 50 : f);  // <= 50: one (0,0) drain, < 2^25 2^(F-14), fits too
 }
 
-cudaError_t launch_herk_emu(const CUtensorMap& tmap, const Prob* probs, const EmuTile* tiles,
+cudaError_t herk_emu_init() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_state_mutex);
+  if (g_state[dev].ready) return cudaSuccess;
+  const size_t smem = herk_emu_smem_bytes();
+  e = cudaFuncSetAttribute(herk_emu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2 * (sms / 2));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  e = cudaOccupancyMaxActiveClusters(&n, herk_emu_kernel, &cfg);
+  if (e != cudaSuccess) return e;
+  if (n < 1) return cudaErrorInvalidConfiguration;
+  g_state[dev].max_pairs = n;
+  g_state[dev].ready = true;
+  return cudaSuccess;
+}
+
+cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuTile* tiles,
                             int n_tiles, const int* rexp, int n_slices, int frac, int* err,
-                            int grid, cudaStream_t st) {
+                            int busy_sms, cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   if (n_slices < 1 || n_slices > kMaxS || frac < 40 || frac > 50) return cudaErrorInvalidValue;
-  static bool attr = false;
-  const size_t smem = herk_emu_smem_bytes();
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(herk_emu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  herk_emu_kernel<<<grid, kThreads, smem, st>>>(tmap, probs, tiles, n_tiles, rexp, n_slices, frac,
-                                                err);
+  cudaError_t e = herk_emu_init();
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  // A persistent pair that cannot be placed at launch starts only when the
+  // concurrent work ends and then delays the whole launch; each SM held
+  // elsewhere can cost at most one pair its place.
+  const int pairs = std::max(1, std::min(n_tiles, g_state[dev].max_pairs - std::max(0, busy_sms)));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2 * pairs);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = herk_emu_smem_bytes();
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, herk_emu_kernel, maps, probs, tiles, n_tiles, rexp, n_slices, frac, err);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
-// Tensor map over SL[slice][plane][row][k] (fp16), 64 x 64 boxes, 128-byte swizzle.
-bool make_slice_tmap(CUtensorMap* map, void* base, int64_t k_alloc, int64_t rows, int n_slices,
-                     std::string* err) {
+// Tensor maps over SL[slice][plane][row][k] (fp16), 128-byte swizzle, boxes of
+// 64 k by: 128 rows (a), 64 rows x 2 planes (b2), 64 rows (b1).
+bool make_slice_tmaps(SliceMaps* maps, void* base, int64_t k_alloc, int64_t rows, int n_slices,
+                      std::string* err) {
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -526,14 +680,17 @@ bool make_slice_tmap(CUtensorMap* map, void* base, int64_t k_alloc, int64_t rows
   const cuuint64_t dims[4] = {(cuuint64_t)k_alloc, (cuuint64_t)rows, 2, (cuuint64_t)n_slices};
   const cuuint64_t strides[3] = {(cuuint64_t)k_alloc * 2, (cuuint64_t)(rows * k_alloc * 2),
                                  (cuuint64_t)(2 * rows * k_alloc * 2)};
-  const cuuint32_t box[4] = {64, 64, 1, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, base, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    *err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
-    return false;
+  const cuuint32_t boxes[3][4] = {{64, 128, 1, 1}, {64, 64, 2, 1}, {64, 64, 1, 1}};
+  CUtensorMap* out[3] = {&maps->a, &maps->b2, &maps->b1};
+  for (int t = 0; t < 3; ++t) {
+    CUresult r = fn(out[t], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, base, dims, strides, boxes[t], estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      *err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+      return false;
+    }
   }
   return true;
 }

@@ -47,23 +47,23 @@ __global__ void noalloc_kmap_kernel(const int* sigma, int K, int kp_pad, int k_a
   }
 }
 
-// Lower-triangle tiles (128 x 64) in bands of 4 row blocks, column by column.
+// Lower-triangle tiles (256 x 64) in bands of 2 row blocks, column by column.
 __global__ void noalloc_tiles_kernel(int N, EmuTile* tiles) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int nib = (N + 127) / 128, njb = (N + 63) / 64;
+  const int nib = (N + 255) / 256, njb = (N + 63) / 64;
   int t = 0;
-  for (int i0 = 0; i0 < nib; i0 += 4)
+  for (int i0 = 0; i0 < nib; i0 += 2)
     for (int jb = 0; jb < njb; ++jb)
-      for (int ib = i0; ib < min(nib, i0 + 4); ++ib)
-        if (jb * 64 <= ib * 128 + 127) tiles[t++] = EmuTile{0, ib, jb, 0};
+      for (int ib = i0; ib < min(nib, i0 + 2); ++ib)
+        if (jb * 64 <= ib * 256 + 255) tiles[t++] = EmuTile{0, ib, jb, 0};
 }
 
 int count_tiles(int N) {
-  const int nib = (N + 127) / 128, njb = (N + 63) / 64;
+  const int nib = (N + 255) / 256, njb = (N + 63) / 64;
   int t = 0;
   for (int ib = 0; ib < nib; ++ib)
     for (int jb = 0; jb < njb; ++jb)
-      if (jb * 64 <= ib * 128 + 127) ++t;
+      if (jb * 64 <= ib * 256 + 255) ++t;
   return t;
 }
 
@@ -138,9 +138,6 @@ extern "C" int flapw_herk_noalloc(const void* Z, int64_t ldz, int K, int N, cons
     }
     base = static_cast<unsigned char*>(g_scratch_dev[dev]);
   }
-  int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return fail(FLAPW_ERR_CUDA, "cudaDeviceGetAttribute failed");
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int* err = reinterpret_cast<int*>(base + o_err);
@@ -155,9 +152,10 @@ extern "C" int flapw_herk_noalloc(const void* Z, int64_t ldz, int K, int N, cons
 
   const Prob P{0, N, kp, kn, layout, 0, layout == FLAPW_LAYOUT_LOWER_FULL ? ldh : N,
                static_cast<double2*>(H)};
-  CUtensorMap tmap;
+  SliceMaps tmap;
   std::string terr;
-  if (!make_slice_tmap(&tmap, SL, k_alloc, N, s, &terr)) return fail(FLAPW_ERR_CUDA, "tensor map encoding failed");
+  if (!make_slice_tmaps(&tmap, SL, k_alloc, N, s, &terr)) return fail(FLAPW_ERR_CUDA, "tensor map encoding failed");
+  if (herk_emu_init() != cudaSuccess) return fail(FLAPW_ERR_CUDA, "contraction kernel setup failed");
   cudaError_t e = cudaMemsetAsync(err, 0, 8 * sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(rowp, 0, (size_t)N * sizeof(int), st);
   if (e == cudaSuccess && sigma)
@@ -170,8 +168,7 @@ extern "C" int flapw_herk_noalloc(const void* Z, int64_t ldz, int K, int N, cons
   if (e == cudaSuccess) e = launch_gather_Z(static_cast<const double2*>(Z), ldz, K, N, kmap, k_alloc, Zs, st);
   if (e == cudaSuccess) e = launch_slicer(Zs, k_alloc, prob, rowp, N, 0, N, s, SL, rexp, st);
   if (e == cudaSuccess)
-    e = launch_herk_emu(tmap, prob, tiles, n_tiles, rexp, s, fixed_frac_bits(K), err,
-                        n_tiles < sms ? n_tiles : sms, st);
+    e = launch_herk_emu(tmap, prob, tiles, n_tiles, rexp, s, fixed_frac_bits(K), err, 0, st);
   if (e != cudaSuccess) return fail(FLAPW_ERR_CUDA, cudaGetErrorString(e));
   return FLAPW_OK;
 }
