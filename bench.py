@@ -266,9 +266,11 @@ def run_ours(args):
                      "achieved_algorithmic": round(achieved_alg, 2),
                      "peak_source": f"{src} bf16 {peak_kind} x 1.0 (fp16 = bf16 nominal rate)"},
         "e2e": e2e,
-        # per step: ab_prep, ab_assemble, tfactor, layout, opform_S, opform_H,
-        # slicer and the contraction for the S half and for the H half
-        "gpu_launches": 10 * args.steps,
+        # per step: ab_prep, ab_assemble, tfactor, layout, opform_S, slicer and
+        # contraction for the S half and for the H half, and the H operands:
+        # with factored operands W and conj(C^H) formed and sliced (4 kernels)
+        # and their tensor-core product, else opform_H
+        "gpu_launches": (14 if args.operands == "factored" else 10) * args.steps,
         "clocks": clk,
         "timed_wall_s": round(t_wall, 3),
     }

@@ -18,7 +18,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libflapw.so")
 SOURCES = ["api.cu", "gvec.cpp", "ab_gen.cu", "tfactor.cu", "opform.cu", "slicer.cu",
-           "herk_f64.cu", "herk_emu.cu", "noalloc.cu"]
+           "herk_f64.cu", "herk_emu.cu", "opgemm.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,6 +31,7 @@ def nvcc() -> str:
 
 def _deps():
     files = [os.path.join(SRC, s) for s in SOURCES] + [os.path.join(SRC, "flapw_internal.h"),
+                                                       os.path.join(SRC, "tc_common.cuh"),
                                                        os.path.join(ROOT, "include", "flapw.h")]
     return max(os.path.getmtime(f) for f in files)
 

@@ -115,6 +115,15 @@ struct flapw_ctx {
   bool prep_valid = false;
 
   // build_HS workspaces
+  // H operands on the tensor cores (emulated path, factored operands): the two
+  // factors in FP64 and sliced, their scale exponents, tiles and tensor maps
+  DevBuf d_opA, d_opB, d_opSLA, d_opSLB, d_oprexp, d_optiles;
+  std::vector<OpTile> optiles;
+  CUtensorMap opmap_a{}, opmap_b{};
+  void* opmap_a_base = nullptr;
+  void* opmap_b_base = nullptr;
+  int64_t opmap_a_rows = 0, opmap_b_rows = 0;
+  int opmap_kp = 0;
   DevBuf d_T, d_work, d_CH, d_fac, d_cnt, d_slot, d_U, d_off, d_probs, d_rowprob, d_Z, d_SL, d_rexp,
       d_emu_tiles, d_f64_tiles, d_combo, d_kmap, d_stageA, d_stageB, d_stageOut;
   PinBuf pin_in, pin_probs;
@@ -132,8 +141,8 @@ struct flapw_ctx {
   cudaStream_t cap_stream = nullptr, aux_stream = nullptr;
   // events: 0 start, 1 factor done (aux), 2 S operands done, 3 S sliced, 4 S contracted,
   // 5 end, 6/7 build_AB, 8 H operands start, 9 S operands start, 10 H operands done,
-  // 11 H sliced, 12 H contracted, 13 fork
-  cudaEvent_t ev[16]{};
+  // 11 H sliced, 12 H contracted, 13 fork, 14/15 autotune, 16 auxiliary work done (join)
+  cudaEvent_t ev[17]{};
   bool ev_recorded = false, ev_ab = false, ev_engine = false;
   cudaStream_t last_stream = nullptr;
   flapw_stats stats{};
@@ -271,7 +280,7 @@ int enqueue_contraction(flapw_ctx* h, const Half& hf, int busy_sms, cudaStream_t
   const int64_t rows = h->rows;
   if (h->opt.precision == FLAPW_PREC_EMU) {
     CK(h, launch_slicer(h->d_Z.as<double2>(), h->k_alloc, h->d_probs.as<Prob>(), h->d_rowprob.as<int>(),
-                        rows, hf.row0, hf.nrows, s, h->d_SL.as<__half>(), h->d_rexp.as<int>(), st),
+                        0, rows, hf.row0, hf.nrows, s, h->d_SL.as<__half>(), h->d_rexp.as<int>(), st),
        "slicer launch");
     CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
     CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf.emu_t0,
@@ -708,6 +717,44 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   CK(h, h->d_T.ensure(t_bytes), "workspace");
   CK(h, h->d_work.ensure(t_bytes), "workspace");
   CK(h, h->d_CH.ensure(t_bytes), "workspace");
+  // emulated path with factored operands: the H operands come from the
+  // tensor-core product of conj(C^H) and W (opgemm.cu)
+  const bool tc_ops = factored && h->opt.precision == FLAPW_PREC_EMU;
+  const int op_kp = round_up(n, kChunk);
+  const int64_t op_rows_a = (int64_t)n_slots * n, op_rows_b = (int64_t)h->n_types * h->g_total;
+  if (tc_ops) {
+    CK(h, opgemm_init(), "operand kernel setup");
+    CK(h, h->d_opA.ensure((size_t)op_rows_a * op_kp * 16), "operand workspace");
+    CK(h, h->d_opB.ensure((size_t)op_rows_b * op_kp * 16), "operand workspace");
+    CK(h, h->d_opSLA.ensure((size_t)kOpSlices * 2 * op_rows_a * op_kp * 2), "operand workspace");
+    CK(h, h->d_opSLB.ensure((size_t)kOpSlices * 2 * op_rows_b * op_kp * 2), "operand workspace");
+    CK(h, h->d_oprexp.ensure((size_t)(op_rows_a + op_rows_b) * 4), "workspace");
+    std::vector<OpTile> tl;
+    const int nrb = (n + 127) / 128;
+    const int64_t ngb = (h->g_total + 63) / 64;
+    for (int c = 0; c < n_combo; ++c)
+      for (int64_t gb = 0; gb < ngb; ++gb)
+        for (int rb = 0; rb < nrb; ++rb) tl.push_back(OpTile{c, rb, (int)gb, 0});
+    if (tl.size() != h->optiles.size() || !std::equal(tl.begin(), tl.end(), h->optiles.begin(),
+                                                       [](const OpTile& x, const OpTile& y) {
+                                                         return x.combo == y.combo && x.rb == y.rb && x.gb == y.gb;
+                                                       })) {
+      if (upload(h, h->d_optiles, tl)) return FLAPW_ERR_CUDA;
+      h->optiles = tl;
+    }
+    if (h->opmap_a_base != h->d_opSLA.p || h->opmap_a_rows != op_rows_a || h->opmap_kp != op_kp ||
+        h->opmap_b_base != h->d_opSLB.p || h->opmap_b_rows != op_rows_b) {
+      std::string e;
+      if (!make_tmap_4d(&h->opmap_a, h->d_opSLA.p, op_kp, op_rows_a, kOpSlices, 128, 1, &e) ||
+          !make_tmap_4d(&h->opmap_b, h->d_opSLB.p, op_kp, op_rows_b, kOpSlices, 64, 2, &e))
+        return fail(h, FLAPW_ERR_CUDA, e);
+      h->opmap_a_base = h->d_opSLA.p;
+      h->opmap_b_base = h->d_opSLB.p;
+      h->opmap_a_rows = op_rows_a;
+      h->opmap_b_rows = op_rows_b;
+      h->opmap_kp = op_kp;
+    }
+  }
   CK(h, h->d_fac.ensure(sizeof(int) * 2 * (size_t)n_slots * n), "workspace");
   CK(h, h->d_cnt.ensure(sizeof(int) * (8 + 2 * (size_t)n_slots)), "workspace");
   CK(h, h->d_slot.ensure(slot_bytes + cmb_ints * 4 + 64), "workspace");
@@ -773,16 +820,6 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     int* kpk = neg_off + h->n_atoms;
     int* perm = h->d_fac.as<int>();
     int* outrow = perm + (size_t)n_slots * n;
-    // fork: factorisation on the auxiliary stream
-    CK(h, cudaEventRecord(h->ev[13], st), "cudaEventRecord");
-    CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev[13], 0), "cudaStreamWaitEvent");
-    CK(h, launch_tfactor(h->d_T.as<double2>(), n, n_slots, h->d_work.as<double2>(), h->d_CH.as<double2>(),
-                         perm, outrow, npos, nneg, cnt, cnt + 2, h->aux_stream),
-       "T factorisation launch");
-    CK(h, launch_layout(npos, nneg, h->d_slot.as<int>(), h->n_atoms, nk, pos_off, neg_off, kpk,
-                        h->d_probs.as<Prob>(), (int)K, h->aux_stream),
-       "layout launch");
-    CK(h, cudaEventRecord(h->ev[1], h->aux_stream), "cudaEventRecord");
     OpformArgs oa{};
     oa.n_atoms = h->n_atoms;
     oa.n_L = h->n_L;
@@ -821,15 +858,73 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     oa.combo_atoms = dc + 2 * n_combo;
     oa.combo_start = dc + 2 * n_combo + combo_atoms.size();
     oa.n_combo = n_combo;
+    // fork: factorisation on the auxiliary stream
+    CK(h, cudaEventRecord(h->ev[13], st), "cudaEventRecord");
+    CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev[13], 0), "cudaStreamWaitEvent");
+    int* oprexp_a = h->d_oprexp.as<int>();
+    int* oprexp_b = oprexp_a + op_rows_a;
+    CK(h, launch_tfactor(h->d_T.as<double2>(), n, n_slots, h->d_work.as<double2>(), h->d_CH.as<double2>(),
+                         perm, outrow, npos, nneg, cnt, cnt + 2, h->aux_stream),
+       "T factorisation launch");
+    CK(h, launch_layout(npos, nneg, h->d_slot.as<int>(), h->n_atoms, nk, pos_off, neg_off, kpk,
+                        h->d_probs.as<Prob>(), (int)K, h->aux_stream),
+       "layout launch");
+    CK(h, cudaEventRecord(h->ev[1], h->aux_stream), "cudaEventRecord");
+    if (tc_ops) {
+      CK(h, launch_opgemm_build(h->d_CH.as<double2>(), perm, n_slots, n, op_kp, nullptr, nullptr, nullptr,
+                                h->n_L, h->lmax, h->n_types, h->g_total, h->d_opA.as<double2>(), nullptr,
+                                h->aux_stream, true),
+         "operand factor launch");
+      CK(h, launch_slicer_rows(h->d_opA.as<double2>(), op_kp, op_rows_a, kOpSlices, h->d_opSLA.as<__half>(),
+                               oprexp_a, h->aux_stream),
+         "operand factor slicer launch");
+    }
+    CK(h, cudaEventRecord(h->ev[16], h->aux_stream), "cudaEventRecord");
     // S on the caller's stream, beside the factorisation (which holds n_slots SMs)
     CK(h, cudaEventRecord(h->ev[9], st), "cudaEventRecord");
+    if (tc_ops) {
+      // the W factor of the H operands needs no factorisation: formed and sliced
+      // here, it is done before the S contraction claims the SMs
+      CK(h, launch_opgemm_build(nullptr, nullptr, 0, n, op_kp, h->d_Yc.as<double2>(), h->d_al.as<double>(),
+                                h->d_bl.as<double>(), h->n_L, h->lmax, h->n_types, h->g_total, nullptr,
+                                h->d_opB.as<double2>(), st, false),
+         "operand factor launch");
+      CK(h, launch_slicer_rows(h->d_opB.as<double2>(), op_kp, op_rows_b, kOpSlices, h->d_opSLB.as<__half>(),
+                               oprexp_b, st),
+         "operand factor slicer launch");
+    }
     CK(h, launch_opform_S(oa, factored, st), "S operand launch");
     CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
     if (int rc = enqueue_contraction(h, hS, n_slots, st, 3, 4)) return rc;
     // join, then H
-    CK(h, cudaStreamWaitEvent(st, h->ev[1], 0), "cudaStreamWaitEvent");
+    CK(h, cudaStreamWaitEvent(st, h->ev[16], 0), "cudaStreamWaitEvent");
     CK(h, cudaEventRecord(h->ev[8], st), "cudaEventRecord");
-    CK(h, launch_opform_H(oa, factored, st), "H operand launch");
+    if (tc_ops) {
+      OpGemmArgs ga{};
+      ga.n = n;
+      ga.kchunks = op_kp / kChunk;
+      ga.G = h->g_total;
+      ga.combo_slot = oa.combo_slot;
+      ga.combo_type = oa.combo_type;
+      ga.combo_atoms = oa.combo_atoms;
+      ga.combo_start = oa.combo_start;
+      ga.outrow = outrow;
+      ga.npos = npos;
+      ga.pos_off = pos_off;
+      ga.neg_off = neg_off;
+      ga.kpk = kpk;
+      ga.rexp_a = oprexp_a;
+      ga.rexp_b = oprexp_b;
+      ga.ph = h->d_ph.as<double2>();
+      ga.Z = h->d_Z.as<double2>();
+      ga.k_alloc = h->k_alloc;
+      ga.h_row0 = 0;
+      CK(h, launch_opgemm(h->opmap_a, h->opmap_b, ga, h->d_optiles.as<OpTile>(), (int)h->optiles.size(),
+                          cnt + 2, h->num_sms, st),
+         "H operand launch");
+    } else {
+      CK(h, launch_opform_H(oa, factored, st), "H operand launch");
+    }
     CK(h, cudaEventRecord(h->ev[10], st), "cudaEventRecord");
     if (int rc = enqueue_contraction(h, hH, 0, st, 11, 12)) return rc;
     for (int i = 0; i < 2 * nk; ++i)
@@ -852,7 +947,9 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   std::vector<uintptr_t> key{(uintptr_t)A, (uintptr_t)B, (uintptr_t)n_slots, (uintptr_t)h->opt.precision,
                              (uintptr_t)layout, (uintptr_t)h->opt.operands, (uintptr_t)slices_of(h),
                              (uintptr_t)h->d_Z.p, (uintptr_t)h->d_SL.p, (uintptr_t)h->pin_in.p,
-                             (uintptr_t)h->d_T.p, (uintptr_t)h->d_stageOut.p, (uintptr_t)h->d_emu_tiles.p};
+                             (uintptr_t)h->d_T.p, (uintptr_t)h->d_stageOut.p, (uintptr_t)h->d_emu_tiles.p,
+                             (uintptr_t)h->d_opA.p, (uintptr_t)h->d_opB.p, (uintptr_t)h->d_opSLA.p,
+                             (uintptr_t)h->d_opSLB.p, (uintptr_t)h->d_oprexp.p, (uintptr_t)h->d_optiles.p};
   for (int k = 0; k < nk; ++k) {
     key.push_back((uintptr_t)H[k]);
     key.push_back((uintptr_t)S[k]);

@@ -19,6 +19,7 @@ constexpr int kChunk = 64;        // columns of K per pipeline step (one 128-byt
 constexpr int kSliceBits = 7;     // magnitude bits per emulation slice
 constexpr int kUnitChunks = 64;   // K chunks per unit: the longest exact FP32 accumulation
                                   // (4096 terms, digit products <= 2^12)
+constexpr int kOpSlices = 8;      // slices of the H operand formation product
 
 // One lower-triangle contraction problem: H or S of one k-point.
 struct Prob {
@@ -131,6 +132,45 @@ struct OpformArgs {
   int n_combo;
 };
 cudaError_t opform_init();
+
+// H operand formation of the emulated path on the tensor cores (opgemm.cu).
+// Tile: 128 rows of C^H (rb) x 64 plane waves (gb) of one (slot, type) combo.
+struct OpTile {
+  int combo;
+  int rb;
+  int gb;
+  int pad;
+};
+struct OpGemmArgs {
+  int n;          // rows of C^H = reduction length 2 N_L
+  int kchunks;    // padded reduction / 64 (<= 6)
+  int64_t G;      // plane waves over all k-points
+  const int* combo_slot;
+  const int* combo_type;
+  const int* combo_atoms;
+  const int* combo_start;
+  const int* outrow;   // [slot][n]
+  const int* npos;     // [slot]
+  const int* pos_off;  // [atom]
+  const int* neg_off;  // [atom]
+  const int* kpk;      // [0] = Kp_pad
+  const int* rexp_a;   // [slot * n + r]: scale exponents of the A rows
+  const int* rexp_b;   // [type * G + g]: scale exponents of the B rows
+  const double2* ph;   // [atom][G] structure-factor phases
+  double2* Z;          // operand rows (row h_row0 + g, column k')
+  int64_t k_alloc;
+  int64_t h_row0;
+};
+cudaError_t opgemm_init();
+size_t opgemm_smem_bytes();
+// build_a: A[slot n + r][perm_s(c)] = conj(C^H_s[r][c]), rows of kp columns;
+// otherwise B[t G + g][c] = W_t(c, g).  Columns n..kp-1 are zero.
+cudaError_t launch_opgemm_build(const double2* CH, const int* perm, int n_slots, int n, int kp,
+                                const double2* Yc, const double* al, const double* bl, int n_L,
+                                int lmax, int n_types, int64_t G, double2* A, double2* B,
+                                cudaStream_t st, bool build_a);
+cudaError_t launch_opgemm(const CUtensorMap& map_a, const CUtensorMap& map_b, const OpGemmArgs& g,
+                          const OpTile* tiles, int n_tiles, int* err, int max_ctas, cudaStream_t st);
 cudaError_t launch_opform_H(const OpformArgs& a, bool factored, cudaStream_t st);
 cudaError_t launch_opform_S(const OpformArgs& a, bool factored, cudaStream_t st);
 
@@ -140,9 +180,14 @@ cudaError_t launch_gather_Z(const double2* Zin, int64_t ldz, int K, int N, const
 
 // FP64 -> integer slices (fp16 carriers) with per-row power-of-two scaling.
 // Rows [row0, row0 + nrows) of the operand; `rows` is the total row count.
+// Valid K columns per row come from its problem (probs[row_prob[row]]), or
+// are [0, k_valid) when probs is null.
 cudaError_t launch_slicer(const double2* Z, int64_t k_alloc, const Prob* probs,
-                          const int* row_prob, int64_t rows, int64_t row0, int64_t nrows,
-                          int n_slices, __half* SL, int* rexp, cudaStream_t st);
+                          const int* row_prob, int64_t k_valid, int64_t rows, int64_t row0,
+                          int64_t nrows, int n_slices, __half* SL, int* rexp, cudaStream_t st);
+// The same for short rows (k_alloc <= 512): one warp per row, all columns valid.
+cudaError_t launch_slicer_rows(const double2* Z, int64_t k_alloc, int64_t rows, int n_slices,
+                               __half* SL, int* rexp, cudaStream_t st);
 
 // Contractions.
 cudaError_t launch_herk_f64(const double2* Z, int64_t k_alloc, const Prob* probs,
@@ -160,6 +205,10 @@ struct SliceMaps {
 };
 bool make_slice_tmaps(SliceMaps* maps, void* base, int64_t k_alloc, int64_t rows, int n_slices,
                       std::string* err);
+// Tensor map of one slice array [n_slices][2][rows][k_alloc] (fp16), 128-byte
+// swizzle, boxes of 64 k x box_rows rows x box_planes planes.
+bool make_tmap_4d(CUtensorMap* map, void* base, int64_t k_alloc, int64_t rows, int n_slices,
+                  uint32_t box_rows, uint32_t box_planes, std::string* err);
 // Kernel attributes and the co-resident CTA-pair count of the current device
 // (host side; call outside stream capture before the first launch).
 cudaError_t herk_emu_init();

@@ -49,10 +49,12 @@
 #include <cstdint>
 #include <mutex>
 
-#include "flapw_internal.h"
+#include "tc_common.cuh"
 
 namespace flapw {
 namespace {
+
+using namespace tc;
 
 constexpr int kStages = 3;
 constexpr int kThreads = 320;
@@ -62,7 +64,6 @@ constexpr uint32_t kTileB = 128 * 128;                   // this CTA's B half: <
 constexpr uint32_t kOffB = kStageChunks * kTileA;        // B after both A chunks
 constexpr uint32_t kStageBytes = kStageChunks * (kTileA + kTileB);
 constexpr uint32_t kTmemCols = 512;
-constexpr unsigned long long kWaitNs = 4000000000ull;    // 4 s
 constexpr int kMaxS = 8;
 constexpr int kPassChunks = 32;                          // longest K sub-span of a pass
 constexpr int kMaxDevices = 64;
@@ -72,16 +73,6 @@ constexpr uint32_t kIdesc256 = (1u << 4) | (0u << 7) | (0u << 10) | ((256u >> 3)
                                ((256u >> 4) << 24);
 constexpr uint32_t kIdesc128 = (1u << 4) | (0u << 7) | (0u << 10) | ((128u >> 3) << 17) |
                                ((256u >> 4) << 24);
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -99,62 +90,6 @@ __device__ __forceinline__ void cluster_sync() {
                "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-// Arrive on a barrier given by its cluster address (either CTA of the pair).
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cbar) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cbar)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Abort flags: one per CTA.  A role that gives up raises both CTAs' flags.
-struct Abort {
-  volatile int* local;
-  uint32_t peer;  // cluster address of the other CTA's flag
-  __device__ void raise() const {
-    *local = 1;
-    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer), "r"(1) : "memory");
-  }
-};
-
-// Bounded wait.  Returns false if the wall-clock limit passed or another role
-// aborted; the first role to time out raises the abort flags.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const Abort& ab) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63) == 0) {
-      if (*ab.local) return false;
-      if (global_ns() - t0 > kWaitNs) {
-        ab.raise();
-        return false;
-      }
-    }
-  }
-}
-// Wait that ignores the abort flags (teardown), still bounded.
-__device__ __forceinline__ void mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  const unsigned long long t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > kWaitNs) break;
-}
-
 // TMA tile load into this CTA's shared memory, completion counted on a
 // barrier of either CTA of the pair (cluster address).
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t cbar,
@@ -164,16 +99,6 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
       " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(cbar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
       : "memory");
-}
-
-// K-major, 128-byte-swizzled operand: 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
-  d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // 128-byte swizzle
-  return d;
 }
 
 // One pair MMA: A rows from both CTAs (128 each), B halves from both CTAs,
@@ -193,53 +118,6 @@ __device__ __forceinline__ void umma_commit_both(uint32_t bar) {
       " [%0], %1;" ::"r"(bar), "h"((uint16_t)3)
       : "memory");
 }
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                 "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-}
-// tcgen05.wait::ld that also marks the loaded registers as written here, so
-// the compiler cannot read them before the wait.
-__device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&r)[8]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
-                 "+r"(r[6]), "+r"(r[7])
-               :
-               : "memory");
-}
-
-// Adds f(v) for the integer values v of 64 consecutive TMEM columns (this
-// thread's lane) to acc[0..63].  The next 8 columns load while the current 8
-// are converted.
-template <class F>
-__device__ __forceinline__ void drain64(uint32_t tb, long long (&acc)[64], F f) {
-  uint32_t xa[8], xb[8];
-  tmem_ld8(tb, xa);
-  tmem_wait_ld_regs(xa);
-#pragma unroll
-  for (int cb = 0; cb < 8; ++cb) {
-    if (cb & 1) {
-      if (cb < 7) tmem_ld8(tb + 8u * (cb + 1), xa);
-#pragma unroll
-      for (int e = 0; e < 8; ++e) acc[8 * cb + e] += f(__float2int_rn(__uint_as_float(xb[e])));
-      if (cb < 7) tmem_wait_ld_regs(xa);
-    } else {
-      if (cb < 7) tmem_ld8(tb + 8u * (cb + 1), xb);
-#pragma unroll
-      for (int e = 0; e < 8; ++e) acc[8 * cb + e] += f(__float2int_rn(__uint_as_float(xa[e])));
-      if (cb < 7) tmem_wait_ld_regs(xb);
-    }
-  }
-}
-
 // Slice pairs (i, j), 0-based, are visited by level: t = i + j = 0..s-1
 // (i.e. 1-based levels i + j + 2 <= s + 1), i = 0..t.  Every role walks the
 // same order.
@@ -388,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   cluster_sync();  // barriers initialised and TMEM allocated in both CTAs
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const Abort ab{abort_word, map_to_rank(smem_u32(abort_word), rank ^ 1u)};
+  const Abort ab{abort_word, map_to_rank(smem_u32(abort_word), rank ^ 1u), true};
 
   if (warp == 0) {
     // ---------------- TMA producer (both CTAs) ----------------
@@ -520,18 +398,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int sh = frac - kSliceBits * (sc.i + sc.j + pq + 2);
           const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * 256u +
                               (uint32_t)pq * 128u + col;
-          if (sh >= 0) {
-            // +-v 2^sh as one 32 x 32 -> 64-bit multiply-add; a shift past 30
-            // is applied to v first (|v| <= 2^24 and sh - 30 <= 6)
-            const int pre = sh > 30 ? sh - 30 : 0;
-            const int mul = sub ? -(1 << (sh - pre)) : (1 << (sh - pre));
-            if (pre == 0) drain64(tb, acc, [=](int v) { return (long long)v * mul; });
-            else drain64(tb, acc, [=](int v) { return (long long)(v << pre) * mul; });
-          } else {
-            // below the fixed point: round the signed value half up
-            const int rs = -sh, half = 1 << (-sh - 1);
-            drain64(tb, acc, [=](int v) { return (long long)(((sub ? -v : v) + half) >> rs); });
-          }
+          drain_fixed<64>(tb, acc, 0, sh, sub);
         }
         tc_fence_before();
         __syncwarp();
@@ -657,10 +524,8 @@ cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuT
   return cudaGetLastError();
 }
 
-// Tensor maps over SL[slice][plane][row][k] (fp16), 128-byte swizzle, boxes of
-// 64 k by: 128 rows (a), 64 rows x 2 planes (b2), 64 rows (b1).
-bool make_slice_tmaps(SliceMaps* maps, void* base, int64_t k_alloc, int64_t rows, int n_slices,
-                      std::string* err) {
+bool make_tmap_4d(CUtensorMap* map, void* base, int64_t k_alloc, int64_t rows, int n_slices,
+                  uint32_t box_rows, uint32_t box_planes, std::string* err) {
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -681,18 +546,24 @@ bool make_slice_tmaps(SliceMaps* maps, void* base, int64_t k_alloc, int64_t rows
   const cuuint64_t strides[3] = {(cuuint64_t)k_alloc * 2, (cuuint64_t)(rows * k_alloc * 2),
                                  (cuuint64_t)(2 * rows * k_alloc * 2)};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const cuuint32_t boxes[3][4] = {{64, 128, 1, 1}, {64, 64, 2, 1}, {64, 64, 1, 1}};
-  CUtensorMap* out[3] = {&maps->a, &maps->b2, &maps->b1};
-  for (int t = 0; t < 3; ++t) {
-    CUresult r = fn(out[t], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, base, dims, strides, boxes[t], estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-      *err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
-      return false;
-    }
+  const cuuint32_t box[4] = {64, box_rows, box_planes, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    *err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+    return false;
   }
   return true;
+}
+
+// Tensor maps over SL[slice][plane][row][k] (fp16), 128-byte swizzle, boxes of
+// 64 k by: 128 rows (a), 64 rows x 2 planes (b2), 64 rows (b1).
+bool make_slice_tmaps(SliceMaps* maps, void* base, int64_t k_alloc, int64_t rows, int n_slices,
+                      std::string* err) {
+  return make_tmap_4d(&maps->a, base, k_alloc, rows, n_slices, 128, 1, err) &&
+         make_tmap_4d(&maps->b2, base, k_alloc, rows, n_slices, 64, 2, err) &&
+         make_tmap_4d(&maps->b1, base, k_alloc, rows, n_slices, 64, 1, err);
 }
 
 }  // namespace flapw

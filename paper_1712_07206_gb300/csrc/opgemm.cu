@@ -1,0 +1,398 @@
+// H operand formation of the emulated path on the tensor cores (factored
+// operands).
+//
+// For every (T slot s, atom type t) combination present the row block of the
+// Hamiltonian operand (Sec. 3: Z_a = C^H [A_a; B_a], 2N_L rows per atom) is
+//     P_{s,t}(r, g) = sum_c C^H_s(r, c) W_t(perm_s(c), g),
+// W_t = [A_t; B_t] the type's matching coefficients without the atom phase,
+// and Z_a = P_{slot(a),type(a)} diag(e^{i K.tau_a}) lands in atom a's
+// sigma-grouped operand rows.  The product uses the split-precision scheme of
+// the contraction on operands of its own:
+//     A(r, c') = conj(C^H_s(r, c)) with c' = perm_s(c)     (rows r, k = c')
+//     B(g, c') = W_t(c', g)                                  (rows g, k = c')
+// both cut into kOpSlices = 8 digit slices with per-row scaling (slicer.cu),
+// so that the contraction's complex combination conj(A)^T B gives C^H W.
+// With 8 slices the dropped pairs (i + j >= 8) weigh below 2^-53 of the
+// scaled product, about FP64 rounding.
+//
+// The reduction is short, K = 2N_L <= 384 (lmax <= 12), so all slice pairs of
+// one level t = i + j sum exactly in one FP32 TMEM accumulator: a term of
+// level t is at most 2 x 2^13 + (t - 1) x 2^12 (only the pairs (0, t), (t, 0)
+// hold a leading digit; (0, 0) alone is 2^14), and 384 x (2^14 + 6 x 2^12) <
+// 2^24.  A tile so takes 2 x kOpSlices accumulations (an R and an I pass per
+// level) instead of one per slice pair, each drained into the 64-bit
+// fixed-point accumulators as in the contraction.
+//
+// CTA tile: 128 rows r x 64 plane waves g; M = 128, N = 128 MMAs (cta_group::1)
+// with B = [Re W_j; Im W_j] for the 64 plane waves; 128-wide K stages (two
+// 64-wide chunks of any slice pair of the current level).  Four 128-column
+// TMEM accumulators rotate over the (level, pass) steps.  Warp roles: 0 TMA
+// producer, 1 TMEM allocator and MMA issuer, 2..9 drain and epilogue (warp w
+// reads TMEM lanes 32 (w % 4)..+31 and owns plane waves 32 ((w - 2) / 4)..+31
+// of the tile, Re and Im).  Every wait is bounded; on expiry the CTA records
+// an error, lets its copies and MMAs complete, frees TMEM and exits.
+#include <algorithm>
+#include <cstdint>
+
+#include "tc_common.cuh"
+
+namespace flapw {
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 320;
+constexpr int kStages = 3;
+constexpr int kStageChunks = 2;
+constexpr uint32_t kTileA = 128 * 128;  // 128 rows x 64 k fp16
+constexpr uint32_t kTileB = 128 * 128;  // Re and Im planes x 64 plane waves x 64 k
+constexpr uint32_t kOffB = kStageChunks * kTileA;
+constexpr uint32_t kStageBytes = kStageChunks * (kTileA + kTileB);
+constexpr int kBufs = 4;                // TMEM accumulators of 128 columns
+constexpr uint32_t kTmemCols = 512;
+constexpr int kMaxKChunks = 6;          // K = 2 N_L <= 384
+constexpr int kFrac = 50;               // fixed-point fraction bits (sums < 2 x 384)
+
+// D = F32, A = B = F16, K-major, M = 128, N = 128
+constexpr uint32_t kIdesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+// The (level t, pass p) steps of a tile, each the chunk sequence q =
+// i * kc + c (slice pair (i, t - i), 64-wide K chunk c), cut into stages of
+// two chunks.  Every role walks the same order.
+struct OpCursor {
+  int kc, t, p, q, nq;
+  __device__ void begin(int kchunks) {
+    kc = kchunks;
+    t = 0;
+    p = 0;
+    q = 0;
+    nq = kc;
+  }
+  __device__ int nv() const { return min(kStageChunks, nq - q); }
+  __device__ bool last_in_step() const { return q + kStageChunks >= nq; }
+  __device__ bool next_stage() {
+    q += kStageChunks;
+    if (q < nq) return true;
+    q = 0;
+    if (++p == 2) {
+      p = 0;
+      if (++t >= kOpSlices) return false;
+    }
+    nq = (t + 1) * kc;
+    return true;
+  }
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    opgemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                  const OpGemmArgs g, const OpTile* __restrict__ tiles, int n_tiles,
+                  int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  // bars: full[kStages], empty[kStages], tfull[kBufs], tempty[kBufs], drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16);
+  int* abort_word = reinterpret_cast<int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * kStages + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * kStages + kBufs + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 2 * kBufs);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < kBufs; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), 8);  // one arrival per drain warp
+    }
+    mbar_init(drain_bar, 1);
+    *abort_word = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const Abort ab{abort_word, 0u, false};
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const OpTile T = tiles[tile];
+        const int rowA = g.combo_slot[T.combo] * g.n + T.rb * 128;
+        const int rowB = (int)(g.combo_type[T.combo] * g.G) + T.gb * 64;
+        OpCursor cur;
+        cur.begin(g.kchunks);
+        do {
+          const int nv = cur.nv();
+          const int stage = it % kStages;
+          if (!mbar_wait(empty_bar(stage), ((it / kStages) & 1u) ^ 1u, ab)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
+          const uint32_t fb = full_bar(stage);
+          mbar_expect_tx(fb, (uint32_t)nv * (kTileA + kTileB));
+          for (int v = 0; v < nv; ++v) {
+            const int qq = cur.q + v, i = qq / cur.kc, kc = (qq % cur.kc) * kChunk;
+            tma_load_4d(sbase + v * kTileA, &map_a, fb, kc, rowA, cur.p, i);
+            tma_load_4d(sbase + kOffB + v * kTileB, &map_b, fb, kc, rowB, 0, cur.t - i);
+          }
+          ++it;
+        } while (cur.next_stage());
+      }
+      if (!ok) {
+        for (uint32_t q = (it > kStages ? it - kStages : 0); q < it; ++q)
+          mbar_wait_bounded(full_bar(q % kStages), (q / kStages) & 1u);
+        atomicExch(err, FLAPW_ERR_TIMEOUT);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t it = 0, step = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        OpCursor cur;
+        cur.begin(g.kchunks);
+        uint32_t d = 0;
+        int buf = 0;
+        do {
+          if (cur.q == 0) {
+            buf = step % kBufs;
+            if (!mbar_wait(tempty_bar(buf), ((step / kBufs) & 1u) ^ 1u, ab)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            d = tmem_base + (uint32_t)buf * 128u;
+          }
+          const int stage = it % kStages;
+          if (!mbar_wait(full_bar(stage), (it / kStages) & 1u, ab)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
+          const int nv = cur.nv();
+          for (int v = 0; v < nv; ++v) {
+            const uint64_t da = sdesc(sbase + v * kTileA), db = sdesc(sbase + kOffB + v * kTileB);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              umma(d, da + 2 * kk, db + 2 * kk, (cur.q > 0 || v > 0 || kk > 0) ? 1u : 0u);
+          }
+          umma_commit(empty_bar(stage));
+          ++it;
+          if (cur.last_in_step()) {
+            umma_commit(tfull_bar(buf));
+            ++step;
+          }
+        } while (cur.next_stage());
+      }
+      umma_commit(drain_bar);
+      mbar_wait_bounded(drain_bar, 0);
+      if (!ok) atomicExch(err, FLAPW_ERR_TIMEOUT);
+    }
+  } else {
+    // ---------------- drain + epilogue ----------------
+    const int q4 = warp & 3;          // TMEM lane quadrant
+    const int hc = (warp - 2) >> 2;   // plane waves 32 hc .. 32 hc + 31 of the tile
+    uint32_t step = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      const OpTile T = tiles[tile];
+      long long acc[64];  // [0, 32): Re, [32, 64): Im
+#pragma unroll
+      for (int n = 0; n < 64; ++n) acc[n] = 0;
+      for (int t = 0; t < kOpSlices && ok; ++t) {
+        const int sh = kFrac - kSliceBits * (t + 2);
+        for (int p = 0; p < 2; ++p) {
+          const int buf = step % kBufs;
+          if (!mbar_wait(tfull_bar(buf), (step / kBufs) & 1u, ab)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          __syncwarp();
+          const uint32_t tb = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)buf * 128u +
+                              (uint32_t)hc * 32u;
+          // accumulator columns: [0, 64) A_p x Re W, [64, 128) A_p x Im W
+          // R pass: Re += RR, Im += RI;  I pass: Re += II, Im -= IR
+          if (p == 0) {
+            drain_fixed<32>(tb, acc, 0, sh, false);
+            drain_fixed<32>(tb + 64u, acc, 32, sh, false);
+          } else {
+            drain_fixed<32>(tb + 64u, acc, 0, sh, false);
+            drain_fixed<32>(tb, acc, 32, sh, true);
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty_bar(buf));
+          ++step;
+        }
+      }
+      if (!ok) break;
+      const int slot = g.combo_slot[T.combo], type = g.combo_type[T.combo];
+      const int r = T.rb * 128 + q4 * 32 + lane;
+      if (r >= g.n) continue;
+      const int rr = g.outrow[slot * g.n + r];  // sigma-grouped position
+      if (rr < 0) continue;                     // zero pivot: the row carries nothing
+      const int np = g.npos[slot];
+      const int er = g.rexp_a[slot * g.n + r];
+      const int a0 = g.combo_start[T.combo], a1 = g.combo_start[T.combo + 1];
+#pragma unroll
+      for (int n = 0; n < 32; ++n) {
+        const int64_t gi = (int64_t)T.gb * 64 + hc * 32 + n;
+        if (gi < g.G) {
+          const int ex = er + g.rexp_b[type * g.G + gi] - kFrac;
+          const double pr = ldexp((double)acc[n], ex), pi = ldexp((double)acc[32 + n], ex);
+          double2* zrow = g.Z + (g.h_row0 + gi) * g.k_alloc;
+          for (int ai = a0; ai < a1; ++ai) {
+            const int a = g.combo_atoms[ai];
+            const int col = (rr < np) ? g.pos_off[a] + rr : g.kpk[0] + g.neg_off[a] + (rr - np);
+            const double2 f = g.ph[(int64_t)a * g.G + gi];
+            zrow[col] = make_double2(f.x * pr - f.y * pi, f.x * pi + f.y * pr);
+          }
+        }
+      }
+    }
+    if (!ok) atomicExch(err, FLAPW_ERR_TIMEOUT);
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+// A(slot n + r, perm_s(c)) = conj(C^H_s(r, c)); columns n..kp-1 zero.
+// grid: n_slots * n rows.
+__global__ void __launch_bounds__(128) opgemm_build_a_kernel(const double2* __restrict__ CH,
+                                                             const int* __restrict__ perm, int n,
+                                                             int kp, double2* __restrict__ A) {
+  const int row = blockIdx.x, slot = row / n, r = row % n;
+  const double2* src = CH + ((int64_t)slot * n + r) * n;
+  const int* pm = perm + (int64_t)slot * n;
+  double2* dst = A + (int64_t)row * kp;
+  for (int c = threadIdx.x; c < kp; c += blockDim.x) {
+    if (c < n) {
+      const double2 v = src[c];
+      dst[pm[c]] = make_double2(v.x, -v.y);
+    } else {
+      dst[c] = make_double2(0.0, 0.0);
+    }
+  }
+}
+
+// B(t G + gi, c) = W_t(c, gi) = [Yc(L, gi) a_l(t, gi); Yc(L, gi) b_l(t, gi)];
+// columns n..kp-1 zero.  A 32 plane-wave x 32 column tile per CTA goes
+// through shared memory so that both the reads (plane waves contiguous) and
+// the writes (columns contiguous) are coalesced.  grid: (ceil(G/32),
+// ceil(kp/32), n_types), 32 x 8 threads.
+__global__ void __launch_bounds__(256) opgemm_build_b_kernel(const double2* __restrict__ Yc,
+                                                             const double* __restrict__ al,
+                                                             const double* __restrict__ bl,
+                                                             int n_L, int lmax, int n, int kp,
+                                                             int64_t G, double2* __restrict__ B) {
+  __shared__ double2 tile[32][33];
+  const int t = blockIdx.z;
+  const int64_t g0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int cc = ty; cc < 32; cc += 8) {
+    const int c = c0 + cc;
+    const int64_t gi = g0 + tx;
+    double2 w = make_double2(0.0, 0.0);
+    if (c < n && gi < G) {
+      const int L = (c < n_L) ? c : c - n_L;
+      int l = 0;  // L = l^2 + (l + m)
+      while ((l + 1) * (l + 1) <= L) ++l;
+      const double2 y = Yc[(int64_t)L * G + gi];
+      const int64_t ro = ((int64_t)t * (lmax + 1) + l) * G + gi;
+      const double rad = (c < n_L) ? al[ro] : bl[ro];
+      w = make_double2(y.x * rad, y.y * rad);
+    }
+    tile[tx][cc] = w;
+  }
+  __syncthreads();
+  for (int gg = ty; gg < 32; gg += 8) {
+    const int64_t gi = g0 + gg;
+    const int c = c0 + tx;
+    if (gi < G && c < kp) B[((int64_t)t * G + gi) * kp + c] = tile[gg][tx];
+  }
+}
+
+}  // namespace
+
+size_t opgemm_smem_bytes() { return kStages * kStageBytes + 1024 + 256; }
+
+cudaError_t opgemm_init() {
+  return cudaFuncSetAttribute(opgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)opgemm_smem_bytes());
+}
+
+cudaError_t launch_opgemm_build(const double2* CH, const int* perm, int n_slots, int n, int kp,
+                                const double2* Yc, const double* al, const double* bl,
+                                int n_L, int lmax, int n_types, int64_t G,
+                                double2* A, double2* B, cudaStream_t st, bool build_a) {
+  if (build_a) {
+    if (n_slots * n > 0) opgemm_build_a_kernel<<<n_slots * n, 128, 0, st>>>(CH, perm, n, kp, A);
+  } else if (G > 0 && n_types > 0) {
+    dim3 grid((unsigned)((G + 31) / 32), (unsigned)((kp + 31) / 32), (unsigned)n_types);
+    opgemm_build_b_kernel<<<grid, 256, 0, st>>>(Yc, al, bl, n_L, lmax, n, kp, G, B);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_opgemm(const CUtensorMap& map_a, const CUtensorMap& map_b, const OpGemmArgs& g,
+                          const OpTile* tiles, int n_tiles, int* err, int max_ctas, cudaStream_t st) {
+  if (n_tiles == 0) return cudaSuccess;
+  if (g.kchunks < 1 || g.kchunks > kMaxKChunks) return cudaErrorInvalidValue;
+  const int grid = std::max(1, std::min(n_tiles, max_ctas));
+  opgemm_kernel<<<grid, kThreads, opgemm_smem_bytes(), st>>>(map_a, map_b, g, tiles, n_tiles, err);
+  return cudaGetLastError();
+}
+
+}  // namespace flapw

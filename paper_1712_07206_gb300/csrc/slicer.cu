@@ -14,6 +14,7 @@
 //
 // Output layout: SL[slice][plane][row][k], k contiguous, fp16; plane 0 = Re,
 // 1 = Im.  Columns outside the problem's valid K ranges are written as 0.
+// Without a problem table every row's valid range is [0, k_valid).
 #include <cstdint>
 
 #include "flapw_internal.h"
@@ -45,13 +46,17 @@ __device__ __forceinline__ long long fixed_point(double x, int shift0) {
 template <int NS>
 __global__ void __launch_bounds__(256) slicer_kernel(const double2* __restrict__ Z, int64_t k_alloc,
                                                      const Prob* __restrict__ probs,
-                                                     const int* __restrict__ row_prob, int64_t rows,
-                                                     int64_t row0, __half* __restrict__ SL,
-                                                     int* __restrict__ rexp) {
+                                                     const int* __restrict__ row_prob, int64_t k_valid,
+                                                     int64_t rows, int64_t row0,
+                                                     __half* __restrict__ SL, int* __restrict__ rexp) {
   __shared__ unsigned long long red[8];
   const int64_t row = row0 + blockIdx.x;
-  const Prob P = probs[row_prob[row]];
-  const int64_t kp = P.kp, kn = P.kn;
+  int64_t kp = k_valid, kn = 0;
+  if (probs) {
+    const Prob P = probs[row_prob[row]];
+    kp = P.kp;
+    kn = P.kn;
+  }
   const int64_t kp_pad = (kp + kChunk - 1) / kChunk * kChunk;
   const double2* zr = Z + row * k_alloc;
   auto valid = [&](int64_t c) { return c < kp || (c >= kp_pad && c < kp_pad + kn); };
@@ -113,17 +118,71 @@ __global__ void __launch_bounds__(256) slicer_kernel(const double2* __restrict__
   }
 }
 
+// One warp per row of at most 512 columns (all valid); 8 rows per CTA.
+template <int NS>
+__global__ void __launch_bounds__(256) slicer_rows_kernel(const double2* __restrict__ Z,
+                                                          int64_t k_alloc, int64_t rows,
+                                                          __half* __restrict__ SL,
+                                                          int* __restrict__ rexp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (row >= rows) return;
+  const double2* zr = Z + row * k_alloc;
+  unsigned long long m = 0;
+  for (int64_t c = lane; c < k_alloc; c += 32) {
+    const double2 z = zr[c];
+    const unsigned long long a = absbits(z.x), b = absbits(z.y);
+    m = a > m ? a : m;
+    m = b > m ? b : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  const int e = (m == 0) ? 0 : (int)((m >> 52) & 0x7FF) - 1022;  // max < 2^e
+  if (lane == 0) rexp[row] = e;
+  const int shift0 = kSliceBits * NS - e;
+  const int64_t plane_stride = rows * k_alloc;
+  for (int64_t c0 = (int64_t)lane * 8; c0 < k_alloc; c0 += 256) {
+    double2 z[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) z[q] = zr[c0 + q];
+#pragma unroll
+    for (int plane = 0; plane < 2; ++plane) {
+      __align__(16) __half d[NS][8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        long long X = fixed_point(plane ? z[q].y : z[q].x, shift0);
+#pragma unroll
+        for (int i = NS - 1; i >= 1; --i) {
+          const long long di = ((X + 64) & 127) - 64;
+          d[i][q] = __ll2half_rn(di);
+          X = (X - di) >> kSliceBits;
+        }
+        d[0][q] = __ll2half_rn(X);
+      }
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        __half* dst = SL + ((int64_t)(2 * i + plane)) * plane_stride + row * k_alloc + c0;
+        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(d[i]);
+      }
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_slicer(const double2* Z, int64_t k_alloc, const Prob* probs,
-                          const int* row_prob, int64_t rows, int64_t row0, int64_t nrows,
-                          int n_slices, __half* SL, int* rexp, cudaStream_t st) {
+                          const int* row_prob, int64_t k_valid, int64_t rows, int64_t row0,
+                          int64_t nrows, int n_slices, __half* SL, int* rexp, cudaStream_t st) {
   if (nrows == 0) return cudaSuccess;
   const unsigned grid = (unsigned)nrows;
   switch (n_slices) {
 #define FLAPW_SLICER_CASE(NS)                                                                    \
   case NS:                                                                                       \
-    slicer_kernel<NS><<<grid, 256, 0, st>>>(Z, k_alloc, probs, row_prob, rows, row0, SL, rexp); \
+    slicer_kernel<NS><<<grid, 256, 0, st>>>(Z, k_alloc, probs, row_prob, k_valid, rows, row0, SL, \
+                                            rexp);                                                \
     break;
     FLAPW_SLICER_CASE(4)
     FLAPW_SLICER_CASE(5)
@@ -133,6 +192,22 @@ cudaError_t launch_slicer(const double2* Z, int64_t k_alloc, const Prob* probs,
 #undef FLAPW_SLICER_CASE
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+}  // namespace flapw
+
+namespace flapw {
+
+cudaError_t launch_slicer_rows(const double2* Z, int64_t k_alloc, int64_t rows, int n_slices,
+                               __half* SL, int* rexp, cudaStream_t st) {
+  if (rows == 0) return cudaSuccess;
+  if (k_alloc % 8 != 0 || k_alloc > 512) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)((rows + 7) / 8);
+  if (n_slices == kOpSlices)
+    slicer_rows_kernel<kOpSlices><<<grid, 256, 0, st>>>(Z, k_alloc, rows, SL, rexp);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
