@@ -268,9 +268,9 @@ def run_ours(args):
         "e2e": e2e,
         # per step: ab_prep, ab_assemble, tfactor, layout, opform_S, slicer and
         # contraction for the S half and for the H half, and the H operands:
-        # with factored operands W and conj(C^H) formed and sliced (4 kernels)
-        # and their tensor-core product, else opform_H
-        "gpu_launches": (14 if args.operands == "factored" else 10) * args.steps,
+        # with factored operands W and conj(C^H) formed and sliced (4 kernels),
+        # their tensor-core product and the per-atom phases, else opform_H
+        "gpu_launches": (15 if args.operands == "factored" else 10) * args.steps,
         "clocks": clk,
         "timed_wall_s": round(t_wall, 3),
     }

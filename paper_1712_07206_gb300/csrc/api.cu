@@ -117,7 +117,7 @@ struct flapw_ctx {
   // build_HS workspaces
   // H operands on the tensor cores (emulated path, factored operands): the two
   // factors in FP64 and sliced, their scale exponents, tiles and tensor maps
-  DevBuf d_opA, d_opB, d_opSLA, d_opSLB, d_oprexp, d_optiles;
+  DevBuf d_opA, d_opB, d_opSLA, d_opSLB, d_oprexp, d_optiles, d_opP;
   std::vector<OpTile> optiles;
   CUtensorMap opmap_a{}, opmap_b{};
   void* opmap_a_base = nullptr;
@@ -729,6 +729,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     CK(h, h->d_opSLA.ensure((size_t)kOpSlices * 2 * op_rows_a * op_kp * 2), "operand workspace");
     CK(h, h->d_opSLB.ensure((size_t)kOpSlices * 2 * op_rows_b * op_kp * 2), "operand workspace");
     CK(h, h->d_oprexp.ensure((size_t)(op_rows_a + op_rows_b) * 4), "workspace");
+    CK(h, h->d_opP.ensure((size_t)n_combo * h->g_total * n * 16), "operand workspace");
     std::vector<OpTile> tl;
     const int nrb = (n + 127) / 128;
     const int64_t ngb = (h->g_total + 63) / 64;
@@ -916,12 +917,14 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       ga.rexp_a = oprexp_a;
       ga.rexp_b = oprexp_b;
       ga.ph = h->d_ph.as<double2>();
+      ga.P = h->d_opP.as<longlong2>();
       ga.Z = h->d_Z.as<double2>();
       ga.k_alloc = h->k_alloc;
       ga.h_row0 = 0;
       CK(h, launch_opgemm(h->opmap_a, h->opmap_b, ga, h->d_optiles.as<OpTile>(), (int)h->optiles.size(),
                           cnt + 2, h->num_sms, st),
          "H operand launch");
+      CK(h, launch_opgemm_phase(ga, n_combo, st), "H operand phase launch");
     } else {
       CK(h, launch_opform_H(oa, factored, st), "H operand launch");
     }
@@ -949,7 +952,8 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
                              (uintptr_t)h->d_Z.p, (uintptr_t)h->d_SL.p, (uintptr_t)h->pin_in.p,
                              (uintptr_t)h->d_T.p, (uintptr_t)h->d_stageOut.p, (uintptr_t)h->d_emu_tiles.p,
                              (uintptr_t)h->d_opA.p, (uintptr_t)h->d_opB.p, (uintptr_t)h->d_opSLA.p,
-                             (uintptr_t)h->d_opSLB.p, (uintptr_t)h->d_oprexp.p, (uintptr_t)h->d_optiles.p};
+                             (uintptr_t)h->d_opSLB.p, (uintptr_t)h->d_oprexp.p, (uintptr_t)h->d_optiles.p,
+                             (uintptr_t)h->d_opP.p};
   for (int k = 0; k < nk; ++k) {
     key.push_back((uintptr_t)H[k]);
     key.push_back((uintptr_t)S[k]);

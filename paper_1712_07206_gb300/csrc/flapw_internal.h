@@ -157,6 +157,7 @@ struct OpGemmArgs {
   const int* rexp_a;   // [slot * n + r]: scale exponents of the A rows
   const int* rexp_b;   // [type * G + g]: scale exponents of the B rows
   const double2* ph;   // [atom][G] structure-factor phases
+  longlong2* P;        // [combo][G][n] fixed-point product (Re, Im)
   double2* Z;          // operand rows (row h_row0 + g, column k')
   int64_t k_alloc;
   int64_t h_row0;
@@ -169,8 +170,10 @@ cudaError_t launch_opgemm_build(const double2* CH, const int* perm, int n_slots,
                                 const double2* Yc, const double* al, const double* bl, int n_L,
                                 int lmax, int n_types, int64_t G, double2* A, double2* B,
                                 cudaStream_t st, bool build_a);
+// P for every tile (opgemm.cu), then every atom's operand rows from P.
 cudaError_t launch_opgemm(const CUtensorMap& map_a, const CUtensorMap& map_b, const OpGemmArgs& g,
                           const OpTile* tiles, int n_tiles, int* err, int max_ctas, cudaStream_t st);
+cudaError_t launch_opgemm_phase(const OpGemmArgs& g, int n_combo, cudaStream_t st);
 cudaError_t launch_opform_H(const OpformArgs& a, bool factored, cudaStream_t st);
 cudaError_t launch_opform_S(const OpformArgs& a, bool factored, cudaStream_t st);
 

@@ -49,6 +49,7 @@
 #include <cstdint>
 #include <mutex>
 
+#include "fixed64.cuh"
 #include "tc_common.cuh"
 
 namespace flapw {
@@ -416,9 +417,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int n = 0; n < 64; ++n) {
           const int64_t gc = (int64_t)T.jb * 64 + n;
           if (gc < ng && gc <= gr) {
-            const int ex = er + rexp[P.row_base + gc] - frac;
-            const double scale = __longlong_as_double((long long)(ex + 1023) << 52);
-            const double val = (double)acc[n] * scale;
+            const double val = fx::to_double(acc[n], er + rexp[P.row_base + gc] - frac);
             const int64_t o = (P.layout == FLAPW_LAYOUT_LOWER_PACKED)
                                   ? gc * ng - gc * (gc - 1) / 2 + (gr - gc)
                                   : gc * P.ld + gr;

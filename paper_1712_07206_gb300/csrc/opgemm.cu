@@ -23,6 +23,10 @@
 // level) instead of one per slice pair, each drained into the 64-bit
 // fixed-point accumulators as in the contraction.
 //
+// The tiles leave P in fixed point (64-bit integers with the scale exponents
+// of its row and plane wave, [combo][g][r]); opgemm_phase_kernel then writes
+// every atom's operand rows with the atom's phase, on the integer pipes.
+//
 // CTA tile: 128 rows r x 64 plane waves g; M = 128, N = 128 MMAs (cta_group::1)
 // with B = [Re W_j; Im W_j] for the 64 plane waves; 128-wide K stages (two
 // 64-wide chunks of any slice pair of the current level).  Four 128-column
@@ -34,6 +38,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "fixed64.cuh"
 #include "tc_common.cuh"
 
 namespace flapw {
@@ -269,28 +274,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (!ok) break;
-      const int slot = g.combo_slot[T.combo], type = g.combo_type[T.combo];
+      // P(r, g) in fixed point, scale 2^(e_r + e_g - kFrac): [combo][g][r]
       const int r = T.rb * 128 + q4 * 32 + lane;
-      if (r >= g.n) continue;
-      const int rr = g.outrow[slot * g.n + r];  // sigma-grouped position
-      if (rr < 0) continue;                     // zero pivot: the row carries nothing
-      const int np = g.npos[slot];
-      const int er = g.rexp_a[slot * g.n + r];
-      const int a0 = g.combo_start[T.combo], a1 = g.combo_start[T.combo + 1];
+      if (r < g.n) {
+        const int64_t gi0 = (int64_t)T.gb * 64 + hc * 32;
+        longlong2* prow = g.P + ((int64_t)T.combo * g.G + gi0) * g.n + r;
 #pragma unroll
-      for (int n = 0; n < 32; ++n) {
-        const int64_t gi = (int64_t)T.gb * 64 + hc * 32 + n;
-        if (gi < g.G) {
-          const int ex = er + g.rexp_b[type * g.G + gi] - kFrac;
-          const double pr = ldexp((double)acc[n], ex), pi = ldexp((double)acc[32 + n], ex);
-          double2* zrow = g.Z + (g.h_row0 + gi) * g.k_alloc;
-          for (int ai = a0; ai < a1; ++ai) {
-            const int a = g.combo_atoms[ai];
-            const int col = (rr < np) ? g.pos_off[a] + rr : g.kpk[0] + g.neg_off[a] + (rr - np);
-            const double2 f = g.ph[(int64_t)a * g.G + gi];
-            zrow[col] = make_double2(f.x * pr - f.y * pi, f.x * pi + f.y * pr);
-          }
-        }
+        for (int n = 0; n < 32; ++n)
+          if (gi0 + n < g.G) prow[(int64_t)n * g.n] = make_longlong2(acc[n], acc[32 + n]);
       }
     }
     if (!ok) atomicExch(err, FLAPW_ERR_TIMEOUT);
@@ -364,6 +355,36 @@ __global__ void __launch_bounds__(256) opgemm_build_b_kernel(const double2* __re
   }
 }
 
+// Z(h_row0 + g, column of (a, r)) = P_{slot(a),type(a)}(r, g) e^{i K.tau_a}
+// for every atom a of a combination: the Q62 phase product of the fixed-point
+// P, then the FP64 value built from its bits (no FP64 arithmetic).  grid:
+// (G, combos), 128 threads over the rows r.
+__global__ void __launch_bounds__(128) opgemm_phase_kernel(const OpGemmArgs g) {
+  const int64_t gi = blockIdx.x;
+  const int combo = blockIdx.y;
+  const int slot = g.combo_slot[combo], type = g.combo_type[combo];
+  const int eb = g.rexp_b[type * g.G + gi] - kFrac;
+  const int np = g.npos[slot];
+  const int a0 = g.combo_start[combo], a1 = g.combo_start[combo + 1];
+  double2* zrow = g.Z + (g.h_row0 + gi) * g.k_alloc;
+  const longlong2* prow = g.P + ((int64_t)combo * g.G + gi) * g.n;
+  for (int r = threadIdx.x; r < g.n; r += blockDim.x) {
+    const int rr = g.outrow[slot * g.n + r];  // sigma-grouped position
+    if (rr < 0) continue;                     // zero pivot: the row carries nothing
+    const longlong2 P = prow[r];
+    const int ex = g.rexp_a[slot * g.n + r] + eb;
+    for (int ai = a0; ai < a1; ++ai) {
+      const int a = g.combo_atoms[ai];
+      const double2 f = g.ph[(int64_t)a * g.G + gi];
+      const long long qr = fx::fixed_point(f.x, 62), qi = fx::fixed_point(f.y, 62);
+      const long long zr = fx::mul_q62(P.x, qr) - fx::mul_q62(P.y, qi);
+      const long long zi = fx::mul_q62(P.x, qi) + fx::mul_q62(P.y, qr);
+      const int col = (rr < np) ? g.pos_off[a] + rr : g.kpk[0] + g.neg_off[a] + (rr - np);
+      zrow[col] = make_double2(fx::to_double(zr, ex), fx::to_double(zi, ex));
+    }
+  }
+}
+
 }  // namespace
 
 size_t opgemm_smem_bytes() { return kStages * kStageBytes + 1024 + 256; }
@@ -392,6 +413,12 @@ cudaError_t launch_opgemm(const CUtensorMap& map_a, const CUtensorMap& map_b, co
   if (g.kchunks < 1 || g.kchunks > kMaxKChunks) return cudaErrorInvalidValue;
   const int grid = std::max(1, std::min(n_tiles, max_ctas));
   opgemm_kernel<<<grid, kThreads, opgemm_smem_bytes(), st>>>(map_a, map_b, g, tiles, n_tiles, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_opgemm_phase(const OpGemmArgs& g, int n_combo, cudaStream_t st) {
+  if (g.G == 0 || n_combo == 0) return cudaSuccess;
+  opgemm_phase_kernel<<<dim3((unsigned)g.G, (unsigned)n_combo), 128, 0, st>>>(g);
   return cudaGetLastError();
 }
 

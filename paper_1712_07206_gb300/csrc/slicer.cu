@@ -17,30 +17,30 @@
 // Without a problem table every row's valid range is [0, k_valid).
 #include <cstdint>
 
+#include "fixed64.cuh"
 #include "flapw_internal.h"
 
 namespace flapw {
 namespace {
 
-__device__ __forceinline__ uint64_t absbits(double x) {
-  return (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-}
+using fx::absbits;
+using fx::fixed_point;
 
-// round(x * 2^shift0) as a signed integer, from the bit pattern.
-__device__ __forceinline__ long long fixed_point(double x, int shift0) {
-  const uint64_t b = (uint64_t)__double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  if (ex == 0) return 0;  // zero or subnormal: below every slice
-  const uint64_t mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int sh = ex - 1075 + shift0;
-  long long X;
-  if (sh >= 0) {
-    X = (long long)(mant << sh);
-  } else {
-    const int r = -sh;
-    X = (r > 62) ? 0 : (long long)((mant + (1ull << (r - 1))) >> r);
+// Writes the NS balanced base-128 digits of the fixed-point values X0, X1 (two
+// adjacent columns) as fp16 pairs d2[i] = (digit i of X0, digit i of X1).  The
+// digits are small integers: each goes to FP32 exactly by the magic-number
+// addition and the pair to fp16 by one packed conversion, so no FP64 or
+// 64-bit-integer conversion instruction is involved.
+template <int NS>
+__device__ __forceinline__ void digits2(long long X0, long long X1, __half2 (&d2)[NS]) {
+#pragma unroll
+  for (int i = NS - 1; i >= 1; --i) {
+    const long long a = ((X0 + 64) & 127) - 64, b = ((X1 + 64) & 127) - 64;
+    d2[i] = __floats2half2_rn(fx::small_int_to_float((int)a), fx::small_int_to_float((int)b));
+    X0 = (X0 - a) >> kSliceBits;
+    X1 = (X1 - b) >> kSliceBits;
   }
-  return (b >> 63) ? -X : X;
+  d2[0] = __floats2half2_rn(fx::small_int_to_float((int)X0), fx::small_int_to_float((int)X1));
 }
 
 template <int NS>
@@ -97,17 +97,14 @@ __global__ void __launch_bounds__(256) slicer_kernel(const double2* __restrict__
     for (int q = 0; q < 8; ++q) z[q] = valid(c0 + q) ? zr[c0 + q] : make_double2(0.0, 0.0);
 #pragma unroll
     for (int plane = 0; plane < 2; ++plane) {
-      __align__(16) __half d[NS][8];
+      __align__(16) __half2 d[NS][4];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        long long X = fixed_point(plane ? z[q].y : z[q].x, shift0);
+      for (int q = 0; q < 8; q += 2) {
+        __half2 d2[NS];
+        digits2<NS>(fixed_point(plane ? z[q].y : z[q].x, shift0),
+                    fixed_point(plane ? z[q + 1].y : z[q + 1].x, shift0), d2);
 #pragma unroll
-        for (int i = NS - 1; i >= 1; --i) {
-          const long long di = ((X + 64) & 127) - 64;
-          d[i][q] = __ll2half_rn(di);
-          X = (X - di) >> kSliceBits;
-        }
-        d[0][q] = __ll2half_rn(X);
+        for (int i = 0; i < NS; ++i) d[i][q / 2] = d2[i];
       }
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
@@ -150,17 +147,14 @@ __global__ void __launch_bounds__(256) slicer_rows_kernel(const double2* __restr
     for (int q = 0; q < 8; ++q) z[q] = zr[c0 + q];
 #pragma unroll
     for (int plane = 0; plane < 2; ++plane) {
-      __align__(16) __half d[NS][8];
+      __align__(16) __half2 d[NS][4];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        long long X = fixed_point(plane ? z[q].y : z[q].x, shift0);
+      for (int q = 0; q < 8; q += 2) {
+        __half2 d2[NS];
+        digits2<NS>(fixed_point(plane ? z[q].y : z[q].x, shift0),
+                    fixed_point(plane ? z[q + 1].y : z[q + 1].x, shift0), d2);
 #pragma unroll
-        for (int i = NS - 1; i >= 1; --i) {
-          const long long di = ((X + 64) & 127) - 64;
-          d[i][q] = __ll2half_rn(di);
-          X = (X - di) >> kSliceBits;
-        }
-        d[0][q] = __ll2half_rn(X);
+        for (int i = 0; i < NS; ++i) d[i][q / 2] = d2[i];
       }
 #pragma unroll
       for (int i = 0; i < NS; ++i) {

@@ -110,6 +110,20 @@ def test_hs_edge_one_atom_lmax0_tiny(precision):
     assert herm_relerr(lower_to_full(Ss[0], ng, 0), So) <= tol
 
 
+@pytest.mark.parametrize("precision,tol", [(fl.PREC_FP64, TOL_F64), (fl.PREC_EMU, TOL_EMU)])
+def test_hs_lmax12_longest_operand_reduction(precision, tol):
+    # lmax 12: 2 N_L = 338 rows of C^H, the H operand product's reduction padded
+    # to 384 terms, the most that one exact FP32 accumulation per slice level
+    # allows; 3 atoms in 2 (slot, type) combinations, one of them shared
+    p = inputs.small(13, n_atoms=3, n_types=2, lmax=12, n_target=(230,))
+    p.atom_slot = np.array([0, 1, 0], dtype=np.int32)
+    h, Hs, Ss, _ = run_hs(p, precision, operands=fl.OPERANDS_FACTORED)
+    Ho, So = oracle_hs(p)
+    ng = Ho.shape[0]
+    assert herm_relerr(lower_to_full(Hs[0], ng, 0), Ho) <= tol
+    assert herm_relerr(lower_to_full(Ss[0], ng, 0), So) <= tol
+
+
 def test_hs_hpd_T_has_no_negative_rows():
     p = inputs.small(11, n_atoms=2, n_types=2, lmax=3, n_target=(260,), hpd=True)
     h, Hs, Ss, _ = run_hs(p, fl.PREC_EMU)
