@@ -33,7 +33,8 @@ __device__ __forceinline__ long long fixed_point(double x, int shift0) {
 }
 
 // x 2^ex rounded to the nearest double (ties to even), built from the bits.
-// Results outside the normal range fall back to ldexp.
+// Results below the normal range flush to a signed zero and above it become
+// a signed infinity (the emulation's scaled values stay far from both).
 __device__ __forceinline__ double to_double(long long x, int ex) {
   if (x == 0) return 0.0;
   const uint64_t sgn = x < 0 ? (1ull << 63) : 0ull;
@@ -51,7 +52,8 @@ __device__ __forceinline__ double to_double(long long x, int ex) {
     }
   }
   const int be = e2 + 1023;
-  if (be <= 0 || be >= 2047) return ldexp((double)x, ex);
+  if (be <= 0) return __longlong_as_double((long long)sgn);
+  if (be >= 2047) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull));
   return __longlong_as_double((long long)(sgn | ((uint64_t)be << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
