@@ -35,7 +35,9 @@
 // of one pass overlaps the MMAs of the next.  Against one CTA per tile (M=128)
 // the pair halves the B bytes each SM loads per MMA flop, and 128-wide stages
 // halve the producer/MMA hand-offs per flop; both bound the tensor pipe's
-// occupancy.  Rows with sigma = -1 form their own K units, subtracted.
+// occupancy.  Rows with sigma = -1 sit in the K chunks from Kp_pad on; their
+// MMAs set the descriptor's negate-B bit, so H = Z^H diag(sigma) Z accumulates
+// both signs in the same sums and has the schedule of S.
 //
 // Warp roles (both CTAs): warp 0 TMA producer, warp 1 TMEM allocator (and in
 // CTA 0 the MMA issuer), warps 2..9 drain/epilogue (warp w reads TMEM lanes
@@ -74,6 +76,7 @@ constexpr uint32_t kIdesc256 = (1u << 4) | (0u << 7) | (0u << 10) | ((256u >> 3)
                                ((256u >> 4) << 24);
 constexpr uint32_t kIdesc128 = (1u << 4) | (0u << 7) | (0u << 10) | ((128u >> 3) << 17) |
                                ((256u >> 4) << 24);
+constexpr uint32_t kNegateB = 1u << 14;  // instruction descriptor: D += A (-B)
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -123,23 +126,19 @@ __device__ __forceinline__ void umma_commit_both(uint32_t bar) {
 // (i.e. 1-based levels i + j + 2 <= s + 1), i = 0..t.  Every role walks the
 // same order.
 
+// K units: the chunks [0, kpc) of the sigma = +1 rows and [kpc, kpc + knc)
+// of the sigma = -1 rows (their MMAs negate B, so both signs accumulate in
+// one sum, bounded by the magnitudes alone), cut into the fewest equal units
+// of at most kUnitChunks.
 struct Units {
   int kpc, knc;  // positive / negative chunk counts
-  __device__ int count() const {
-    return (kpc + kUnitChunks - 1) / kUnitChunks + (knc + kUnitChunks - 1) / kUnitChunks;
-  }
-  // unit u -> [c0, c1) chunk range and sign (1 = negative)
-  __device__ void get(int u, int& c0, int& c1, int& neg) const {
-    const int up = (kpc + kUnitChunks - 1) / kUnitChunks;
-    if (u < up) {
-      c0 = u * kUnitChunks;
-      c1 = min(kpc, c0 + kUnitChunks);
-      neg = 0;
-    } else {
-      c0 = kpc + (u - up) * kUnitChunks;
-      c1 = min(kpc + knc, c0 + kUnitChunks);
-      neg = 1;
-    }
+  __device__ int total() const { return kpc + knc; }
+  __device__ int count() const { return (total() + kUnitChunks - 1) / kUnitChunks; }
+  // unit u -> [c0, c1) chunk range
+  __device__ void get(int u, int& c0, int& c1) const {
+    const int n = count(), t = total();
+    c0 = (int)((long long)u * t / n);
+    c1 = (int)((long long)(u + 1) * t / n);
   }
 };
 
@@ -157,14 +156,14 @@ __device__ __forceinline__ Units units_of(const Prob& P) {
 }
 
 // The drain steps of one tile, in the order every role walks them: for each
-// K unit (sign-homogeneous, <= kUnitChunks chunks), for each slice group
+// K unit (<= kUnitChunks chunks), for each slice group
 // (i; j, j+1) with i + j + 1 <= s - 1, for each sub-span of the unit, an R
 // pass then an I pass.  A sub-span is as long as both pairs of the group may
 // accumulate exactly (and at most kPassChunks).
 struct Sched {
   Units U;
   int s, nu;
-  int u, c0, c1, neg;
+  int u, c0, c1;
   int i, j, two;
   int nsub, k;  // sub-spans of the unit for this group, current one
   int s0, s1, pass;
@@ -186,7 +185,7 @@ struct Sched {
     nu = U.count();
     u = 0;
     if (nu == 0) return false;
-    U.get(0, c0, c1, neg);
+    U.get(0, c0, c1);
     i = 0;
     j = 0;
     pass = 0;
@@ -210,7 +209,7 @@ struct Sched {
       if (++i >= s) {
         i = 0;
         if (++u >= nu) return false;
-        U.get(u, c0, c1, neg);
+        U.get(u, c0, c1);
       }
     }
     set_group();
@@ -347,9 +346,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
             for (int q = 0; q < nv; ++q) {
               const uint64_t da = sdesc(sbase + q * kTileA), db = sdesc(sbase + kOffB + q * kTileB);
+              const uint32_t id = (c + q >= sc.U.kpc) ? (idesc | kNegateB) : idesc;  // sigma = -1
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk)
-                umma_pair(d, da + 2 * kk, db + 2 * kk, idesc, (c > sc.s0 || q > 0 || kk > 0) ? 1u : 0u);
+                umma_pair(d, da + 2 * kk, db + 2 * kk, id, (c > sc.s0 || q > 0 || kk > 0) ? 1u : 0u);
             }
             umma_commit_both(empty_bar(stage));
             ++it;
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // R pass: Re += RR (cols 0..63 of a pair block), Im += RI (64..127);
         // I pass: Re += II (64..127), Im -= IR (0..63).
         const uint32_t col = (h == 0) ? (sc.pass ? 64u : 0u) : (sc.pass ? 0u : 64u);
-        const bool sub = (sc.neg != 0) != (h == 1 && sc.pass == 1);
+        const bool sub = (h == 1 && sc.pass == 1);
         for (int pq = 0; pq <= sc.two; ++pq) {
           const int sh = frac - kSliceBits * (sc.i + sc.j + pq + 2);
           const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * 256u +
