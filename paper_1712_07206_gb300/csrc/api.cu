@@ -133,6 +133,9 @@ struct flapw_ctx {
   int tile_order = 3;            // emulated tile order in use (see make_tiles)
   int64_t tuned_key = -1;        // shape the autotuner last ran on
   int64_t tiles_rows_key = -1;
+  int tiles_pairs = -1;          // pair counts the tile lists' last waves were split for
+  int split_ids = 0;             // split tiles of a half (scratch slots)
+  DevBuf d_split;                // their partial sums and completion counts
   SliceMaps tmap{};
   void* tmap_base = nullptr;
   int64_t tmap_k = 0, tmap_rows = 0;
@@ -222,8 +225,9 @@ int upload(flapw_ctx* h, DevBuf& d, const std::vector<T>& v) {
 //   order 0: row blocks outer, column blocks inner;  1: column blocks outer;
 //   order 2/3/4: grouped raster -- bands of 4/2/8 row blocks, and within a
 //   band column by column, so the concurrent tiles touch a compact set of rows.
-void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order,
-                std::vector<EmuTile>* emu, std::vector<F64Tile>* f64) {
+void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order, int pairs,
+                std::vector<EmuTile>* emu, std::vector<F64Tile>* f64, int* n_split_ids) {
+  const size_t emu0 = emu->size();
   for (int p = p0; p < p1; ++p) {
     const int ng = probs[p].n_g;
     const int nib = (ng + 255) / 256, njb = (ng + 63) / 64;
@@ -247,6 +251,24 @@ void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order,
     for (int ib = 0; ib < nb; ++ib)
       for (int jb = 0; jb <= ib; ++jb) f64->push_back(F64Tile{p, ib, jb, 0});
   }
+  // The pairs take the tiles round-robin, so the last rem = n mod pairs tiles
+  // form a partly empty last wave.  Each of them becomes f K parts (f pairs
+  // share it), so the last wave lasts 1/f of a tile.
+  *n_split_ids = 0;
+  const int n = (int)(emu->size() - emu0);
+  if (pairs < 2 || n <= pairs) return;
+  const int rem = n % pairs;
+  const int f = rem ? std::min(kMaxSplit, pairs / rem) : 1;
+  if (f < 2) return;
+  std::vector<EmuTile> last(emu->end() - rem, emu->end());
+  emu->resize(emu->size() - rem);
+  for (int t = 0; t < rem; ++t)
+    for (int part = 0; part < f; ++part) {
+      EmuTile x = last[t];
+      x.split = make_split(f, part, t);
+      emu->push_back(x);
+    }
+  *n_split_ids = rem;
 }
 
 // Output pointers: device pointers are used in place; host pointers get a
@@ -271,6 +293,16 @@ struct Half {
   int emu_t0, emu_nt, f64_t0, f64_nt;
 };
 
+// Split-tile scratch of the handle; its counts are zeroed on `st` first.
+int split_scratch(flapw_ctx* h, cudaStream_t st, SplitScratch* out) {
+  const size_t counts = (size_t)std::max(1, h->split_ids) * 2 * 8 * 4;
+  const size_t total = split_scratch_bytes(std::max(1, h->split_ids));
+  out->partial = h->d_split.as<long long>();
+  out->count = reinterpret_cast<int*>(h->d_split.as<char>() + (total - counts));
+  CK(h, cudaMemsetAsync(out->count, 0, counts, st), "cudaMemsetAsync");
+  return FLAPW_OK;
+}
+
 // Slices (emulated precision) and contracts one half beside concurrent work
 // that holds busy_sms SMs.  Records ev_sl after the slicer and ev_k after the
 // contraction.
@@ -283,9 +315,11 @@ int enqueue_contraction(flapw_ctx* h, const Half& hf, int busy_sms, cudaStream_t
                         0, rows, hf.row0, hf.nrows, s, h->d_SL.as<__half>(), h->d_rexp.as<int>(), st),
        "slicer launch");
     CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
+    SplitScratch sp{};
+    if (int rc = split_scratch(h, st, &sp)) return rc;
     CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf.emu_t0,
                           hf.emu_nt, h->d_rexp.as<int>(), s, fixed_frac_bits(h->k_terms),
-                          h->d_cnt.as<int>() + 2, busy_sms, st),
+                          h->d_cnt.as<int>() + 2, busy_sms, sp, st),
        "emulated contraction launch");
   } else {
     CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
@@ -315,23 +349,35 @@ int ensure_slices(flapw_ctx* h) {
   return FLAPW_OK;
 }
 
-// Tile lists of problems [0, n_first) then [n_first, n_prob).
+// Tile lists of problems [0, n_first) then [n_first, n_prob), the first half
+// contracted beside busy_first busy SMs, the second beside busy_second.
 int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int64_t key,
-                 Half* first, Half* second) {
+                 Half* first, Half* second, int busy_first = 0, int busy_second = 0) {
   const int order = h->tile_order;
-  if (h->tiles_rows_key != key || h->tiles_order != order) {
+  int pf = 0, ps = 0;
+  if (h->opt.precision == FLAPW_PREC_EMU) {
+    CK(h, herk_emu_init(), "contraction kernel setup");
+    pf = herk_emu_pairs(busy_first);
+    ps = herk_emu_pairs(busy_second);
+  }
+  if (h->tiles_rows_key != key || h->tiles_order != order || h->tiles_pairs != pf * 1024 + ps) {
     std::vector<EmuTile> emu;
     std::vector<F64Tile> f64;
-    make_tiles(probs, 0, n_first, order, &emu, &f64);
+    int ids_first = 0, ids_second = 0;
+    make_tiles(probs, 0, n_first, order, pf, &emu, &f64, &ids_first);
     h->split_emu = (int)emu.size();
     h->split_f64 = (int)f64.size();
-    make_tiles(probs, n_first, (int)probs.size(), order, &emu, &f64);
+    make_tiles(probs, n_first, (int)probs.size(), order, ps, &emu, &f64, &ids_second);
     h->n_emu_tiles = (int)emu.size();
     h->n_f64_tiles = (int)f64.size();
     if (upload(h, h->d_emu_tiles, emu)) return FLAPW_ERR_CUDA;
     if (upload(h, h->d_f64_tiles, f64)) return FLAPW_ERR_CUDA;
+    // the halves run one after the other on one stream: they share the scratch
+    h->split_ids = std::max(ids_first, ids_second);
+    CK(h, h->d_split.ensure(split_scratch_bytes(std::max(1, h->split_ids))), "split-tile scratch");
     h->tiles_rows_key = key;
     h->tiles_order = order;
+    h->tiles_pairs = pf * 1024 + ps;
   }
   first->emu_t0 = 0;
   first->emu_nt = h->split_emu;
@@ -357,14 +403,16 @@ int autotune_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, in
   for (int o = 0; o < kNumTileOrders; ++o) {
     h->tile_order = o;
     Half a, b;
-    if (int rc = ensure_tiles(h, probs, n_first, key, &a, &b)) return rc;
+    if (int rc = ensure_tiles(h, probs, n_first, key, &a, &b, 0, n_slots)) return rc;
     float t_best = 1e30f;
     for (int rep = 0; rep < 2; ++rep) {
       CK(h, cudaEventRecord(h->ev[14], st), "cudaEventRecord");
       for (const Half* hf : {&b, &a}) {
+        SplitScratch sp{};
+        if (int rc = split_scratch(h, st, &sp)) return rc;
         CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf->emu_t0,
                               hf->emu_nt, h->d_rexp.as<int>(), s, fixed_frac_bits(h->k_terms),
-                              h->d_cnt.as<int>() + 2, 0, st),
+                              h->d_cnt.as<int>() + 2, 0, sp, st),
            "emulated contraction launch");
       }
       CK(h, cudaEventRecord(h->ev[15], st), "cudaEventRecord");
@@ -378,10 +426,9 @@ int autotune_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, in
       best_o = o;
     }
   }
-  (void)n_slots;
   h->tile_order = best_o;
   Half a, b;
-  if (int rc = ensure_tiles(h, probs, n_first, key, &a, &b)) return rc;
+  if (int rc = ensure_tiles(h, probs, n_first, key, &a, &b, 0, n_slots)) return rc;
   h->tuned_key = key;
   return FLAPW_OK;
 }
@@ -771,7 +818,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     if (upload(h, h->d_rowprob, rp)) return FLAPW_ERR_CUDA;
   }
   Half hH, hS;
-  if (int rc = ensure_tiles(h, probs, nk, h->rows, &hH, &hS)) return rc;
+  if (int rc = ensure_tiles(h, probs, nk, h->rows, &hH, &hS, 0, n_slots)) return rc;
   hH.row0 = 0;
   hH.nrows = h->g_total;
   hS.row0 = h->g_total;
@@ -953,7 +1000,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
                              (uintptr_t)h->d_T.p, (uintptr_t)h->d_stageOut.p, (uintptr_t)h->d_emu_tiles.p,
                              (uintptr_t)h->d_opA.p, (uintptr_t)h->d_opB.p, (uintptr_t)h->d_opSLA.p,
                              (uintptr_t)h->d_opSLB.p, (uintptr_t)h->d_oprexp.p, (uintptr_t)h->d_optiles.p,
-                             (uintptr_t)h->d_opP.p};
+                             (uintptr_t)h->d_opP.p, (uintptr_t)h->d_split.p};
   for (int k = 0; k < nk; ++k) {
     key.push_back((uintptr_t)H[k]);
     key.push_back((uintptr_t)S[k]);

@@ -34,13 +34,28 @@ struct Prob {
 };
 
 // Output tile of the emulated contraction: 256 rows (G') x 64 columns (G),
-// computed by a CTA pair.
+// computed by a CTA pair.  `split` is 0 for a whole tile, or, for one of the
+// `parts` K parts of a tile of the last wave, parts | part << 4 | id << 8
+// (id: the split tile's scratch slot).
 struct EmuTile {
   int prob;
   int ib;  // row block (256)
   int jb;  // column block (64)
-  int pad;
+  int split;
 };
+constexpr int kMaxSplit = 4;  // K parts of a split tile
+__host__ __device__ inline int split_parts(int s) { return (s & 15) ? (s & 15) : 1; }
+__host__ __device__ inline int split_part(int s) { return (s >> 4) & 15; }
+__host__ __device__ inline int split_id(int s) { return s >> 8; }
+inline int make_split(int parts, int part, int id) { return parts | (part << 4) | (id << 8); }
+// Scratch of the split tiles: 64-bit partial sums per (id, cta, drain warp,
+// part) and one completion count per (id, cta, drain warp), zero between
+// launches (split_scratch_bytes: both, counts after the partial sums).
+struct SplitScratch {
+  long long* partial;
+  int* count;
+};
+size_t split_scratch_bytes(int n_ids);
 
 // Output tile of the FP64 contraction: 64 x 64.
 struct F64Tile {
@@ -219,7 +234,9 @@ cudaError_t herk_emu_init();
 // where busy_sms is the number of SMs that concurrent work holds.
 cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuTile* tiles,
                             int n_tiles, const int* rexp, int n_slices, int frac, int* err,
-                            int busy_sms, cudaStream_t st);
+                            int busy_sms, const SplitScratch& split, cudaStream_t st);
+// The pair count a launch beside busy_sms busy SMs gets (0 before herk_emu_init).
+int herk_emu_pairs(int busy_sms);
 size_t herk_emu_smem_bytes();
 
 // ---- host G enumeration ----------------------------------------------------

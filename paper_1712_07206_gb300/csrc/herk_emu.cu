@@ -132,13 +132,14 @@ __device__ __forceinline__ void umma_commit_both(uint32_t bar) {
 // of at most kUnitChunks.
 struct Units {
   int kpc, knc;  // positive / negative chunk counts
-  __device__ int total() const { return kpc + knc; }
+  int cb, ce;    // the chunk window of this tile part: [cb, ce)
+  __device__ int total() const { return ce - cb; }
   __device__ int count() const { return (total() + kUnitChunks - 1) / kUnitChunks; }
   // unit u -> [c0, c1) chunk range
   __device__ void get(int u, int& c0, int& c1) const {
     const int n = count(), t = total();
-    c0 = (int)((long long)u * t / n);
-    c1 = (int)((long long)(u + 1) * t / n);
+    c0 = cb + (int)((long long)u * t / n);
+    c1 = cb + (int)((long long)(u + 1) * t / n);
   }
 };
 
@@ -148,10 +149,15 @@ __device__ __forceinline__ int pair_span(int i, int j) {
   return (i == 0 && j == 0) ? kUnitChunks / 4 : (i == 0 || j == 0) ? kUnitChunks / 2 : kUnitChunks;
 }
 
-__device__ __forceinline__ Units units_of(const Prob& P) {
+// A tile's K chunks, or part `part` of `parts` equal parts of them (a tile of
+// the last wave split over several pairs; EmuTile::split).
+__device__ __forceinline__ Units units_of(const Prob& P, int split) {
   Units u;
   u.kpc = (P.kp + kChunk - 1) / kChunk;
   u.knc = (P.kn + kChunk - 1) / kChunk;
+  const int parts = split_parts(split), part = split_part(split), t = u.kpc + u.knc;
+  u.cb = (int)((long long)part * t / parts);
+  u.ce = (int)((long long)(part + 1) * t / parts);
   return u;
 }
 
@@ -220,7 +226,7 @@ struct Sched {
 __global__ void __launch_bounds__(kThreads, 1)
     herk_emu_kernel(const __grid_constant__ SliceMaps maps, const Prob* __restrict__ probs,
                     const EmuTile* __restrict__ tiles, int n_tiles, const int* __restrict__ rexp,
-                    int n_slices, int frac, int* __restrict__ err) {
+                    int n_slices, int frac, int* __restrict__ err, SplitScratch split) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
@@ -278,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const Prob P = probs[T.prob];
         const int rowA = P.row_base + T.ib * 256 + (int)rank * 128, rowB = P.row_base + T.jb * 64;
         Sched sc;
-        for (bool more = sc.begin(units_of(P), n_slices); more && ok; more = sc.next()) {
+        for (bool more = sc.begin(units_of(P, T.split), n_slices); more && ok; more = sc.next()) {
           const uint32_t b_bytes = sc.two ? kTileB : kTileB / 2;
           for (int c = sc.s0; c < sc.s1; c += kStageChunks) {
             const int nv = min(kStageChunks, sc.s1 - c);
@@ -325,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const EmuTile T = tiles[tile];
         const Prob P = probs[T.prob];
         Sched sc;
-        for (bool more = sc.begin(units_of(P), n_slices); more && ok; more = sc.next()) {
+        for (bool more = sc.begin(units_of(P, T.split), n_slices); more && ok; more = sc.next()) {
           const int buf = acc_it & 1;  // equals sc.pass: R passes use acc_R, I passes acc_I
           const uint32_t use = acc_it >> 1;
           if (!mbar_wait(tempty_bar(buf), (use & 1u) ^ 1u, ab)) {
@@ -382,7 +388,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int n = 0; n < 64; ++n) acc[n] = 0;
       Sched sc;
-      for (bool more = sc.begin(units_of(P), n_slices); more && ok; more = sc.next()) {
+      for (bool more = sc.begin(units_of(P, T.split), n_slices); more && ok; more = sc.next()) {
         const int buf = acc_it & 1;
         const uint32_t use = acc_it >> 1;
         if (!mbar_wait(tfull_bar(buf), use & 1u, ab)) {
@@ -407,6 +413,34 @@ __global__ void __launch_bounds__(kThreads, 1)
         ++acc_it;
       }
       if (!ok) break;
+      if (split_parts(T.split) > 1) {
+        // This pair summed one K part of the tile: leave the partial sums in
+        // the scratch; per drain warp (32 rows x 64 columns of Re or Im) the
+        // part that finishes last adds the others' and writes.  Only
+        // warp-level synchronisation is involved.
+        const int parts = split_parts(T.split), part = split_part(T.split);
+        const int64_t base = ((int64_t)split_id(T.split) * 2 + rank) * 8 + ew;  // this warp's slice
+        long long* mine = split.partial + ((base * kMaxSplit + part) * 64) * 32 + lane;
+#pragma unroll
+        for (int n = 0; n < 64; ++n) mine[n * 32] = acc[n];
+        __threadfence();
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+          const int done = atomicAdd(split.count + base, 1);
+          last = (done == parts - 1);
+          if (last) split.count[base] = 0;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (!last) continue;
+        __threadfence();
+        for (int o = 0; o < parts; ++o) {
+          if (o == part) continue;
+          const long long* other = split.partial + ((base * kMaxSplit + o) * 64) * 32 + lane;
+#pragma unroll
+          for (int n = 0; n < 64; ++n) acc[n] += __ldcg(other + n * 32);
+        }
+      }
       // write the lower-triangle part of this CTA's rows of the tile
       const int64_t ng = P.n_g;
       const int64_t gr = (int64_t)T.ib * 256 + (int64_t)rank * 128 + m;
@@ -452,6 +486,11 @@ DevState g_state[kMaxDevices];
 
 size_t herk_emu_smem_bytes() { return kStages * kStageBytes + 1024 + 256; }
 
+// partial sums: [id][cta][drain warp][part][64][32] int64; counts: [id][cta][drain warp]
+size_t split_scratch_bytes(int n_ids) {
+  return (size_t)n_ids * 2 * 8 * (kMaxSplit * 64 * 32 * 8 + 4);
+}
+
 int fixed_frac_bits(int64_t k_terms) {
   int lg = 0;
   while (lg < 62 && ((int64_t)1 << lg) < k_terms) ++lg;
@@ -492,9 +531,15 @@ cudaError_t herk_emu_init() {
   return cudaSuccess;
 }
 
+int herk_emu_pairs(int busy_sms) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices || !g_state[dev].ready) return 0;
+  return std::max(1, g_state[dev].max_pairs - std::max(0, busy_sms));
+}
+
 cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuTile* tiles,
                             int n_tiles, const int* rexp, int n_slices, int frac, int* err,
-                            int busy_sms, cudaStream_t st) {
+                            int busy_sms, const SplitScratch& split, cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   if (n_slices < 1 || n_slices > kMaxS || frac < 40 || frac > 50) return cudaErrorInvalidValue;
   cudaError_t e = herk_emu_init();
@@ -518,7 +563,8 @@ cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuT
   cfg.stream = st;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, herk_emu_kernel, maps, probs, tiles, n_tiles, rexp, n_slices, frac, err);
+  e = cudaLaunchKernelEx(&cfg, herk_emu_kernel, maps, probs, tiles, n_tiles, rexp, n_slices, frac, err,
+                         split);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

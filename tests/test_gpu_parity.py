@@ -124,6 +124,18 @@ def test_hs_lmax12_longest_operand_reduction(precision, tol):
     assert herm_relerr(lower_to_full(Ss[0], ng, 0), So) <= tol
 
 
+@pytest.mark.parametrize("layout", [fl.LAYOUT_LOWER_FULL, fl.LAYOUT_LOWER_PACKED])
+def test_hs_split_last_wave_full_parity(layout):
+    # N_G ~1600: more 256 x 64 tiles than co-resident CTA pairs, so the
+    # partly empty last wave is split into K parts over several pairs
+    p = inputs.small(17, n_atoms=2, n_types=2, lmax=3, n_target=(1600,))
+    h, Hs, Ss, _ = run_hs(p, fl.PREC_EMU, layout=layout, operands=fl.OPERANDS_FACTORED)
+    Ho, So = oracle_hs(p)
+    ng = Ho.shape[0]
+    assert herm_relerr(lower_to_full(Hs[0], ng, layout), Ho) <= TOL_EMU
+    assert herm_relerr(lower_to_full(Ss[0], ng, layout), So) <= TOL_EMU
+
+
 def test_hs_hpd_T_has_no_negative_rows():
     p = inputs.small(11, n_atoms=2, n_types=2, lmax=3, n_target=(260,), hpd=True)
     h, Hs, Ss, _ = run_hs(p, fl.PREC_EMU)
