@@ -116,8 +116,10 @@ def workload(cfg):
     return inputs.CONFIGS[cfg]()
 
 
-def hs_flops(p, ngs):
-    return 16.0 * p.n_atoms * p.n_L * float(np.sum(np.asarray(ngs, dtype=np.float64) ** 2))
+def hs_flops(p, ngs, per=16.0):
+    """per N_A N_L N_G^2 per k-point: 16 in the rank-K (HERK) count of the metric,
+    20 in the count of the paper's Alg. 3 operation sequence."""
+    return per * p.n_atoms * p.n_L * float(np.sum(np.asarray(ngs, dtype=np.float64) ** 2))
 
 
 def run_ours(args):
@@ -136,7 +138,7 @@ def run_ours(args):
     operands = fl.OPERANDS_FACTORED if args.operands == "factored" else fl.OPERANDS_FROM_AB
     layout = fl.LAYOUT_LOWER_PACKED if p.layout == "packed" else fl.LAYOUT_LOWER_FULL
     opt = fl.default_options(precision=fl.PREC_EMU, layout=layout, operands=operands, n_slices=args.slices,
-                             tile_order=args.tile_order)
+                             tile_order=args.tile_order, use_graph=1 if args.graph else 0)
     h = fl.from_problem(p, opt)
     ngs = [h.num_g(k) for k in range(p.n_k)]
     flops = hs_flops(p, ngs)
@@ -205,7 +207,8 @@ def run_ours(args):
         # the FP64 leg writes its own outputs, so both paths can be checked
         H64 = [torch.zeros_like(x) for x in H]
         S64 = [torch.zeros_like(x) for x in S]
-        h.set_options(fl.default_options(precision=fl.PREC_FP64, layout=layout, operands=operands))
+        h.set_options(fl.default_options(precision=fl.PREC_FP64, layout=layout, operands=operands,
+                                         use_graph=1 if args.graph else 0))
         f_ms = []
         for i in range(args.fp64_steps + 1):
             flush.zero_()
@@ -248,13 +251,15 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "ms_per_kpoint": round(ms / p.n_k, 4),
+        "value_alg3_count": round(hs_flops(p, ngs, 20.0) / (ms * 1e-3) / 1e12 * ws, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c128 via fp16 slices (int64 accumulation)", "data": "synthetic",
         "config": {"workload": p.name, "n_atoms": p.n_atoms, "n_types": p.n_types, "lmax": p.lmax,
                    "n_L": p.n_L, "n_k": p.n_k, "n_g": ngs if len(ngs) <= 4 else [min(ngs), max(ngs)],
                    "K": int(st["k_total"]), "slices": args.slices, "operands": args.operands,
                    "layout": p.layout, "l2": "256 MB L2 flush between steps; A/B 166 MB and operands exceed L2",
-                   "flops_per_step": flops, "parallelism": f"replicas{ws}"},
+                   "flops_per_step": flops, "graph_replay": bool(args.graph),
+                   "parallelism": f"replicas{ws}"},
         "fp64_path": None if f64_ms is None else {
             "value": round(flops / (f64_ms * 1e-3) / 1e12 * ws, 4), "unit": "TFLOP/s",
             "ms_per_step": round(f64_ms, 3), "steps": args.fp64_steps},
@@ -276,6 +281,7 @@ def run_ours(args):
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, h, H, S, layout, ngs, args, H64, S64)
+        line["refined_cpu"] = refined_cpu(p, args)
     h.destroy()
     if ws > 1:
         import torch.distributed as dist
@@ -283,6 +289,37 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def refined_cpu(p, args):
+    """The paper's refined CPU code path (Alg. 3: zherk, zher2k, zherkx on host
+    BLAS) for a block of columns of k-point 0, numpy complex128 on all host
+    cores, A/B from the oracle: a comparator in the manner of the paper's
+    refined CPU baseline, in the metric's flop count."""
+    import os
+    import oracle
+
+    oracle.build()
+    n3 = oracle.gvectors(p.lattice, p.k_frac[0], p.kmax[0])
+    A, B = oracle.build_ab(p, 0, n3)
+    ng, nl = len(n3), p.n_L
+    m = min(ng, args.refined_cols)
+    ls = np.concatenate([[l] * (2 * l + 1) for l in range(p.lmax + 1)])
+    Ast = np.vstack(list(A))
+    Bst = np.vstack(list(B))
+    t0 = time.perf_counter()
+    X = np.vstack([p.U[p.atom_type[a], ls][:, None] * B[a] for a in range(p.n_atoms)])
+    S = Ast.conj().T @ Ast[:, :m] + X.conj().T @ X[:, :m]
+    Z = np.vstack([p.T[p.atom_slot[a]][nl:, :nl] @ A[a] + 0.5 * p.T[p.atom_slot[a]][nl:, nl:] @ B[a]
+                   for a in range(p.n_atoms)])
+    H = Z.conj().T @ Bst[:, :m] + Bst.conj().T @ Z[:, :m]
+    Y = np.vstack([p.T[p.atom_slot[a]][:nl, :nl] @ A[a] for a in range(p.n_atoms)])
+    H += Ast.conj().T @ Y[:, :m]
+    dt = time.perf_counter() - t0
+    per_col = 16.0 * p.n_atoms * p.n_L * ng
+    return {"value": round(m * per_col / dt / 1e12, 6), "unit": "TFLOP/s",
+            "cores": len(os.sched_getaffinity(0)), "kind": "numpy BLAS, Alg. 3 sequence",
+            "sample": f"{m} of {ng} columns of H and S at k-point 0 (operand products for all rows), {dt:.2f} s"}
 
 
 def cpu_baseline(p, h, H, S, layout, ngs, args, H64=None, S64=None):
@@ -371,6 +408,10 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cols", type=int, default=48)
+    ap.add_argument("--refined-cols", type=int, default=1024,
+                    help="columns of the host-BLAS Alg. 3 comparator")
+    ap.add_argument("--graph", action="store_true",
+                    help="replay the captured build_HS sequence (the stage timers then read -1)")
     ap.add_argument("--ref-cols", type=int, default=32)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per contraction launch from an ncu capture")
