@@ -61,6 +61,15 @@ typedef struct flapw_ctx* flapw_handle;
 #define FLAPW_OPERANDS_FROM_AB 0  /* build_HS forms its operands from the A, B it is given */
 #define FLAPW_OPERANDS_FACTORED 1 /* build_HS regenerates the per-type part of A, B itself */
 
+/* How build_HS forms S.  FLAPW_S_LEGENDRE sums over m by the addition
+ * theorem, sum_m Y_lm(u) conj(Y_lm(v)) = (2l+1)/(4 pi) P_l(u.v), so that
+ *   S_{G'G} = (4 pi / Omega) sum_t rho_t(G', G) sum_l (2l+1) P_l(Khat'.Khat)
+ *             [a_l(K') a_l(K) + U_l^2 b_l(K') b_l(K)],
+ *   rho_t = sum over the atoms a of type t of conj(e^{iK'.tau_a}) e^{iK.tau_a}
+ * (Eq. (def_overlap) with the matching of Sec. 2): no factor N_L, no slices. */
+#define FLAPW_S_CONTRACTION 0
+#define FLAPW_S_LEGENDRE 1
+
 typedef struct flapw_options {
   int precision; /* FLAPW_PREC_EMU (default) or FLAPW_PREC_FP64 */
   int n_slices;  /* emulation: 7-bit slices per operand entry, 4..8 (0 = default 7) */
@@ -72,8 +81,11 @@ typedef struct flapw_options {
                     keep the fastest (default 0: fixed choice) */
   int tile_order; /* 0: library default; k+1 forces tile order k of the emulated
                      contraction (0 row-major, 1 column-major, 2/3/4 bands of
-                     8/4/16 row blocks), ignored when autotune is on */
-  int reserved[9];
+                     4/2/8 row blocks of 256), ignored when autotune is on */
+  int s_method;   /* FLAPW_S_CONTRACTION (default): S = Z_S^H Z_S like H;
+                     FLAPW_S_LEGENDRE: S by the addition theorem (requires
+                     FLAPW_OPERANDS_FACTORED; FP64 in either precision) */
+  int reserved[8];
 } flapw_options;
 
 typedef struct flapw_stats {
@@ -94,6 +106,8 @@ typedef struct flapw_stats {
   int tile_order;      /* tile-order variant in use */
   int graph_replays;   /* build_HS calls served by CUDA-graph replay */
   int reserved[8];
+  double ms_s;         /* the S half of ms_contract: its contraction, or with
+                          FLAPW_S_LEGENDRE the addition-theorem evaluation */
 } flapw_stats;
 
 /* Defaults listed in flapw_options. */

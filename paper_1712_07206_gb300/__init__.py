@@ -28,6 +28,7 @@ _HEADER = os.path.join(os.path.dirname(_HERE), "include", "flapw.h")
 PREC_FP64, PREC_EMU = 0, 1
 LAYOUT_LOWER_FULL, LAYOUT_LOWER_PACKED = 0, 1
 OPERANDS_FROM_AB, OPERANDS_FACTORED = 0, 1
+S_CONTRACTION, S_LEGENDRE = 0, 1
 ERR = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_FACTOR",
        -5: "ERR_TIMEOUT", -6: "ERR_STATE", -7: "ERR_UNSUPPORTED"}
 
@@ -41,7 +42,7 @@ class FlapwError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_slices", ctypes.c_int), ("layout", ctypes.c_int),
                 ("operands", ctypes.c_int), ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("tile_order", ctypes.c_int), ("reserved", ctypes.c_int * 9)]
+                ("tile_order", ctypes.c_int), ("s_method", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
 
 
 class Stats(ctypes.Structure):
@@ -52,7 +53,7 @@ class Stats(ctypes.Structure):
                 ("k_total", ctypes.c_int64), ("n_pos", ctypes.c_int), ("n_neg", ctypes.c_int),
                 ("n_pivot2", ctypes.c_int), ("n_slices", ctypes.c_int), ("n_tiles", ctypes.c_int),
                 ("tile_order", ctypes.c_int), ("graph_replays", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("reserved", ctypes.c_int * 8), ("ms_s", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

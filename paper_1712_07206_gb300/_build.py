@@ -18,7 +18,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libflapw.so")
 SOURCES = ["api.cu", "gvec.cpp", "ab_gen.cu", "tfactor.cu", "opform.cu", "slicer.cu",
-           "herk_f64.cu", "herk_emu.cu", "opgemm.cu", "noalloc.cu"]
+           "herk_f64.cu", "herk_emu.cu", "opgemm.cu", "slegendre.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

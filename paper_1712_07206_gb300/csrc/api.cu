@@ -118,6 +118,8 @@ struct flapw_ctx {
   // H operands on the tensor cores (emulated path, factored operands): the two
   // factors in FP64 and sliced, their scale exponents, tiles and tensor maps
   DevBuf d_opA, d_opB, d_opSLA, d_opSLB, d_oprexp, d_optiles, d_opP;
+  DevBuf d_khat, d_typeatoms;    // S by the addition theorem: Khat per G, atoms by type
+  bool khat_valid = false;       // both depend on the crystal only
   std::vector<OpTile> optiles;
   CUtensorMap opmap_a{}, opmap_b{};
   void* opmap_a_base = nullptr;
@@ -195,6 +197,10 @@ int check_options(flapw_ctx* h, const flapw_options& o) {
     return fail(h, FLAPW_ERR_ARG, "options.operands is not a FLAPW_OPERANDS_* value");
   if (o.tile_order < 0 || o.tile_order > kNumTileOrders)
     return fail(h, FLAPW_ERR_ARG, "options.tile_order must be in 0..5");
+  if (o.s_method != FLAPW_S_CONTRACTION && o.s_method != FLAPW_S_LEGENDRE)
+    return fail(h, FLAPW_ERR_ARG, "options.s_method is not a FLAPW_S_* value");
+  if (o.s_method == FLAPW_S_LEGENDRE && o.operands != FLAPW_OPERANDS_FACTORED)
+    return fail(h, FLAPW_ERR_ARG, "options.s_method FLAPW_S_LEGENDRE needs FLAPW_OPERANDS_FACTORED");
   return FLAPW_OK;
 }
 
@@ -764,6 +770,29 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   CK(h, h->d_T.ensure(t_bytes), "workspace");
   CK(h, h->d_work.ensure(t_bytes), "workspace");
   CK(h, h->d_CH.ensure(t_bytes), "workspace");
+  // S by the addition theorem: Khat of every plane wave and the atoms grouped
+  // by type, both fixed by the crystal (computed once)
+  const bool s_legendre = h->opt.s_method == FLAPW_S_LEGENDRE;
+  if (s_legendre && !h->khat_valid) {
+    std::vector<int> ta;
+    std::vector<int> start{0};
+    for (int t = 0; t < h->n_types; ++t) {
+      for (int a = 0; a < h->n_atoms; ++a)
+        if (h->type[a] == t) ta.push_back(a);
+      start.push_back((int)ta.size());
+    }
+    ta.insert(ta.end(), start.begin(), start.end());
+    if (upload(h, h->d_typeatoms, ta)) return FLAPW_ERR_CUDA;
+    CK(h, h->d_khat.ensure((size_t)h->g_total * 3 * 8), "workspace");
+    Geom geo{h->n_atoms, h->n_types, h->lmax, h->n_L, h->n_k, h->g_total,
+             h->d_rec.as<double>(), h->d_pos.as<double>(), h->d_type.as<int>(),
+             h->d_radius.as<double>(), h->d_kfrac.as<double>(), h->d_ktau.as<double>(),
+             4.0 * M_PI / std::sqrt(h->volume)};
+    GData gd{h->d_n3.as<int>(), h->d_gk.as<int>(), h->d_goff.as<int64_t>()};
+    CK(h, launch_khat(geo, gd, h->d_khat.as<double>(), nullptr), "Khat launch");
+    CK(h, cudaDeviceSynchronize(), "Khat");
+    h->khat_valid = true;
+  }
   // emulated path with factored operands: the H operands come from the
   // tensor-core product of conj(C^H) and W (opgemm.cu)
   const bool tc_ops = factored && h->opt.precision == FLAPW_PREC_EMU;
@@ -941,9 +970,32 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
                                oprexp_b, st),
          "operand factor slicer launch");
     }
-    CK(h, launch_opform_S(oa, factored, st), "S operand launch");
-    CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
-    if (int rc = enqueue_contraction(h, hS, n_slots, st, 3, 4)) return rc;
+    if (s_legendre) {
+      // S by the addition theorem: no S operands, slices or contraction
+      CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
+      CK(h, cudaEventRecord(h->ev[3], st), "cudaEventRecord");
+      SLegArgs la{};
+      la.probs = h->d_probs.as<Prob>();
+      la.s_row0 = h->g_total;
+      la.g_total = h->g_total;
+      la.lmax = h->lmax;
+      la.n_types = h->n_types;
+      la.khat = h->d_khat.as<double>();
+      la.al = h->d_al.as<double>();
+      la.bl = h->d_bl.as<double>();
+      la.U = h->d_U.as<double>();
+      la.ph = h->d_ph.as<double2>();
+      la.type_atoms = h->d_typeatoms.as<int>();
+      la.type_start = h->d_typeatoms.as<int>() + h->n_atoms;
+      la.scale = 4.0 * M_PI / h->volume;
+      CK(h, launch_slegendre(la, h->d_f64_tiles.as<F64Tile>() + hS.f64_t0, hS.f64_nt, st),
+         "S (addition theorem) launch");
+      CK(h, cudaEventRecord(h->ev[4], st), "cudaEventRecord");
+    } else {
+      CK(h, launch_opform_S(oa, factored, st), "S operand launch");
+      CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
+      if (int rc = enqueue_contraction(h, hS, n_slots, st, 3, 4)) return rc;
+    }
     // join, then H
     CK(h, cudaStreamWaitEvent(st, h->ev[16], 0), "cudaStreamWaitEvent");
     CK(h, cudaEventRecord(h->ev[8], st), "cudaEventRecord");
@@ -995,6 +1047,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
 
   // graph replay, keyed on everything the captured sequence bakes in
   std::vector<uintptr_t> key{(uintptr_t)A, (uintptr_t)B, (uintptr_t)n_slots, (uintptr_t)h->opt.precision,
+                             (uintptr_t)h->opt.s_method,
                              (uintptr_t)layout, (uintptr_t)h->opt.operands, (uintptr_t)slices_of(h),
                              (uintptr_t)h->d_Z.p, (uintptr_t)h->d_SL.p, (uintptr_t)h->pin_in.p,
                              (uintptr_t)h->d_T.p, (uintptr_t)h->d_stageOut.p, (uintptr_t)h->d_emu_tiles.p,
@@ -1139,6 +1192,7 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
     s.ms_operands = el(9, 2) + el(8, 10);
     s.ms_slice = (h->opt.precision == FLAPW_PREC_EMU) ? el(2, 3) + el(10, 11) : 0.0;
     s.ms_contract = el(3, 4) + el(11, 12);
+    s.ms_s = el(3, 4);
     s.ms_hs_total = el(0, 5);
   }
   s.n_slices = slices_of(h);
@@ -1167,7 +1221,7 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
       const int S_ = slices_of(h);
       const double pairs = S_ * (S_ + 1) / 2.0;
       const double chH = std::ceil(kpk[1] / 64.0) + std::ceil(kpk[2] / 64.0);
-      const double chS = std::ceil((double)s.k_total / 64.0);
+      const double chS = (h->opt.s_method == FLAPW_S_LEGENDRE) ? 0.0 : std::ceil((double)s.k_total / 64.0);
       double tf = 0;
       for (int k = 0; k < h->n_k; ++k) {
         const int ng = (int)(h->goff[k + 1] - h->goff[k]);

@@ -207,6 +207,25 @@ cudaError_t launch_slicer(const double2* Z, int64_t k_alloc, const Prob* probs,
 cudaError_t launch_slicer_rows(const double2* Z, int64_t k_alloc, int64_t rows, int n_slices,
                                __half* SL, int* rexp, cudaStream_t st);
 
+// S by the addition theorem (slegendre.cu), on the 64 x 64 lower tiles of the
+// S problems.
+struct SLegArgs {
+  const Prob* probs;      // problems (row_base - s_row0 = first global plane wave)
+  int64_t s_row0;
+  int64_t g_total;
+  int lmax, n_types;
+  const double* khat;     // [G][3] unit vectors (z for K = 0)
+  const double* al;       // [t][l][G] matching coefficients
+  const double* bl;
+  const double* U;        // [t][l]
+  const double2* ph;      // [atom][G] e^{iK.tau_a}
+  const int* type_atoms;  // atoms grouped by type
+  const int* type_start;  // [n_types + 1]
+  double scale;           // 4 pi / Omega
+};
+cudaError_t launch_khat(const Geom& geo, const GData& gd, double* khat, cudaStream_t st);
+cudaError_t launch_slegendre(const SLegArgs& a, const F64Tile* tiles, int n_tiles, cudaStream_t st);
+
 // Contractions.
 cudaError_t launch_herk_f64(const double2* Z, int64_t k_alloc, const Prob* probs,
                             const F64Tile* tiles, int n_tiles, cudaStream_t st);

@@ -1,0 +1,179 @@
+// Overlap matrix by the addition theorem (an alternative to the S contraction
+// for the library's own matching coefficients).
+//
+// With A_{aLG} = e^{iK.tau_a} Yc_L(K) a_{t,l}(|K|), Yc_L = (4 pi / sqrt(Omega))
+// i^l conj(Y_lm(Khat)) (the Rayleigh matching of Sec. 2), the sum over m in
+// S_{G'G} = sum_a sum_L conj(A_{aLG'}) A_{aLG} + U_{tl}^2 conj(B_{aLG'}) B_{aLG}
+// (Eq. (def_overlap)) collapses by sum_m Y_lm(u) conj(Y_lm(v)) = (2l+1)/(4 pi)
+// P_l(u.v):
+//     S_{G'G} = (4 pi / Omega) sum_t rho_t(G', G) sum_l (2l+1) P_l(Khat'.Khat)
+//               [a_l(K') a_l(K) + U_l^2 b_l(K') b_l(K)],
+//     rho_t(G', G) = sum_{atoms a of type t} conj(e^{iK'.tau_a}) e^{iK.tau_a}.
+// It removes the factor N_L of the contraction: one of the compressions of A
+// and B by mathematical identities that the Conclusions point to.  Per
+// element it costs N_A complex multiply-adds for the structure factors and
+// (l_max + 1) per type for the Legendre sum, against 8 N_A N_L for the
+// contraction.
+//
+// FP64 SIMT (the Legendre recurrence P_{l+1} = ((2l+1) x P_l - l P_{l-1}) /
+// (l+1) and the phase sums need FP64).  CTA tile: 64 x 64 of the lower
+// triangle (the FP64 contraction's tile list), 256 threads with a 4 x 4 block
+// each; per type the atoms' phases stream through shared memory 8 at a time.
+#include "flapw_internal.h"
+
+namespace flapw {
+namespace {
+
+constexpr int kT = 64;
+constexpr int kChunkAtoms = 8;  // keeps the static shared memory under 48 KB
+constexpr int kL1 = kMaxLmax + 1;
+
+// Khat of every plane wave (z for K = 0), the K of ab_prep.
+__global__ void __launch_bounds__(128) khat_kernel(Geom geo, GData gd, double* khat) {
+  const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= geo.g_total) return;
+  const int k = gd.gk[gi];
+  const double q0 = gd.n3[3 * gi] + geo.kfrac[3 * k], q1 = gd.n3[3 * gi + 1] + geo.kfrac[3 * k + 1],
+               q2 = gd.n3[3 * gi + 2] + geo.kfrac[3 * k + 2];
+  double K[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) K[c] = q0 * geo.rec[c] + q1 * geo.rec[3 + c] + q2 * geo.rec[6 + c];
+  const double kabs = sqrt(K[0] * K[0] + K[1] * K[1] + K[2] * K[2]);
+  double* o = khat + 3 * gi;
+  if (kabs > 0) {
+    o[0] = K[0] / kabs;
+    o[1] = K[1] / kabs;
+    o[2] = K[2] / kabs;
+  } else {
+    o[0] = 0.0;
+    o[1] = 0.0;
+    o[2] = 1.0;
+  }
+}
+
+__global__ void __launch_bounds__(256) slegendre_kernel(SLegArgs a, const F64Tile* __restrict__ tiles) {
+  __shared__ double kh[2][kT][3];          // [0] rows G', [1] columns G
+  __shared__ double rad[4][kL1][kT];        // a_l rows, U^2 b_l rows, a_l cols, b_l cols
+  __shared__ double2 phs[2][kChunkAtoms][kT];
+  const F64Tile T = tiles[blockIdx.x];
+  const Prob P = a.probs[T.prob];
+  const int64_t ng = P.n_g;
+  const int64_t g0 = P.row_base - a.s_row0;  // global plane wave of the problem's first row
+  const int r0 = T.ib * kT, c0 = T.jb * kT;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int L1 = a.lmax + 1;
+  const int64_t G = a.g_total;
+  for (int i = tid; i < 2 * kT * 3; i += 256) {
+    const int w = i / (kT * 3), e = i % (kT * 3), g = e / 3, c = e % 3;
+    const int64_t gl = (w == 0 ? r0 : c0) + g;
+    kh[w][g][c] = (gl < ng) ? a.khat[3 * (g0 + gl) + c] : 0.0;
+  }
+  double2 S[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) S[i][j] = make_double2(0.0, 0.0);
+
+  for (int t = 0; t < a.n_types; ++t) {
+    __syncthreads();
+    for (int i = tid; i < 4 * L1 * kT; i += 256) {
+      const int w = i / (L1 * kT), e = i % (L1 * kT), l = e / kT, g = e % kT;
+      const int64_t gl = ((w < 2) ? r0 : c0) + g;
+      double v = 0.0;
+      if (gl < ng) {
+        const int64_t ro = ((int64_t)t * L1 + l) * G + g0 + gl;
+        if (w == 0 || w == 2) v = a.al[ro];
+        else v = a.bl[ro] * ((w == 1) ? a.U[t * L1 + l] * a.U[t * L1 + l] : 1.0);
+      }
+      rad[w][l][g] = v;
+    }
+    // rho_t for this thread's 4 x 4 block
+    double2 rho[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) rho[i][j] = make_double2(0.0, 0.0);
+    const int a0 = a.type_start[t], a1 = a.type_start[t + 1];
+    for (int ab = a0; ab < a1; ab += kChunkAtoms) {
+      const int na = min(kChunkAtoms, a1 - ab);
+      __syncthreads();
+      for (int i = tid; i < 2 * kChunkAtoms * kT; i += 256) {
+        const int w = i / (kChunkAtoms * kT), e = i % (kChunkAtoms * kT), q = e / kT, g = e % kT;
+        const int64_t gl = (w == 0 ? r0 : c0) + g;
+        double2 v = make_double2(0.0, 0.0);
+        if (q < na && gl < ng) v = a.ph[(int64_t)a.type_atoms[ab + q] * G + g0 + gl];
+        phs[w][q][g] = v;
+      }
+      __syncthreads();
+      for (int q = 0; q < na; ++q) {
+        double2 pr[4], pc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          pr[i] = phs[0][q][ty * 4 + i];
+          pc[i] = phs[1][q][tx * 4 + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {  // conj(pr) pc
+            rho[i][j].x = fma(pr[i].x, pc[j].x, fma(pr[i].y, pc[j].y, rho[i][j].x));
+            rho[i][j].y = fma(pr[i].x, pc[j].y, fma(-pr[i].y, pc[j].x, rho[i][j].y));
+          }
+      }
+    }
+    __syncthreads();
+    // Legendre sum of type t, times rho_t
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int ri = ty * 4 + i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int cj = tx * 4 + j;
+        const double x = kh[0][ri][0] * kh[1][cj][0] + kh[0][ri][1] * kh[1][cj][1] + kh[0][ri][2] * kh[1][cj][2];
+        double pm = 1.0, p = x;  // P_{l-1}, P_l from l = 1
+        double Lt = rad[0][0][ri] * rad[2][0][cj] + rad[1][0][ri] * rad[3][0][cj];
+        for (int l = 1; l < L1; ++l) {
+          Lt = fma((double)(2 * l + 1) * p, rad[0][l][ri] * rad[2][l][cj] + rad[1][l][ri] * rad[3][l][cj], Lt);
+          const double pn = ((double)(2 * l + 1) * x * p - (double)l * pm) / (double)(l + 1);
+          pm = p;
+          p = pn;
+        }
+        S[i][j].x = fma(rho[i][j].x, Lt, S[i][j].x);
+        S[i][j].y = fma(rho[i][j].y, Lt, S[i][j].y);
+      }
+    }
+  }
+  // lower triangle of the problem, scaled by 4 pi / Omega
+  double* outd = reinterpret_cast<double*>(P.out);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gr = r0 + ty * 4 + i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gc = c0 + tx * 4 + j;
+      if (gr < ng && gc <= gr) {
+        const int64_t o = (P.layout == FLAPW_LAYOUT_LOWER_PACKED) ? gc * ng - gc * (gc - 1) / 2 + (gr - gc)
+                                                                   : gc * P.ld + gr;
+        outd[2 * o] = a.scale * S[i][j].x;
+        outd[2 * o + 1] = a.scale * S[i][j].y;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_khat(const Geom& geo, const GData& gd, double* khat, cudaStream_t st) {
+  if (geo.g_total == 0) return cudaSuccess;
+  khat_kernel<<<(unsigned)((geo.g_total + 127) / 128), 128, 0, st>>>(geo, gd, khat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slegendre(const SLegArgs& a, const F64Tile* tiles, int n_tiles, cudaStream_t st) {
+  if (n_tiles == 0) return cudaSuccess;
+  if (a.lmax < 0 || a.lmax > kMaxLmax) return cudaErrorInvalidValue;
+  slegendre_kernel<<<n_tiles, 256, 0, st>>>(a, tiles);
+  return cudaGetLastError();
+}
+
+}  // namespace flapw

@@ -1,6 +1,8 @@
 """C-ABI library: loads without a GPU, exports what include/flapw.h declares,
 and its host-side logic (plane-wave set, argument checks) is right."""
 import ctypes
+import os
+import subprocess
 
 import numpy as np
 import pytest
@@ -78,7 +80,29 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
         fl.hs_create(p.lattice, p.pos_frac, p.atom_type, p.mt_radius, 4, p.k_frac, p.kmax, bad)
 
 
-def test_structs_match_header_sizes():
-    # flapw_options: 6 ints + 10 reserved; flapw_stats: 8 doubles + int64 + 8 ints + 8 reserved
-    assert ctypes.sizeof(fl.Options) == 16 * 4
-    assert ctypes.sizeof(fl.Stats) == 8 * 8 + 8 + 8 * 4 + 8 * 4
+def test_structs_match_header_layout(tmp_path):
+    # the ctypes mirrors against the C compiler's view of include/flapw.h
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stddef.h>
+#include <stdio.h>
+#include "flapw.h"
+int main(void) {
+  printf("%zu %zu\\n", sizeof(flapw_options), sizeof(flapw_stats));
+  printf("%zu %zu %zu\\n", offsetof(flapw_options, tile_order), offsetof(flapw_options, s_method),
+         offsetof(flapw_options, reserved));
+  printf("%zu %zu %zu %zu\\n", offsetof(flapw_stats, flops_tensor), offsetof(flapw_stats, k_total),
+         offsetof(flapw_stats, graph_replays), offsetof(flapw_stats, ms_s));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    vals = [int(v) for v in out]
+    assert vals[0] == ctypes.sizeof(fl.Options) and vals[1] == ctypes.sizeof(fl.Stats)
+    assert vals[2:5] == [fl.Options.tile_order.offset, fl.Options.s_method.offset,
+                         fl.Options.reserved.offset]
+    assert vals[5:9] == [fl.Stats.flops_tensor.offset, fl.Stats.k_total.offset,
+                         fl.Stats.graph_replays.offset, fl.Stats.ms_s.offset]
