@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(256) slegendre_kernel(SLegArgs a, const F64Til
   __shared__ double kh[2][kT][3];          // [0] rows G', [1] columns G
   __shared__ double rad[4][kL1][kT];        // a_l rows, U^2 b_l rows, a_l cols, b_l cols
   __shared__ double2 phs[2][kChunkAtoms][kT];
+  __shared__ double rec_ab[kL1][2];  // P_{l+1} = alpha_l x P_l - beta_l P_{l-1}
   const F64Tile T = tiles[blockIdx.x];
   const Prob P = a.probs[T.prob];
   const int64_t ng = P.n_g;
@@ -63,6 +64,10 @@ __global__ void __launch_bounds__(256) slegendre_kernel(SLegArgs a, const F64Til
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int L1 = a.lmax + 1;
   const int64_t G = a.g_total;
+  if (tid < kL1) {
+    rec_ab[tid][0] = (double)(2 * tid + 1) / (double)(tid + 1);
+    rec_ab[tid][1] = (double)tid / (double)(tid + 1);
+  }
   for (int i = tid; i < 2 * kT * 3; i += 256) {
     const int w = i / (kT * 3), e = i % (kT * 3), g = e / 3, c = e % 3;
     const int64_t gl = (w == 0 ? r0 : c0) + g;
@@ -81,9 +86,13 @@ __global__ void __launch_bounds__(256) slegendre_kernel(SLegArgs a, const F64Til
       const int64_t gl = ((w < 2) ? r0 : c0) + g;
       double v = 0.0;
       if (gl < ng) {
+        // rows carry the factor 2l + 1, and U^2 on b_l
         const int64_t ro = ((int64_t)t * L1 + l) * G + g0 + gl;
-        if (w == 0 || w == 2) v = a.al[ro];
-        else v = a.bl[ro] * ((w == 1) ? a.U[t * L1 + l] * a.U[t * L1 + l] : 1.0);
+        const double u = a.U[t * L1 + l];
+        if (w == 0) v = (2 * l + 1) * a.al[ro];
+        else if (w == 1) v = (2 * l + 1) * u * u * a.bl[ro];
+        else if (w == 2) v = a.al[ro];
+        else v = a.bl[ro];
       }
       rad[w][l][g] = v;
     }
@@ -131,10 +140,10 @@ __global__ void __launch_bounds__(256) slegendre_kernel(SLegArgs a, const F64Til
         const int cj = tx * 4 + j;
         const double x = kh[0][ri][0] * kh[1][cj][0] + kh[0][ri][1] * kh[1][cj][1] + kh[0][ri][2] * kh[1][cj][2];
         double pm = 1.0, p = x;  // P_{l-1}, P_l from l = 1
-        double Lt = rad[0][0][ri] * rad[2][0][cj] + rad[1][0][ri] * rad[3][0][cj];
+        double Lt = fma(rad[0][0][ri], rad[2][0][cj], rad[1][0][ri] * rad[3][0][cj]);
         for (int l = 1; l < L1; ++l) {
-          Lt = fma((double)(2 * l + 1) * p, rad[0][l][ri] * rad[2][l][cj] + rad[1][l][ri] * rad[3][l][cj], Lt);
-          const double pn = ((double)(2 * l + 1) * x * p - (double)l * pm) / (double)(l + 1);
+          Lt = fma(p, fma(rad[0][l][ri], rad[2][l][cj], rad[1][l][ri] * rad[3][l][cj]), Lt);
+          const double pn = fma(rec_ab[l][0] * x, p, -rec_ab[l][1] * pm);
           pm = p;
           p = pn;
         }
