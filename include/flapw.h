@@ -84,7 +84,8 @@ typedef struct flapw_options {
                      4/2/8 row blocks of 256), ignored when autotune is on */
   int s_method;   /* FLAPW_S_CONTRACTION (default): S = Z_S^H Z_S like H;
                      FLAPW_S_LEGENDRE: S by the addition theorem (requires
-                     FLAPW_OPERANDS_FACTORED; FP64 in either precision) */
+                     FLAPW_OPERANDS_FACTORED; in FP64 on the FP64 path, in
+                     double-float FP32 pairs on the emulated path) */
   int reserved[8];
 } flapw_options;
 

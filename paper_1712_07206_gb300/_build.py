@@ -33,6 +33,7 @@ def _deps():
     files = [os.path.join(SRC, s) for s in SOURCES] + [os.path.join(SRC, "flapw_internal.h"),
                                                        os.path.join(SRC, "tc_common.cuh"),
                                                        os.path.join(SRC, "fixed64.cuh"),
+                                                       os.path.join(SRC, "dfloat.cuh"),
                                                        os.path.join(ROOT, "include", "flapw.h")]
     return max(os.path.getmtime(f) for f in files)
 

@@ -119,6 +119,7 @@ struct flapw_ctx {
   // factors in FP64 and sliced, their scale exponents, tiles and tensor maps
   DevBuf d_opA, d_opB, d_opSLA, d_opSLB, d_oprexp, d_optiles, d_opP;
   DevBuf d_khat, d_typeatoms;    // S by the addition theorem: Khat per G, atoms by type
+  DevBuf d_sdf;                  // its double-float inputs (emulated precision)
   bool khat_valid = false;       // both depend on the crystal only
   std::vector<OpTile> optiles;
   CUtensorMap opmap_a{}, opmap_b{};
@@ -793,6 +794,9 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     CK(h, cudaDeviceSynchronize(), "Khat");
     h->khat_valid = true;
   }
+  if (s_legendre && h->opt.precision == FLAPW_PREC_EMU)
+    CK(h, h->d_sdf.ensure(slegendre_df_floats2(h->n_types, h->lmax, h->n_atoms, h->g_total) * 8),
+       "workspace");
   // emulated path with factored operands: the H operands come from the
   // tensor-core product of conj(C^H) and W (opgemm.cu)
   const bool tc_ops = factored && h->opt.precision == FLAPW_PREC_EMU;
@@ -988,6 +992,8 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       la.type_atoms = h->d_typeatoms.as<int>();
       la.type_start = h->d_typeatoms.as<int>() + h->n_atoms;
       la.scale = 4.0 * M_PI / h->volume;
+      la.n_atoms = h->n_atoms;
+      la.dfw = (h->opt.precision == FLAPW_PREC_EMU) ? h->d_sdf.as<float2>() : nullptr;
       CK(h, launch_slegendre(la, h->d_f64_tiles.as<F64Tile>() + hS.f64_t0, hS.f64_nt, st),
          "S (addition theorem) launch");
       CK(h, cudaEventRecord(h->ev[4], st), "cudaEventRecord");

@@ -222,7 +222,11 @@ struct SLegArgs {
   const int* type_atoms;  // atoms grouped by type
   const int* type_start;  // [n_types + 1]
   double scale;           // 4 pi / Omega
+  int n_atoms;
+  float2* dfw;            // double-float workspace (slegendre_df_floats2 pairs):
+                          // evaluate in double-float; null: in FP64
 };
+size_t slegendre_df_floats2(int n_types, int lmax, int n_atoms, int64_t G);
 cudaError_t launch_khat(const Geom& geo, const GData& gd, double* khat, cudaStream_t st);
 cudaError_t launch_slegendre(const SLegArgs& a, const F64Tile* tiles, int n_tiles, cudaStream_t st);
 

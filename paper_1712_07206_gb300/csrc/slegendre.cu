@@ -15,10 +15,14 @@
 // (l_max + 1) per type for the Legendre sum, against 8 N_A N_L for the
 // contraction.
 //
-// FP64 SIMT (the Legendre recurrence P_{l+1} = ((2l+1) x P_l - l P_{l-1}) /
-// (l+1) and the phase sums need FP64).  CTA tile: 64 x 64 of the lower
-// triangle (the FP64 contraction's tile list), 256 threads with a 4 x 4 block
-// each; per type the atoms' phases stream through shared memory 8 at a time.
+// The Legendre recurrence P_{l+1} = ((2l+1) x P_l - l P_{l-1}) / (l+1) and the
+// phase sums need more than FP32: the FP64 path evaluates them in FP64, the
+// emulated path in double-float arithmetic on the FP32 pipes (dfloat.cuh; a
+// pre-pass splits the inputs into FP32 pairs), which GB300 issues 64 times
+// faster than FP64.  CTA tile: 64 x 64 of the lower triangle (the FP64
+// contraction's tile list), 256 threads with a 4 x 4 block each; per type the
+// atoms' phases stream through shared memory 8 at a time.
+#include "dfloat.cuh"
 #include "flapw_internal.h"
 
 namespace flapw {
@@ -170,6 +174,157 @@ __global__ void __launch_bounds__(256) slegendre_kernel(SLegArgs a, const F64Til
   }
 }
 
+// Double-float copies of the kernel's inputs: rows (2l+1) a_l and (2l+1) U^2
+// b_l, columns a_l and b_l ([4][t][l][G]), phases ([atom][G] as Re, Im
+// pairs) and Khat ([G][3]).  One thread per plane wave.
+__global__ void __launch_bounds__(128) slegendre_split_kernel(SLegArgs a) {
+  const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t G = a.g_total;
+  if (gi >= G) return;
+  const int L1 = a.lmax + 1;
+  const int64_t nr = (int64_t)a.n_types * L1 * G;
+  float2* rad = a.dfw;
+  float2* ph = rad + 4 * nr;
+  float2* kh = ph + 2 * (int64_t)a.n_atoms * G;
+  for (int t = 0; t < a.n_types; ++t)
+    for (int l = 0; l < L1; ++l) {
+      const int64_t ro = ((int64_t)t * L1 + l) * G + gi;
+      const double u = a.U[t * L1 + l], al = a.al[ro], bl = a.bl[ro];
+      rad[ro] = dfl::split((2 * l + 1) * al);
+      rad[nr + ro] = dfl::split((2 * l + 1) * u * u * bl);
+      rad[2 * nr + ro] = dfl::split(al);
+      rad[3 * nr + ro] = dfl::split(bl);
+    }
+  for (int at = 0; at < a.n_atoms; ++at) {
+    const double2 v = a.ph[(int64_t)at * G + gi];
+    ph[2 * ((int64_t)at * G + gi)] = dfl::split(v.x);
+    ph[2 * ((int64_t)at * G + gi) + 1] = dfl::split(v.y);
+  }
+  for (int c = 0; c < 3; ++c) kh[3 * gi + c] = dfl::split(a.khat[3 * gi + c]);
+}
+
+// slegendre_kernel in double-float.
+__global__ void __launch_bounds__(256) slegendre_df_kernel(SLegArgs a, const F64Tile* __restrict__ tiles) {
+  using dfl::df;
+  __shared__ float2 kh[2][kT][3];
+  __shared__ float2 rad[4][kL1][kT];
+  __shared__ float4 phs[2][kChunkAtoms][kT];
+  __shared__ float2 rec_ab[kL1][2];
+  const F64Tile T = tiles[blockIdx.x];
+  const Prob P = a.probs[T.prob];
+  const int64_t ng = P.n_g;
+  const int64_t g0 = P.row_base - a.s_row0;
+  const int r0 = T.ib * kT, c0 = T.jb * kT;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int L1 = a.lmax + 1;
+  const int64_t G = a.g_total;
+  const int64_t nr = (int64_t)a.n_types * L1 * G;
+  const float2* radg = a.dfw;
+  const float4* phg = reinterpret_cast<const float4*>(a.dfw + 4 * nr);
+  const float2* khg = a.dfw + 4 * nr + 2 * (int64_t)a.n_atoms * G;
+  const float2 zero2 = make_float2(0.f, 0.f);
+  if (tid < kL1) {
+    rec_ab[tid][0] = dfl::split((double)(2 * tid + 1) / (double)(tid + 1));
+    rec_ab[tid][1] = dfl::split((double)tid / (double)(tid + 1));
+  }
+  for (int i = tid; i < 2 * kT * 3; i += 256) {
+    const int w = i / (kT * 3), e = i % (kT * 3), g = e / 3, c = e % 3;
+    const int64_t gl = (w == 0 ? r0 : c0) + g;
+    kh[w][g][c] = (gl < ng) ? khg[3 * (g0 + gl) + c] : zero2;
+  }
+  df Sr[4][4], Si[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) Sr[i][j] = Si[i][j] = df{0.f, 0.f};
+
+  for (int t = 0; t < a.n_types; ++t) {
+    __syncthreads();
+    for (int i = tid; i < 4 * L1 * kT; i += 256) {
+      const int w = i / (L1 * kT), e = i % (L1 * kT), l = e / kT, g = e % kT;
+      const int64_t gl = ((w < 2) ? r0 : c0) + g;
+      rad[w][l][g] = (gl < ng) ? radg[w * nr + ((int64_t)t * L1 + l) * G + g0 + gl] : zero2;
+    }
+    df rr[4][4], ri[4][4];  // rho_t
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) rr[i][j] = ri[i][j] = df{0.f, 0.f};
+    const int a0 = a.type_start[t], a1 = a.type_start[t + 1];
+    for (int ab = a0; ab < a1; ab += kChunkAtoms) {
+      const int na = min(kChunkAtoms, a1 - ab);
+      __syncthreads();
+      for (int i = tid; i < 2 * kChunkAtoms * kT; i += 256) {
+        const int w = i / (kChunkAtoms * kT), e = i % (kChunkAtoms * kT), q = e / kT, g = e % kT;
+        const int64_t gl = (w == 0 ? r0 : c0) + g;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < na && gl < ng) v = phg[(int64_t)a.type_atoms[ab + q] * G + g0 + gl];
+        phs[w][q][g] = v;
+      }
+      __syncthreads();
+      for (int q = 0; q < na; ++q) {
+        float4 pr[4], pc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          pr[i] = phs[0][q][ty * 4 + i];
+          pc[i] = phs[1][q][tx * 4 + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const df ar{pr[i].x, pr[i].y}, ai{pr[i].z, pr[i].w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {  // conj(pr) pc
+            const df br{pc[j].x, pc[j].y}, bi{pc[j].z, pc[j].w};
+            rr[i][j] = dfl::fma(ar, br, dfl::fma(ai, bi, rr[i][j]));
+            ri[i][j] = dfl::fma(ar, bi, dfl::fma(dfl::neg(ai), br, ri[i][j]));
+          }
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int rw = ty * 4 + i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int cl = tx * 4 + j;
+        const df x = dfl::fma(dfl::make(kh[0][rw][0]), dfl::make(kh[1][cl][0]),
+                              dfl::fma(dfl::make(kh[0][rw][1]), dfl::make(kh[1][cl][1]),
+                                       dfl::mul(dfl::make(kh[0][rw][2]), dfl::make(kh[1][cl][2]))));
+        df pm{1.f, 0.f}, p = x;
+        df Lt = dfl::fma(dfl::make(rad[0][0][rw]), dfl::make(rad[2][0][cl]),
+                         dfl::mul(dfl::make(rad[1][0][rw]), dfl::make(rad[3][0][cl])));
+        for (int l = 1; l < L1; ++l) {
+          const df c = dfl::fma(dfl::make(rad[0][l][rw]), dfl::make(rad[2][l][cl]),
+                                dfl::mul(dfl::make(rad[1][l][rw]), dfl::make(rad[3][l][cl])));
+          Lt = dfl::fma(p, c, Lt);
+          const df pn = dfl::fma(dfl::mul(dfl::make(rec_ab[l][0]), x), p,
+                                 dfl::neg(dfl::mul(dfl::make(rec_ab[l][1]), pm)));
+          pm = p;
+          p = pn;
+        }
+        Sr[i][j] = dfl::fma(rr[i][j], Lt, Sr[i][j]);
+        Si[i][j] = dfl::fma(ri[i][j], Lt, Si[i][j]);
+      }
+    }
+  }
+  double* outd = reinterpret_cast<double*>(P.out);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gr = r0 + ty * 4 + i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gc = c0 + tx * 4 + j;
+      if (gr < ng && gc <= gr) {
+        const int64_t o = (P.layout == FLAPW_LAYOUT_LOWER_PACKED) ? gc * ng - gc * (gc - 1) / 2 + (gr - gc)
+                                                                   : gc * P.ld + gr;
+        outd[2 * o] = a.scale * dfl::to_double(Sr[i][j]);
+        outd[2 * o + 1] = a.scale * dfl::to_double(Si[i][j]);
+      }
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_khat(const Geom& geo, const GData& gd, double* khat, cudaStream_t st) {
@@ -178,10 +333,19 @@ cudaError_t launch_khat(const Geom& geo, const GData& gd, double* khat, cudaStre
   return cudaGetLastError();
 }
 
+size_t slegendre_df_floats2(int n_types, int lmax, int n_atoms, int64_t G) {
+  return (size_t)(4 * (int64_t)n_types * (lmax + 1) * G + 2 * (int64_t)n_atoms * G + 3 * G);
+}
+
 cudaError_t launch_slegendre(const SLegArgs& a, const F64Tile* tiles, int n_tiles, cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   if (a.lmax < 0 || a.lmax > kMaxLmax) return cudaErrorInvalidValue;
-  slegendre_kernel<<<n_tiles, 256, 0, st>>>(a, tiles);
+  if (a.dfw) {
+    slegendre_split_kernel<<<(unsigned)((a.g_total + 127) / 128), 128, 0, st>>>(a);
+    slegendre_df_kernel<<<n_tiles, 256, 0, st>>>(a, tiles);
+  } else {
+    slegendre_kernel<<<n_tiles, 256, 0, st>>>(a, tiles);
+  }
   return cudaGetLastError();
 }
 
