@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
   __shared__ int perm[kMaxN], blk[kMaxN], outrow[kMaxN];
   __shared__ double lam[kMaxN];
   __shared__ double2 qv[kMaxN][2];
+  __shared__ double2 col0[kMaxN], col1[kMaxN], lc0[kMaxN], lc1[kMaxN];  // pivot columns, L columns
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ double s_colmax, s_rowmax;
@@ -175,26 +176,33 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
     }
     __syncthreads();
     const int m = n - k - kstep;  // trailing size
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     if (kstep == 1) {
       const double d = A[(int64_t)k * n + k].x;
       if (d != 0.0) {
         const double rd = 1.0 / d;
-        for (int idx = tid; idx < m * m; idx += nt) {
-          const int ii = idx / m, jj = idx % m;
-          if (jj > ii) continue;
-          const int i = k + 1 + ii, j = k + 1 + jj;
-          const double2 a = A[(int64_t)i * n + k], b = A[(int64_t)j * n + k];
-          double2 u = cmul(a, cconj(b));
-          double2 x = A[(int64_t)i * n + j];
-          x.x -= u.x * rd;
-          x.y = (i == j) ? 0.0 : x.y - u.y * rd;
-          A[(int64_t)i * n + j] = x;
-        }
-        __syncthreads();
+        // pivot column a (unscaled) and L column l = a / d, once per step
         for (int i = k + 1 + tid; i < n; i += nt) {
           const double2 a = A[(int64_t)i * n + k];
-          A[(int64_t)i * n + k] = make_double2(a.x * rd, a.y * rd);
+          col0[i] = a;
+          lc0[i] = make_double2(a.x * rd, a.y * rd);
         }
+        __syncthreads();
+        // A[i][j] -= l_i conj(a_j) on the lower trailing triangle: a warp per
+        // row, lanes along the row (contiguous j)
+        for (int i = k + 1 + warp; i < n; i += nw) {
+          const double2 li = lc0[i];
+          double2* row = A + (int64_t)i * n;
+          for (int j = k + 1 + lane; j <= i; j += 32) {
+            const double2 aj = col0[j];
+            double2 x = row[j];
+            x.x = fma(-li.x, aj.x, fma(-li.y, aj.y, x.x));
+            x.y = (i == j) ? 0.0 : fma(-li.y, aj.x, fma(li.x, aj.y, x.y));
+            row[j] = x;
+          }
+        }
+        __syncthreads();
+        for (int i = k + 1 + tid; i < n; i += nt) A[(int64_t)i * n + k] = lc0[i];
       }
       if (tid == 0) {
         lam[k] = d;
@@ -210,30 +218,35 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
         if (tid == 0) s_bad = 1;
       } else {
         const double rdet = 1.0 / det;
-        // W D^{-1}:  l1 = (w1 d22 - w2 d21)/det,  l2 = (w2 d11 - w1 conj(d21))/det
-        for (int idx = tid; idx < m * m; idx += nt) {
-          const int ii = idx / m, jj = idx % m;
-          if (jj > ii) continue;
-          const int i = k + 2 + ii, j = k + 2 + jj;
-          const double2 w1 = A[(int64_t)i * n + k], w2 = A[(int64_t)i * n + k + 1];
-          const double2 t1 = cmul(w2, d21);
-          const double2 t2 = cmul(w1, cconj(d21));
-          const double2 l1 = make_double2((w1.x * d22 - t1.x) * rdet, (w1.y * d22 - t1.y) * rdet);
-          const double2 l2 = make_double2((w2.x * d11 - t2.x) * rdet, (w2.y * d11 - t2.y) * rdet);
-          const double2 v1 = A[(int64_t)j * n + k], v2 = A[(int64_t)j * n + k + 1];
-          const double2 u = cmul(l1, cconj(v1)), u2 = cmul(l2, cconj(v2));
-          double2 x = A[(int64_t)i * n + j];
-          x.x -= u.x + u2.x;
-          x.y = (i == j) ? 0.0 : x.y - (u.y + u2.y);
-          A[(int64_t)i * n + j] = x;
-        }
-        __syncthreads();
+        // pivot columns w1, w2 (unscaled) and L = W D^{-1}:
+        //   l1 = (w1 d22 - w2 d21)/det,  l2 = (w2 d11 - w1 conj(d21))/det
         for (int i = k + 2 + tid; i < n; i += nt) {
           const double2 w1 = A[(int64_t)i * n + k], w2 = A[(int64_t)i * n + k + 1];
           const double2 t1 = cmul(w2, d21);
           const double2 t2 = cmul(w1, cconj(d21));
-          A[(int64_t)i * n + k] = make_double2((w1.x * d22 - t1.x) * rdet, (w1.y * d22 - t1.y) * rdet);
-          A[(int64_t)i * n + k + 1] = make_double2((w2.x * d11 - t2.x) * rdet, (w2.y * d11 - t2.y) * rdet);
+          col0[i] = w1;
+          col1[i] = w2;
+          lc0[i] = make_double2((w1.x * d22 - t1.x) * rdet, (w1.y * d22 - t1.y) * rdet);
+          lc1[i] = make_double2((w2.x * d11 - t2.x) * rdet, (w2.y * d11 - t2.y) * rdet);
+        }
+        __syncthreads();
+        // A[i][j] -= l1_i conj(w1_j) + l2_i conj(w2_j), lower trailing triangle
+        for (int i = k + 2 + warp; i < n; i += nw) {
+          const double2 l1 = lc0[i], l2 = lc1[i];
+          double2* row = A + (int64_t)i * n;
+          for (int j = k + 2 + lane; j <= i; j += 32) {
+            const double2 v1 = col0[j], v2 = col1[j];
+            double2 x = row[j];
+            x.x = fma(-l1.x, v1.x, fma(-l1.y, v1.y, fma(-l2.x, v2.x, fma(-l2.y, v2.y, x.x))));
+            x.y = (i == j) ? 0.0
+                           : fma(-l1.y, v1.x, fma(l1.x, v1.y, fma(-l2.y, v2.x, fma(l2.x, v2.y, x.y))));
+            row[j] = x;
+          }
+        }
+        __syncthreads();
+        for (int i = k + 2 + tid; i < n; i += nt) {
+          A[(int64_t)i * n + k] = lc0[i];
+          A[(int64_t)i * n + k + 1] = lc1[i];
         }
       }
       if (tid == 0) {
