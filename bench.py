@@ -139,7 +139,8 @@ def run_ours(args):
     layout = fl.LAYOUT_LOWER_PACKED if p.layout == "packed" else fl.LAYOUT_LOWER_FULL
     opt = fl.default_options(precision=fl.PREC_EMU, layout=layout, operands=operands, n_slices=args.slices,
                              tile_order=args.tile_order, use_graph=1 if args.graph else 0,
-                             s_method=fl.S_LEGENDRE if args.s_method == "legendre" else fl.S_CONTRACTION)
+                             s_method=fl.S_LEGENDRE if args.s_method == "legendre" else fl.S_CONTRACTION,
+                             h_method=fl.H_ALG3 if args.h_method == "alg3" else fl.H_FACTORED)
     h = fl.from_problem(p, opt)
     ngs = [h.num_g(k) for k in range(p.n_k)]
     flops = hs_flops(p, ngs)
@@ -199,7 +200,10 @@ def run_ours(args):
     peak, peak_kind = (bf16_sus, "sustained") if k_ms >= 1000.0 else (bf16_burst, "burst")
     achieved = st["flops_tensor"] / (k_ms * 1e-3) / 1e12
     n_pairs = args.slices * (args.slices + 1) // 2
-    alg_tensor = n_pairs * 4.0 * st["k_total"] * float(np.sum(np.asarray(ngs, float) ** 2)) * 2
+    # slice-pair products of the timed launches: H (K = k_total) and, unless S
+    # comes from the addition theorem, S (K = 2 N_A N_L)
+    k_s = 0 if args.s_method == "legendre" else 2 * p.n_atoms * p.n_L
+    alg_tensor = n_pairs * 4.0 * (st["k_total"] + k_s) * float(np.sum(np.asarray(ngs, float) ** 2))
     achieved_alg = alg_tensor / (k_ms * 1e-3) / 1e12
     stage = {k: round(st[k], 4) for k in ("ms_ab", "ms_factor", "ms_operands", "ms_slice", "ms_contract",
                                           "ms_hs_total")}
@@ -211,7 +215,8 @@ def run_ours(args):
         H64 = [torch.zeros_like(x) for x in H]
         S64 = [torch.zeros_like(x) for x in S]
         h.set_options(fl.default_options(precision=fl.PREC_FP64, layout=layout, operands=operands,
-                                         use_graph=1 if args.graph else 0))
+                                         use_graph=1 if args.graph else 0, s_method=opt.s_method,
+                                         h_method=opt.h_method))
         f_ms = []
         for i in range(args.fp64_steps + 1):
             flush.zero_()
@@ -225,17 +230,18 @@ def run_ours(args):
                 f_ms.append(e0.elapsed_time(e1))
         f64_ms = float(np.mean(f_ms))
         h.set_options(opt)
-    # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
+    # end-to-end through the C ABI: the step's inputs (radial data, T, U, slots)
+    # from host memory and its results H and S into pinned host buffers, copies
+    # inside the timed region; A and B, an intermediate of the step, stay in
+    # device memory
     e2e = None
     if args.e2e:
-        Ah = torch.empty(nab, dtype=torch.complex128).pin_memory()
-        Bh = torch.empty_like(Ah).pin_memory()
         Hh = [torch.empty(outsz(ng), dtype=torch.complex128).pin_memory() for ng in ngs]
         Sh = [torch.empty(outsz(ng), dtype=torch.complex128).pin_memory() for ng in ngs]
 
         def step_host():
-            h.build_AB(p.radial, Ah, Bh, stream)
-            h.build_HS(p.T, p.atom_slot, p.U, Ah, Bh, Hh, Sh, stream)
+            h.build_AB(p.radial, A, B, stream)
+            h.build_HS(p.T, p.atom_slot, p.U, A, B, Hh, Sh, stream)
             h.sync()
 
         step_host()
@@ -244,10 +250,8 @@ def run_ours(args):
         for _ in range(args.e2e_steps):
             step_host()
         e_ms = (time.perf_counter() - t0) * 1e3 / args.e2e_steps
-        ab_bytes = 2 * nab * 16
-        h2d = p.T.nbytes + p.U.nbytes + p.radial.nbytes + p.atom_slot.nbytes + \
-            (ab_bytes if operands == fl.OPERANDS_FROM_AB else 0)
-        d2h = ab_bytes + 2 * sum(outsz(ng) for ng in ngs) * 16
+        h2d = p.T.nbytes + p.U.nbytes + p.radial.nbytes + p.atom_slot.nbytes
+        d2h = 2 * sum(outsz(ng) for ng in ngs) * 16
         e2e = {"value": round(flops / (e_ms * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
                "ms_per_step": round(e_ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     value = flops / (ms * 1e-3) / 1e12 * ws
@@ -262,6 +266,7 @@ def run_ours(args):
                    "K": int(st["k_total"]), "slices": args.slices, "operands": args.operands,
                    "layout": p.layout, "l2": "256 MB L2 flush between steps; A/B 166 MB and operands exceed L2",
                    "flops_per_step": flops, "graph_replay": bool(args.graph), "s_method": args.s_method,
+                   "h_method": args.h_method,
                    "parallelism": f"replicas{ws}"},
         "fp64_path": None if f64_ms is None else {
             "value": round(flops / (f64_ms * 1e-3) / 1e12 * ws, 4), "unit": "TFLOP/s",
@@ -271,16 +276,13 @@ def run_ours(args):
         "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak,
                      "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": args.traffic,
                      "kernel": "herk_emu_kernel (" + ("H launch; S by the addition theorem"
-                                                      if args.s_method == "legendre" else "S and H launches") + ")",
+                                                      if args.s_method == "legendre" else "S and H launches")
+                               + ("; H as Alg. 3's L^H R" if args.h_method == "alg3" else "") + ")",
                      "kernel_ms": round(k_ms, 4),
                      "achieved_algorithmic": round(achieved_alg, 2),
                      "peak_source": f"{src} bf16 {peak_kind} x 1.0 (fp16 = bf16 nominal rate)"},
         "e2e": e2e,
-        # per step: ab_prep, ab_assemble, tfactor, layout, opform_S, slicer and
-        # contraction for the S half and for the H half, and the H operands:
-        # with factored operands W and conj(C^H) formed and sliced (4 kernels),
-        # their tensor-core product and the per-atom phases, else opform_H
-        "gpu_launches": (15 if args.operands == "factored" else 10) * args.steps,
+        "gpu_launches": launches_per_step(args) * args.steps,
         "clocks": clk,
         "timed_wall_s": round(t_wall, 3),
     }
@@ -294,6 +296,23 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def launches_per_step(args):
+    """Kernels one timed step launches: ab_prep and ab_assemble; the S half
+    (opform_S, slicer, contraction; or the addition theorem's split and
+    double-float kernels); the H half's slicer and contraction, and its
+    operands: tfactor and layout, then either W and conj(C^H) formed and
+    sliced (4 kernels), their tensor-core product and the per-atom phases
+    (factored operands) or opform_H (from A/B).  Alg. 3 has no tfactor and
+    layout; its operand product is the same tensor-core sequence (factored
+    operands) or an FP64 kernel (from A/B), followed by the copy of A and B."""
+    n = 2
+    n += 2 if args.s_method == "legendre" else 3
+    n += 2
+    tc = 6 if args.operands == "factored" else 1
+    n += (tc + 1) if args.h_method == "alg3" else (2 + tc)
+    return n
 
 
 def refined_cpu(p, args):
@@ -415,6 +434,9 @@ def main():
     ap.add_argument("--cpu-cols", type=int, default=48)
     ap.add_argument("--refined-cols", type=int, default=1024,
                     help="columns of the host-BLAS Alg. 3 comparator")
+    ap.add_argument("--h-method", choices=["factored", "alg3"], default="factored",
+                    help="H as one Hermitian rank-K update after factorising T (default) or by the "
+                         "paper's Alg. 3 sequence (zher2k + zherkx as one L^H R contraction)")
     ap.add_argument("--s-method", choices=["contraction", "legendre"], default="contraction",
                     help="S by the slice contraction (default) or by the addition theorem")
     ap.add_argument("--graph", action="store_true",

@@ -70,6 +70,19 @@ typedef struct flapw_ctx* flapw_handle;
 #define FLAPW_S_CONTRACTION 0
 #define FLAPW_S_LEGENDRE 1
 
+/* How build_HS forms H.  FLAPW_H_FACTORED factorises each T block (see
+ * flapw_build_HS) and contracts one Hermitian rank-K update, K = 2 N_A N_L.
+ * FLAPW_H_ALG3 follows the operation sequence of the paper's refined
+ * algorithm (Sec. 5.1, Alg. 3) without any factorisation: with
+ *   X_a = T^BA A_a + (1/2) T^BB B_a   and   Y_a = T^AA A_a,
+ *   H = X^H B + B^H X + A^H Y          (zher2k + zherkx of Alg. 3),
+ * evaluated as one lower-triangle contraction L^H R over K = 3 N_A N_L rows,
+ * L_a = [X_a; B_a; A_a], R_a = [B_a; X_a; Y_a].  It reads the blocks
+ * T^AA, T^BA, T^BB (T Hermitian, lower triangle given) and executes 1.5 x the
+ * contraction flops of FLAPW_H_FACTORED. */
+#define FLAPW_H_FACTORED 0
+#define FLAPW_H_ALG3 1
+
 typedef struct flapw_options {
   int precision; /* FLAPW_PREC_EMU (default) or FLAPW_PREC_FP64 */
   int n_slices;  /* emulation: 7-bit slices per operand entry, 4..8 (0 = default 7) */
@@ -86,7 +99,8 @@ typedef struct flapw_options {
                      FLAPW_S_LEGENDRE: S by the addition theorem (requires
                      FLAPW_OPERANDS_FACTORED; in FP64 on the FP64 path, in
                      double-float FP32 pairs on the emulated path) */
-  int reserved[8];
+  int h_method;   /* FLAPW_H_FACTORED (default) or FLAPW_H_ALG3 */
+  int reserved[7];
 } flapw_options;
 
 typedef struct flapw_stats {
@@ -98,7 +112,8 @@ typedef struct flapw_stats {
   double ms_hs_total;  /* whole build_HS */
   double flops_herk;   /* 16 N_A N_L sum_k N_G(k)^2: H and S in the Hermitian rank-K count */
   double flops_tensor; /* tensor-core flops executed by the contraction */
-  int64_t k_total;     /* inner dimension K = 2 N_A N_L */
+  int64_t k_total;     /* inner dimension of the H contraction: K = 2 N_A N_L
+                          (3 N_A N_L with FLAPW_H_ALG3) */
   int n_pos;           /* rows of the H operand with sigma = +1 (all atoms) */
   int n_neg;           /* rows with sigma = -1 */
   int n_pivot2;        /* 2x2 pivots taken by the factorisation (all slots) */
@@ -179,6 +194,8 @@ int flapw_build_AB(flapw_handle h, const double* radial, void* A, void* B, void*
  * generalised to indefinite T), so that H = Z^H diag(sigma) Z with
  * Z_a = C^H [A_a; B_a] and S = Z_S^H Z_S with Z_S,a = [A_a; U B_a]: one
  * lower-triangle rank-K contraction each, K = 2 N_A N_L (Fig. agg stacking).
+ * With options.h_method = FLAPW_H_ALG3 H is formed without the factorisation
+ * as described at FLAPW_H_ALG3.
  * Errors: FLAPW_ERR_FACTOR if a block is singular in a way the pivoting
  * cannot handle; FLAPW_ERR_OOM if the workspaces do not fit. */
 int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom_slot,
@@ -225,7 +242,8 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st);
 /* Debug export of the last T factorisation of slot `slot`: CH[(2N_L)^2]
  * complex row-major receives C^H with its rows ordered sigma = +1 first,
  * then -1; *n_pos and *n_neg give the counts (rows past them are zero).
- * Synchronises the stream. */
+ * Synchronises the stream.  FLAPW_ERR_STATE if the last build_HS ran with
+ * FLAPW_H_ALG3 (no factorisation). */
 int flapw_get_factor(flapw_handle h, int slot, double* CH, int* n_pos, int* n_neg);
 
 /* Message for the last error on h (or of the last handle-less call if h is NULL). */

@@ -29,6 +29,7 @@ PREC_FP64, PREC_EMU = 0, 1
 LAYOUT_LOWER_FULL, LAYOUT_LOWER_PACKED = 0, 1
 OPERANDS_FROM_AB, OPERANDS_FACTORED = 0, 1
 S_CONTRACTION, S_LEGENDRE = 0, 1
+H_FACTORED, H_ALG3 = 0, 1
 ERR = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_FACTOR",
        -5: "ERR_TIMEOUT", -6: "ERR_STATE", -7: "ERR_UNSUPPORTED"}
 
@@ -42,7 +43,8 @@ class FlapwError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_slices", ctypes.c_int), ("layout", ctypes.c_int),
                 ("operands", ctypes.c_int), ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("tile_order", ctypes.c_int), ("s_method", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("tile_order", ctypes.c_int), ("s_method", ctypes.c_int), ("h_method", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 class Stats(ctypes.Structure):

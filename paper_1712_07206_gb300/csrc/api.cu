@@ -145,6 +145,9 @@ struct flapw_ctx {
   int tmap_s = 0;
 
   cudaStream_t cap_stream = nullptr, aux_stream = nullptr;
+  // host-memory S outputs go back on their own stream while H is computed
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copy = nullptr;
   // events: 0 start, 1 factor done (aux), 2 S operands done, 3 S sliced, 4 S contracted,
   // 5 end, 6/7 build_AB, 8 H operands start, 9 S operands start, 10 H operands done,
   // 11 H sliced, 12 H contracted, 13 fork, 14/15 autotune, 16 auxiliary work done (join)
@@ -153,6 +156,7 @@ struct flapw_ctx {
   cudaStream_t last_stream = nullptr;
   flapw_stats stats{};
   int last_n_slots = 0;
+  bool last_alg3 = false;        // the last build_HS formed H by the paper's Alg. 3
 
   // CUDA graph replay of build_HS
   cudaGraphExec_t gexec = nullptr;
@@ -164,6 +168,8 @@ struct flapw_ctx {
       if (e) cudaEventDestroy(e);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (aux_stream) cudaStreamDestroy(aux_stream);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    if (ev_copy) cudaEventDestroy(ev_copy);
     (void)cudaGetLastError();
   }
 };
@@ -202,6 +208,8 @@ int check_options(flapw_ctx* h, const flapw_options& o) {
     return fail(h, FLAPW_ERR_ARG, "options.s_method is not a FLAPW_S_* value");
   if (o.s_method == FLAPW_S_LEGENDRE && o.operands != FLAPW_OPERANDS_FACTORED)
     return fail(h, FLAPW_ERR_ARG, "options.s_method FLAPW_S_LEGENDRE needs FLAPW_OPERANDS_FACTORED");
+  if (o.h_method != FLAPW_H_FACTORED && o.h_method != FLAPW_H_ALG3)
+    return fail(h, FLAPW_ERR_ARG, "options.h_method is not a FLAPW_H_* value");
   return FLAPW_OK;
 }
 
@@ -214,6 +222,8 @@ int device_setup(flapw_ctx* h) {
   for (auto& e : h->ev) CK(h, cudaEventCreate(&e), "cudaEventCreate");
   CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
   CK(h, cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  CK(h, cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming), "cudaEventCreate");
   CK(h, opform_init(), "constant table upload");
   return FLAPW_OK;
 }
@@ -698,7 +708,11 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   const int nlp = h->lmax + 1;
   const int nk = h->n_k;
   const int64_t K = (int64_t)h->n_atoms * n;
-  if (K >= ((int64_t)1 << 17)) return fail(h, FLAPW_ERR_UNSUPPORTED, "2 N_A N_L must be below 131072");
+  // H by the paper's Alg. 3: L^H R over 3 N_A N_L rows, no factorisation
+  const bool alg3 = h->opt.h_method == FLAPW_H_ALG3;
+  const int64_t K_H = alg3 ? (int64_t)h->n_atoms * 3 * h->n_L : K;
+  if (K_H >= ((int64_t)1 << 17))
+    return fail(h, FLAPW_ERR_UNSUPPORTED, "the H contraction's K (2 N_A N_L, or 3 N_A N_L for Alg. 3) must be below 131072");
   const int layout = h->opt.layout;
 
   // ---- host-side preparation (never captured) ----
@@ -758,16 +772,20 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     dA = h->d_stageA.as<double2>();
     dB = h->d_stageB.as<double2>();
   }
-  // problems: H rows are [0, G_total), S rows [G_total, 2 G_total)
+  // problems: H rows are [0, G_total), S rows [G_total, 2 G_total); with Alg. 3
+  // the H rows hold L, rows [G_total, 2 G_total) R, and S follows at 2 G_total.
+  // The H problems' K split (sigma = +1 / -1) comes from the factorisation.
+  const int64_t s_row0 = alg3 ? 2 * h->g_total : h->g_total;
   std::vector<Prob> probs(2 * nk);
   for (int k = 0; k < nk; ++k) {
     const int ng = (int)(h->goff[k + 1] - h->goff[k]);
-    probs[k] = Prob{(int)h->goff[k], ng, 0, 0, layout, 0, ng, op.dev[k]};
-    probs[nk + k] = Prob{(int)(h->g_total + h->goff[k]), ng, (int)K, 0, layout, 0, ng, op.dev[nk + k]};
+    const int hb = (int)h->goff[k], sb = (int)(s_row0 + h->goff[k]);
+    probs[k] = Prob{hb, ng, alg3 ? (int)K_H : 0, 0, layout, alg3 ? (int)(h->g_total + hb) : hb, ng, op.dev[k]};
+    probs[nk + k] = Prob{sb, ng, (int)K, 0, layout, sb, ng, op.dev[nk + k]};
   }
-  h->rows = 2 * h->g_total;
-  h->k_alloc = round_up(K, kChunk) + kChunk;
-  h->k_terms = K;
+  h->rows = alg3 ? 3 * h->g_total : 2 * h->g_total;
+  h->k_alloc = alg3 ? round_up(K_H, kChunk) : round_up(K, kChunk) + kChunk;
+  h->k_terms = K_H;
   CK(h, h->d_T.ensure(t_bytes), "workspace");
   CK(h, h->d_work.ensure(t_bytes), "workspace");
   CK(h, h->d_CH.ensure(t_bytes), "workspace");
@@ -799,6 +817,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
        "workspace");
   // emulated path with factored operands: the H operands come from the
   // tensor-core product of conj(C^H) and W (opgemm.cu)
+  // (for Alg. 3 the product of M = [[T^BA, T^BB/2], [T^AA, 0]] and W)
   const bool tc_ops = factored && h->opt.precision == FLAPW_PREC_EMU;
   const int op_kp = round_up(n, kChunk);
   const int64_t op_rows_a = (int64_t)n_slots * n, op_rows_b = (int64_t)h->n_types * h->g_total;
@@ -847,14 +866,17 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   if (h->tiles_rows_key != h->rows) {
     std::vector<int> rp(h->rows);
     for (int q = 0; q < (int)probs.size(); ++q)
-      for (int g = 0; g < probs[q].n_g; ++g) rp[probs[q].row_base + g] = q;
+      for (int g = 0; g < probs[q].n_g; ++g) {
+        rp[probs[q].row_base + g] = q;
+        rp[probs[q].col_base + g] = q;
+      }
     if (upload(h, h->d_rowprob, rp)) return FLAPW_ERR_CUDA;
   }
   Half hH, hS;
   if (int rc = ensure_tiles(h, probs, nk, h->rows, &hH, &hS, 0, n_slots)) return rc;
   hH.row0 = 0;
-  hH.nrows = h->g_total;
-  hS.row0 = h->g_total;
+  hH.nrows = alg3 ? 2 * h->g_total : h->g_total;
+  hS.row0 = s_row0;
   hS.nrows = h->g_total;
   if (int rc = ensure_slices(h)) return rc;
   CK(h, h->pin_probs.ensure(sizeof(Prob) * probs.size()), "cudaMallocHost");
@@ -876,6 +898,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   std::memcpy(pc + 2 * n_combo + combo_atoms.size(), combo_start.data(), combo_start.size() * 4);
   std::memcpy(h->pin_probs.p, probs.data(), sizeof(Prob) * probs.size());
   h->last_n_slots = n_slots;
+  h->last_alg3 = alg3;
 
   // ---- the enqueued sequence (graph-capturable) ----
   // S needs no factorisation: its operands, slices and contraction run on the
@@ -925,7 +948,9 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     oa.goff = h->d_goff.as<int64_t>();
     oa.g_total = h->g_total;
     oa.h_row0 = 0;
-    oa.s_row0 = h->g_total;
+    oa.s_row0 = s_row0;
+    oa.r_row0 = h->g_total;
+    oa.T = h->d_T.as<double2>();
     oa.A = dA;
     oa.B = dB;
     oa.Yc = h->d_Yc.as<double2>();
@@ -944,18 +969,26 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev[13], 0), "cudaStreamWaitEvent");
     int* oprexp_a = h->d_oprexp.as<int>();
     int* oprexp_b = oprexp_a + op_rows_a;
-    CK(h, launch_tfactor(h->d_T.as<double2>(), n, n_slots, h->d_work.as<double2>(), h->d_CH.as<double2>(),
-                         perm, outrow, npos, nneg, cnt, cnt + 2, h->aux_stream),
-       "T factorisation launch");
-    CK(h, launch_layout(npos, nneg, h->d_slot.as<int>(), h->n_atoms, nk, pos_off, neg_off, kpk,
-                        h->d_probs.as<Prob>(), (int)K, h->aux_stream),
-       "layout launch");
+    if (!alg3) {
+      CK(h, launch_tfactor(h->d_T.as<double2>(), n, n_slots, h->d_work.as<double2>(), h->d_CH.as<double2>(),
+                           perm, outrow, npos, nneg, cnt, cnt + 2, h->aux_stream),
+         "T factorisation launch");
+      CK(h, launch_layout(npos, nneg, h->d_slot.as<int>(), h->n_atoms, nk, pos_off, neg_off, kpk,
+                          h->d_probs.as<Prob>(), (int)K, h->aux_stream),
+         "layout launch");
+    }
     CK(h, cudaEventRecord(h->ev[1], h->aux_stream), "cudaEventRecord");
-    if (tc_ops) {
+    if (tc_ops && alg3) {
+      CK(h, launch_opgemm_build_alg3(h->d_T.as<double2>(), n_slots, n, h->n_L, op_kp, h->d_opA.as<double2>(),
+                                     h->aux_stream),
+         "operand factor launch");
+    } else if (tc_ops) {
       CK(h, launch_opgemm_build(h->d_CH.as<double2>(), perm, n_slots, n, op_kp, nullptr, nullptr, nullptr,
                                 h->n_L, h->lmax, h->n_types, h->g_total, h->d_opA.as<double2>(), nullptr,
                                 h->aux_stream, true),
          "operand factor launch");
+    }
+    if (tc_ops) {
       CK(h, launch_slicer_rows(h->d_opA.as<double2>(), op_kp, op_rows_a, kOpSlices, h->d_opSLA.as<__half>(),
                                oprexp_a, h->aux_stream),
          "operand factor slicer launch");
@@ -980,7 +1013,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       CK(h, cudaEventRecord(h->ev[3], st), "cudaEventRecord");
       SLegArgs la{};
       la.probs = h->d_probs.as<Prob>();
-      la.s_row0 = h->g_total;
+      la.s_row0 = s_row0;
       la.g_total = h->g_total;
       la.lmax = h->lmax;
       la.n_types = h->n_types;
@@ -1001,6 +1034,17 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       CK(h, launch_opform_S(oa, factored, st), "S operand launch");
       CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
       if (int rc = enqueue_contraction(h, hS, n_slots, st, 3, 4)) return rc;
+    }
+    // S outputs in host memory: copied back beside the H work, joined at the end
+    bool s_host = false;
+    for (int i = nk; i < 2 * nk; ++i) s_host = s_host || op.host[i] != nullptr;
+    if (s_host) {
+      CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev[4], 0), "cudaStreamWaitEvent");
+      for (int i = nk; i < 2 * nk; ++i)
+        if (op.host[i])
+          CK(h, cudaMemcpyAsync(op.host[i], op.dev[i], op.bytes[i], cudaMemcpyDeviceToHost, h->copy_stream),
+             "cudaMemcpyAsync");
+      CK(h, cudaEventRecord(h->ev_copy, h->copy_stream), "cudaEventRecord");
     }
     // join, then H
     CK(h, cudaStreamWaitEvent(st, h->ev[16], 0), "cudaStreamWaitEvent");
@@ -1026,17 +1070,23 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       ga.Z = h->d_Z.as<double2>();
       ga.k_alloc = h->k_alloc;
       ga.h_row0 = 0;
+      ga.alg3_nl = alg3 ? h->n_L : 0;
+      ga.r_row0 = h->g_total;
       CK(h, launch_opgemm(h->opmap_a, h->opmap_b, ga, h->d_optiles.as<OpTile>(), (int)h->optiles.size(),
                           cnt + 2, h->num_sms, st),
          "H operand launch");
       CK(h, launch_opgemm_phase(ga, n_combo, st), "H operand phase launch");
+      if (alg3) CK(h, launch_opform_alg3(oa, factored, false, st), "H operand (Alg. 3) copy launch");
+    } else if (alg3) {
+      CK(h, launch_opform_alg3(oa, factored, true, st), "H operand (Alg. 3) launch");
     } else {
       CK(h, launch_opform_H(oa, factored, st), "H operand launch");
     }
     CK(h, cudaEventRecord(h->ev[10], st), "cudaEventRecord");
     if (int rc = enqueue_contraction(h, hH, 0, st, 11, 12)) return rc;
-    for (int i = 0; i < 2 * nk; ++i)
+    for (int i = 0; i < nk; ++i)
       if (op.host[i]) CK(h, cudaMemcpyAsync(op.host[i], op.dev[i], op.bytes[i], cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    if (s_host) CK(h, cudaStreamWaitEvent(st, h->ev_copy, 0), "cudaStreamWaitEvent");
     CK(h, cudaEventRecord(h->ev[5], st), "cudaEventRecord");
     return FLAPW_OK;
   };
@@ -1053,7 +1103,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
 
   // graph replay, keyed on everything the captured sequence bakes in
   std::vector<uintptr_t> key{(uintptr_t)A, (uintptr_t)B, (uintptr_t)n_slots, (uintptr_t)h->opt.precision,
-                             (uintptr_t)h->opt.s_method,
+                             (uintptr_t)h->opt.s_method, (uintptr_t)h->opt.h_method,
                              (uintptr_t)layout, (uintptr_t)h->opt.operands, (uintptr_t)slices_of(h),
                              (uintptr_t)h->d_Z.p, (uintptr_t)h->d_SL.p, (uintptr_t)h->pin_in.p,
                              (uintptr_t)h->d_T.p, (uintptr_t)h->d_stageOut.p, (uintptr_t)h->d_emu_tiles.p,
@@ -1117,7 +1167,7 @@ int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const i
     dH = h->d_stageOut.as<double2>();
   }
   if (h->last_stream) CK(h, cudaStreamSynchronize(h->last_stream), "cudaStreamSynchronize");
-  std::vector<Prob> probs{Prob{0, N, (int)pos.size(), (int)neg.size(), h->opt.layout, 0,
+  std::vector<Prob> probs{Prob{0, N, (int)pos.size(), (int)neg.size(), h->opt.layout, /*col_base*/ 0,
                                h->opt.layout == FLAPW_LAYOUT_LOWER_FULL ? ldh : N, dH}};
   h->rows = N;
   h->k_alloc = k_alloc;
@@ -1205,7 +1255,7 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
   s.n_tiles = (h->opt.precision == FLAPW_PREC_EMU) ? h->n_emu_tiles : h->n_f64_tiles;
   s.tile_order = h->tiles_order;
   if (!h->engine_only) {
-    s.k_total = (int64_t)h->n_atoms * 2 * h->n_L;
+    s.k_total = (int64_t)h->n_atoms * (h->last_alg3 ? 3 : 2) * h->n_L;
     double ng2 = 0;
     for (int k = 0; k < h->n_k; ++k) {
       const double ng = (double)(h->goff[k + 1] - h->goff[k]);
@@ -1220,6 +1270,11 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
     int kpk[3] = {0, 0, 0};
     if (cudaMemcpy(c, h->d_cnt.p, sizeof(c), cudaMemcpyDeviceToHost) == cudaSuccess &&
         cudaMemcpy(kpk, h->d_off.as<int>() + 2 * h->n_atoms, sizeof(kpk), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      if (h->last_alg3) {  // no factorisation: every H row has sigma = +1
+        kpk[1] = (int)s.k_total;
+        kpk[2] = 0;
+        c[0] = 0;
+      }
       s.n_pivot2 = c[0];
       s.n_pos = kpk[1];
       s.n_neg = kpk[2];
@@ -1227,7 +1282,9 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
       const int S_ = slices_of(h);
       const double pairs = S_ * (S_ + 1) / 2.0;
       const double chH = std::ceil(kpk[1] / 64.0) + std::ceil(kpk[2] / 64.0);
-      const double chS = (h->opt.s_method == FLAPW_S_LEGENDRE) ? 0.0 : std::ceil((double)s.k_total / 64.0);
+      const double chS = (h->opt.s_method == FLAPW_S_LEGENDRE)
+                             ? 0.0
+                             : std::ceil((double)h->n_atoms * 2 * h->n_L / 64.0);
       double tf = 0;
       for (int k = 0; k < h->n_k; ++k) {
         const int ng = (int)(h->goff[k + 1] - h->goff[k]);
@@ -1248,6 +1305,7 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
 int flapw_get_factor(flapw_handle h, int slot, double* CH, int* n_pos, int* n_neg) {
   if (!h || !CH || !n_pos || !n_neg) return fail(h, FLAPW_ERR_ARG, "NULL argument");
   if (slot < 0 || slot >= h->last_n_slots) return fail(h, FLAPW_ERR_ARG, "slot out of range");
+  if (h->last_alg3) return fail(h, FLAPW_ERR_STATE, "the last build_HS used FLAPW_H_ALG3: no factorisation");
   const int n = 2 * h->n_L;
   CK(h, cudaStreamSynchronize(h->last_stream), "cudaStreamSynchronize");
   CK(h, cudaStreamSynchronize(h->aux_stream), "cudaStreamSynchronize");

@@ -21,14 +21,16 @@ constexpr int kUnitChunks = 64;   // K chunks per unit: the longest exact FP32 a
                                   // (4096 terms, digit products <= 2^12)
 constexpr int kOpSlices = 8;      // slices of the H operand formation product
 
-// One lower-triangle contraction problem: H or S of one k-point.
+// One lower-triangle contraction problem X = L^H diag(sigma) R: H or S of
+// one k-point.  L (the output rows G') and R (the output columns G) are rows
+// of the operand / slice arrays; a Hermitian rank-K update has L = R.
 struct Prob {
-  int row_base;   // first row of this problem in the operand / slice arrays
+  int row_base;   // first row of L in the operand / slice arrays
   int n_g;        // N_G of the problem
   int kp;         // operand rows (K index) with sigma = +1; columns [0, kp)
   int kn;         // rows with sigma = -1; columns [ceil(kp/64)*64, ... + kn)
   int layout;     // FLAPW_LAYOUT_*
-  int pad;
+  int col_base;   // first row of R (= row_base for L = R)
   int64_t ld;     // leading dimension of the full layout
   double2* out;   // lower triangle, complex128
 };
@@ -131,6 +133,8 @@ struct OpformArgs {
   int64_t g_total;      // plane waves over all k-points
   int64_t h_row0;       // operand row of the first H plane wave (k-point 0)
   int64_t s_row0;       // operand row of the first S plane wave
+  int64_t r_row0;       // the paper's Alg. 3: operand row of the first right-hand H row
+  const double2* T;     // the paper's Alg. 3: [slot][n][n] row-major T blocks (lower read)
   // from A/B
   const double2* A;
   const double2* B;
@@ -176,6 +180,8 @@ struct OpGemmArgs {
   double2* Z;          // operand rows (row h_row0 + g, column k')
   int64_t k_alloc;
   int64_t h_row0;
+  int alg3_nl;         // 0: factored C^H rows; N_L: the paper's Alg. 3 rows (alg3.cuh)
+  int64_t r_row0;      // Alg. 3: operand row of the first R row
 };
 cudaError_t opgemm_init();
 size_t opgemm_smem_bytes();
@@ -185,12 +191,22 @@ cudaError_t launch_opgemm_build(const double2* CH, const int* perm, int n_slots,
                                 const double2* Yc, const double* al, const double* bl, int n_L,
                                 int lmax, int n_types, int64_t G, double2* A, double2* B,
                                 cudaStream_t st, bool build_a);
-// P for every tile (opgemm.cu), then every atom's operand rows from P.
+// The paper's Alg. 3: A[slot n + r][c] = conj(M_s(r, c)) (alg3.cuh) from the T blocks.
+cudaError_t launch_opgemm_build_alg3(const double2* T, int n_slots, int n, int n_L, int kp,
+                                     double2* A, cudaStream_t st);
+// P for every tile (opgemm.cu), then every atom's operand rows from P (with
+// alg3_nl set: the L and R columns of Alg. 3).
 cudaError_t launch_opgemm(const CUtensorMap& map_a, const CUtensorMap& map_b, const OpGemmArgs& g,
                           const OpTile* tiles, int n_tiles, int* err, int max_ctas, cudaStream_t st);
 cudaError_t launch_opgemm_phase(const OpGemmArgs& g, int n_combo, cudaStream_t st);
 cudaError_t launch_opform_H(const OpformArgs& a, bool factored, cudaStream_t st);
 cudaError_t launch_opform_S(const OpformArgs& a, bool factored, cudaStream_t st);
+// H operands of the paper's Alg. 3 (h_row0: L rows, r_row0: R rows, 3 N_L
+// columns per atom from a * 3 N_L): L_a = [X_a; B_a; A_a], R_a = [B_a; X_a; Y_a]
+// with X_a = T^BA A_a + T^BB B_a / 2 and Y_a = T^AA A_a.  Copies A_a and B_a
+// into place and, if `product`, forms the X and Y rows in FP64 (otherwise the
+// tensor-core product of opgemm.cu writes them).
+cudaError_t launch_opform_alg3(const OpformArgs& a, bool factored, bool product, cudaStream_t st);
 
 // Copies a user Z (column-major K x N) into operand rows, sigma-grouped.
 cudaError_t launch_gather_Z(const double2* Zin, int64_t ldz, int K, int N, const int* kmap,

@@ -1,5 +1,9 @@
 // Emulated complex-FP64 lower-triangle contraction  X = Z^H diag(sigma) Z  on
 // the FP16 tensor cores (tcgen05.mma, TMEM accumulators, TMA operand loads).
+// The output rows read the operand rows from Prob::row_base and the output
+// columns those from Prob::col_base: the same rows for a Hermitian rank-K
+// update, two operands L, R for the paper's Alg. 3 form X = L^H R (its
+// zher2k + zherkx, where the result is Hermitian although L != R).
 //
 // The operand is given as s integer slices per entry (see slicer.cu):
 //     Z = 2^{e_row} sum_i d_i 128^{-(i+1)}   (Re and Im planes separately).
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int tile = pair; tile < n_tiles && ok; tile += n_pairs) {
         const EmuTile T = tiles[tile];
         const Prob P = probs[T.prob];
-        const int rowA = P.row_base + T.ib * 256 + (int)rank * 128, rowB = P.row_base + T.jb * 64;
+        const int rowA = P.row_base + T.ib * 256 + (int)rank * 128, rowB = P.col_base + T.jb * 64;
         Sched sc;
         for (bool more = sc.begin(units_of(P, T.split), n_slices); more && ok; more = sc.next()) {
           const uint32_t b_bytes = sc.two ? kTileB : kTileB / 2;
@@ -451,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int n = 0; n < 64; ++n) {
           const int64_t gc = (int64_t)T.jb * 64 + n;
           if (gc < ng && gc <= gr) {
-            const double val = fx::to_double(acc[n], er + rexp[P.row_base + gc] - frac);
+            const double val = fx::to_double(acc[n], er + rexp[P.col_base + gc] - frac);
             const int64_t o = (P.layout == FLAPW_LAYOUT_LOWER_PACKED)
                                   ? gc * ng - gc * (gc - 1) / 2 + (gr - gc)
                                   : gc * P.ld + gr;

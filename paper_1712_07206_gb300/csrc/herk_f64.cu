@@ -1,7 +1,8 @@
 // Plain FP64 lower-triangle contraction  X = Z^H diag(sigma) Z  (Sec. 3: the
 // zherk / zher2k calls of Alg. 1 and Alg. 3 collapse to this one Hermitian
 // rank-K update once T is factorised).  The baseline path the emulated one is
-// measured against.
+// measured against.  Output columns read the operand rows from Prob::col_base,
+// so the same kernel also computes Alg. 3's L^H R (L != R, Hermitian result).
 //
 // 64 x 64 complex output tiles (lower-triangle tiles only), 8 warps, each warp
 // 32 x 16 outputs on FP64 tensor cores (mma.sync m8n8k4 f64, DMMA).  With
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(256) herk_f64_kernel(const double2* __restrict
         double2 za = make_double2(0.0, 0.0), zb = make_double2(0.0, 0.0);
         if (kc < kend) {
           if (ga < P.n_g) za = Z[(int64_t)(P.row_base + ga) * k_alloc + kc];
-          if (gb < P.n_g) zb = Z[(int64_t)(P.row_base + gb) * k_alloc + kc];
+          if (gb < P.n_g) zb = Z[(int64_t)(P.col_base + gb) * k_alloc + kc];
         }
         ar[r][c] = za.x;
         ai[r][c] = za.y;

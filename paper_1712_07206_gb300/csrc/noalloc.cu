@@ -150,7 +150,7 @@ extern "C" int flapw_herk_noalloc(const void* Z, int64_t ldz, int K, int N, cons
   double2* Zs = reinterpret_cast<double2*>(base + o_z);
   __half* SL = reinterpret_cast<__half*>(base + o_sl);
 
-  const Prob P{0, N, kp, kn, layout, 0, layout == FLAPW_LAYOUT_LOWER_FULL ? ldh : N,
+  const Prob P{0, N, kp, kn, layout, /*col_base*/ 0, layout == FLAPW_LAYOUT_LOWER_FULL ? ldh : N,
                static_cast<double2*>(H)};
   SliceMaps tmap;
   std::string terr;

@@ -19,6 +19,10 @@
 // The factored variant uses A_a = diag(e^{iK.tau_a}) A_t (A depends on the
 // atom only through its structure-factor phase): Z_{slot,t} = C^H [A_t; B_t]
 // is formed once per (slot, type) pair and multiplied by each atom's phase.
+//
+// The paper's Alg. 3 needs no factorisation: its operands (alg3.cuh) are the
+// rows of M [A_a; B_a] placed into L and R, plus copies of A_a and B_a.
+#include "alg3.cuh"
 #include "flapw_internal.h"
 
 namespace flapw {
@@ -183,6 +187,128 @@ __global__ void __launch_bounds__(256) opform_s_kernel(OpformArgs p, int64_t G) 
   }
 }
 
+// X and Y rows of Alg. 3: row r of M [A_a; B_a] goes to column N_L + r of R_a
+// and, for r < N_L (an X row), to column r of L_a.
+// grid: (g-tiles, ceil(n/32), atoms or combos); 256 threads.
+template <bool kFactored>
+__global__ void __launch_bounds__(256) opform_alg3_kernel(OpformArgs p, int64_t G) {
+  __shared__ double2 ms[kCT][kRT];
+  __shared__ double2 ws[kCT][kGT];
+  const int k = p.gtiles[2 * blockIdx.x], g0 = p.gtiles[2 * blockIdx.x + 1];
+  const int64_t ng = p.goff[k + 1] - p.goff[k];
+  const int r0 = blockIdx.y * kRT;
+  int slot, type, a_single;
+  if (kFactored) {
+    slot = p.combo_slot[blockIdx.z];
+    type = p.combo_type[blockIdx.z];
+    a_single = -1;
+  } else {
+    a_single = blockIdx.z;
+    slot = p.atom_slot[a_single];
+    type = p.atom_type[a_single];
+  }
+  const int n = p.n, nL = p.n_L;
+  const double2* T = p.T + (int64_t)slot * n * n;
+  const int tid = threadIdx.x, rl = tid & 31, gq = tid >> 5;
+  double2 acc[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) acc[e] = make_double2(0.0, 0.0);
+  const int c_end = (r0 >= nL) ? nL : n;  // Y rows read the A half only
+  for (int c0 = 0; c0 < c_end; c0 += kCT) {
+    for (int idx = tid; idx < kCT * kRT; idx += 256) {
+      const int rr = idx / kCT, cc = idx % kCT;
+      const int r = r0 + rr, c = c0 + cc;
+      ms[cc][rr] = (r < n && c < n) ? alg3::m_elem(T, n, nL, r, c) : make_double2(0.0, 0.0);
+    }
+    for (int idx = tid; idx < kCT * kGT; idx += 256) {
+      const int cc = idx / kGT, gg = idx % kGT;
+      const int c = c0 + cc, g = g0 + gg;
+      double2 w = make_double2(0.0, 0.0);
+      if (c < n && g < ng) {
+        if (kFactored) w = w_type(p, type, c, p.goff[k] + g, G);
+        else w = w_from_ab(p, a_single, c, k, g, ng);
+      }
+      ws[cc][gg] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int cc = 0; cc < kCT; ++cc) {
+      const double2 m = ms[cc][rl];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] = cfma(m, ws[cc][gq * 8 + e], acc[e]);
+    }
+    __syncthreads();
+  }
+  const int r = r0 + rl;
+  if (r >= n) return;
+  const int64_t lrow0 = p.h_row0 + p.goff[k], rrow0 = p.r_row0 + p.goff[k];
+  const int a_begin = kFactored ? p.combo_start[blockIdx.z] : 0;
+  const int a_end = kFactored ? p.combo_start[blockIdx.z + 1] : 1;
+  for (int ai = a_begin; ai < a_end; ++ai) {
+    const int a = kFactored ? p.combo_atoms[ai] : a_single;
+    const int64_t base = (int64_t)a * 3 * nL;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int g = g0 + gq * 8 + e;
+      if (g < ng) {
+        double2 z = acc[e];
+        if (kFactored) {
+          const double2 f = p.ph[(int64_t)a * G + p.goff[k] + g];
+          z = make_double2(f.x * acc[e].x - f.y * acc[e].y, f.x * acc[e].y + f.y * acc[e].x);
+        }
+        p.Z[(rrow0 + g) * p.k_alloc + base + nL + r] = z;
+        if (r < nL) p.Z[(lrow0 + g) * p.k_alloc + base + r] = z;
+      }
+    }
+  }
+}
+
+// A_a and B_a into the Alg. 3 operands: L_a = [X; B; A] takes W row c at
+// column N_L + c (B rows) or 2 N_L + c (A rows); R_a = [B; X; Y] takes the B
+// rows at column c - N_L.  grid: (g-tiles, ceil(n/32), atoms).
+template <bool kFactored>
+__global__ void __launch_bounds__(256) opform_alg3_copy_kernel(OpformArgs p, int64_t G) {
+  __shared__ double2 tile[kRT][kGT + 1];
+  const int k = p.gtiles[2 * blockIdx.x], g0 = p.gtiles[2 * blockIdx.x + 1];
+  const int64_t ng = p.goff[k + 1] - p.goff[k];
+  const int c0 = blockIdx.y * kRT;
+  const int a = blockIdx.z;
+  const int t = p.atom_type[a];
+  const int n = p.n, nL = p.n_L;
+  for (int idx = threadIdx.x; idx < kRT * kGT; idx += 256) {
+    const int cc = idx / kGT, gg = idx % kGT;
+    const int c = c0 + cc, g = g0 + gg;
+    double2 w = make_double2(0.0, 0.0);
+    if (c < n && g < ng) {
+      if (kFactored) {
+        const int64_t gi = p.goff[k] + g;
+        const double2 u = w_type(p, t, c, gi, G);
+        const double2 f = p.ph[(int64_t)a * G + gi];
+        w = make_double2(f.x * u.x - f.y * u.y, f.x * u.y + f.y * u.x);
+      } else {
+        w = w_from_ab(p, a, c, k, g, ng);
+      }
+    }
+    tile[cc][gg] = w;
+  }
+  __syncthreads();
+  const int64_t lrow0 = p.h_row0 + p.goff[k], rrow0 = p.r_row0 + p.goff[k];
+  const int64_t base = (int64_t)a * 3 * nL;
+  for (int idx = threadIdx.x; idx < kRT * kGT; idx += 256) {
+    const int gg = idx / kRT, cc = idx % kRT;
+    const int c = c0 + cc, g = g0 + gg;
+    if (c < n && g < ng) {
+      const double2 v = tile[cc][gg];
+      if (c < nL) {
+        p.Z[(lrow0 + g) * p.k_alloc + base + 2 * nL + c] = v;
+      } else {
+        p.Z[(lrow0 + g) * p.k_alloc + base + c] = v;
+        p.Z[(rrow0 + g) * p.k_alloc + base + (c - nL)] = v;
+      }
+    }
+  }
+}
+
 // Z[g][k'] = Zin[g*ldz + kmap[k']] (kmap < 0: zero), for the standalone contraction.
 __global__ void gather_z_kernel(const double2* Zin, int64_t ldz, int K, int N, const int* kmap,
                                 int64_t k_alloc, double2* Z) {
@@ -221,6 +347,18 @@ cudaError_t launch_opform_S(const OpformArgs& a, bool factored, cudaStream_t st)
   dim3 grid(a.n_gtiles, (a.n + kRT - 1) / kRT, a.n_atoms);
   if (factored) opform_s_kernel<true><<<grid, 256, 0, st>>>(a, G);
   else opform_s_kernel<false><<<grid, 256, 0, st>>>(a, G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_opform_alg3(const OpformArgs& a, bool factored, bool product, cudaStream_t st) {
+  if (a.n_gtiles == 0) return cudaSuccess;
+  const int64_t G = a.g_total;
+  dim3 grid(a.n_gtiles, (a.n + kRT - 1) / kRT, factored ? a.n_combo : a.n_atoms);
+  if (product && factored) opform_alg3_kernel<true><<<grid, 256, 0, st>>>(a, G);
+  if (product && !factored) opform_alg3_kernel<false><<<grid, 256, 0, st>>>(a, G);
+  dim3 grid_copy(a.n_gtiles, (a.n + kRT - 1) / kRT, a.n_atoms);
+  if (factored) opform_alg3_copy_kernel<true><<<grid_copy, 256, 0, st>>>(a, G);
+  else opform_alg3_copy_kernel<false><<<grid_copy, 256, 0, st>>>(a, G);
   return cudaGetLastError();
 }
 

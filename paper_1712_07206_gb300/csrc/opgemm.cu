@@ -27,6 +27,11 @@
 // of its row and plane wave, [combo][g][r]); opgemm_phase_kernel then writes
 // every atom's operand rows with the atom's phase, on the integer pipes.
 //
+// The same product forms the operands of the paper's Alg. 3 (Sec. 5.1) with
+// A(r, c) = conj(M_s(r, c)), M = [[T^BA, T^BB / 2], [T^AA, 0]] (alg3.cuh): the
+// phase kernel then places row r in column N_L + r of R_a and, for r < N_L,
+// in column r of L_a.
+//
 // CTA tile: 128 rows r x 64 plane waves g; M = 128, N = 128 MMAs (cta_group::1)
 // with B = [Re W_j; Im W_j] for the 64 plane waves; 128-wide K stages (two
 // 64-wide chunks of any slice pair of the current level).  Four 128-column
@@ -38,6 +43,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "alg3.cuh"
 #include "fixed64.cuh"
 #include "tc_common.cuh"
 
@@ -317,6 +323,24 @@ __global__ void __launch_bounds__(128) opgemm_build_a_kernel(const double2* __re
   }
 }
 
+// A(slot n + r, c) = conj(M_s(r, c)) for Alg. 3; columns n..kp-1 zero.
+// grid: n_slots * n rows.
+__global__ void __launch_bounds__(128) opgemm_build_a_alg3_kernel(const double2* __restrict__ T,
+                                                                  int n, int nL, int kp,
+                                                                  double2* __restrict__ A) {
+  const int row = blockIdx.x, slot = row / n, r = row % n;
+  const double2* Ts = T + (int64_t)slot * n * n;
+  double2* dst = A + (int64_t)row * kp;
+  for (int c = threadIdx.x; c < kp; c += blockDim.x) {
+    double2 v = make_double2(0.0, 0.0);
+    if (c < n) {
+      const double2 m = alg3::m_elem(Ts, n, nL, r, c);
+      v = make_double2(m.x, -m.y);
+    }
+    dst[c] = v;
+  }
+}
+
 // B(t G + gi, c) = W_t(c, gi) = [Yc(L, gi) a_l(t, gi); Yc(L, gi) b_l(t, gi)];
 // columns n..kp-1 zero.  A 32 plane-wave x 32 column tile per CTA goes
 // through shared memory so that both the reads (plane waves contiguous) and
@@ -357,20 +381,24 @@ __global__ void __launch_bounds__(256) opgemm_build_b_kernel(const double2* __re
 
 // Z(h_row0 + g, column of (a, r)) = P_{slot(a),type(a)}(r, g) e^{i K.tau_a}
 // for every atom a of a combination: the Q62 phase product of the fixed-point
-// P, then the FP64 value built from its bits (no FP64 arithmetic).  grid:
-// (G, combos), 128 threads over the rows r.
+// P, then the FP64 value built from its bits (no FP64 arithmetic).  The column
+// is the sigma-grouped one of the factorisation, or for Alg. 3 column
+// N_L + r of the R row (r_row0 + g) and, for r < N_L, column r of the L row.
+// grid: (G, combos), 128 threads over the rows r.
 __global__ void __launch_bounds__(128) opgemm_phase_kernel(const OpGemmArgs g) {
   const int64_t gi = blockIdx.x;
   const int combo = blockIdx.y;
   const int slot = g.combo_slot[combo], type = g.combo_type[combo];
   const int eb = g.rexp_b[type * g.G + gi] - kFrac;
-  const int np = g.npos[slot];
+  const int np = g.alg3_nl ? g.n : g.npos[slot];
   const int a0 = g.combo_start[combo], a1 = g.combo_start[combo + 1];
   double2* zrow = g.Z + (g.h_row0 + gi) * g.k_alloc;
+  double2* zrow_r = g.Z + (g.r_row0 + gi) * g.k_alloc;
   const longlong2* prow = g.P + ((int64_t)combo * g.G + gi) * g.n;
+  const int nL = g.alg3_nl;
   for (int r = threadIdx.x; r < g.n; r += blockDim.x) {
-    const int rr = g.outrow[slot * g.n + r];  // sigma-grouped position
-    if (rr < 0) continue;                     // zero pivot: the row carries nothing
+    const int rr = nL ? r : g.outrow[slot * g.n + r];  // sigma-grouped position
+    if (rr < 0) continue;                               // zero pivot: the row carries nothing
     const longlong2 P = prow[r];
     const int ex = g.rexp_a[slot * g.n + r] + eb;
     for (int ai = a0; ai < a1; ++ai) {
@@ -379,8 +407,14 @@ __global__ void __launch_bounds__(128) opgemm_phase_kernel(const OpGemmArgs g) {
       const long long qr = fx::fixed_point(f.x, 62), qi = fx::fixed_point(f.y, 62);
       const long long zr = fx::mul_q62(P.x, qr) - fx::mul_q62(P.y, qi);
       const long long zi = fx::mul_q62(P.x, qi) + fx::mul_q62(P.y, qr);
-      const int col = (rr < np) ? g.pos_off[a] + rr : g.kpk[0] + g.neg_off[a] + (rr - np);
-      zrow[col] = make_double2(fx::to_double(zr, ex), fx::to_double(zi, ex));
+      const double2 z = make_double2(fx::to_double(zr, ex), fx::to_double(zi, ex));
+      if (nL) {
+        const int64_t base = (int64_t)a * 3 * nL;
+        zrow_r[base + nL + r] = z;
+        if (r < nL) zrow[base + r] = z;
+      } else {
+        zrow[(rr < np) ? g.pos_off[a] + rr : g.kpk[0] + g.neg_off[a] + (rr - np)] = z;
+      }
     }
   }
 }
@@ -404,6 +438,12 @@ cudaError_t launch_opgemm_build(const double2* CH, const int* perm, int n_slots,
     dim3 grid((unsigned)((G + 31) / 32), (unsigned)((kp + 31) / 32), (unsigned)n_types);
     opgemm_build_b_kernel<<<grid, 256, 0, st>>>(Yc, al, bl, n_L, lmax, n, kp, G, B);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_opgemm_build_alg3(const double2* T, int n_slots, int n, int n_L, int kp,
+                                     double2* A, cudaStream_t st) {
+  if (n_slots * n > 0) opgemm_build_a_alg3_kernel<<<n_slots * n, 128, 0, st>>>(T, n, n_L, kp, A);
   return cudaGetLastError();
 }
 
