@@ -54,6 +54,15 @@ def max_over_ranks(x: float) -> float:
     return float(t.item())
 
 
+# DRAM bytes (read + write) per herk_emu_kernel launch, mean of the S and the
+# H launch of one step, from an ncu --set full capture of the current kernel
+# (profiles/herk_emu_c2_ortho16_l8_ng3990_full.md); keyed by workload, slices,
+# S method and H method.  Other shapes report null.
+MEASURED_TRAFFIC = {
+    ("c2_ortho_16at_l8_ng4000", 7, "contraction", "factored"): 4.8165e9,
+}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -163,7 +172,7 @@ def run_ours(args):
 
     def timed(n_steps, collect_kernel=False):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
-        kms = []
+        kms, abms = [], []
         for i in range(n_steps):
             flush.zero_()
             ev[i][0].record(stream)
@@ -174,8 +183,9 @@ def run_ours(args):
                 st_ = h.stats()
                 # the tensor-core contraction alone (with Legendre S only the H half)
                 kms.append(st_["ms_contract"] - (st_["ms_s"] if args.s_method == "legendre" else 0.0))
+                abms.append(st_["ms_ab_assemble"])
         torch.cuda.synchronize()
-        return [a.elapsed_time(b) for a, b in ev], kms
+        return [a.elapsed_time(b) for a, b in ev], (kms, abms)
 
     for _ in range(args.warmup):
         step()
@@ -192,7 +202,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms = max_over_ranks(float(np.mean(step_ms)))
     # contraction kernel duration, from the library's own events on the launching stream
-    _, kms = timed(3, collect_kernel=True)
+    _, (kms, abms) = timed(3, collect_kernel=True)
     st = h.stats()
     k_ms = float(np.mean(kms))
     bf16_burst, bf16_sus, hbm, src = peaks()
@@ -251,7 +261,7 @@ def run_ours(args):
             step_host()
         e_ms = (time.perf_counter() - t0) * 1e3 / args.e2e_steps
         h2d = p.T.nbytes + p.U.nbytes + p.radial.nbytes + p.atom_slot.nbytes
-        d2h = 2 * sum(outsz(ng) for ng in ngs) * 16
+        d2h = 2 * sum(copied_elements(ng, layout) for ng in ngs) * 16
         e2e = {"value": round(flops / (e_ms * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
                "ms_per_step": round(e_ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     value = flops / (ms * 1e-3) / 1e12 * ws
@@ -274,13 +284,22 @@ def run_ours(args):
         "speedup_emu_vs_fp64": None if f64_ms is None else round(f64_ms / ms, 2),
         "stages_ms": stage,
         "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak,
-                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": args.traffic,
+                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                     "traffic": args.traffic if args.traffic is not None else
+                     MEASURED_TRAFFIC.get((p.name, args.slices, args.s_method, args.h_method)),
                      "kernel": "herk_emu_kernel (" + ("H launch; S by the addition theorem"
                                                       if args.s_method == "legendre" else "S and H launches")
                                + ("; H as Alg. 3's L^H R" if args.h_method == "alg3" else "") + ")",
                      "kernel_ms": round(k_ms, 4),
                      "achieved_algorithmic": round(achieved_alg, 2),
                      "peak_source": f"{src} bf16 {peak_kind} x 1.0 (fp16 = bf16 nominal rate)"},
+        # the A/B assembly (HBM store-bound): 32 bytes stored per (atom, L, G)
+        "roofline_ab": {"bound": "hbm", "kernel": "ab_assemble_kernel",
+                        "bytes": int(32 * p.n_atoms * p.n_L * sum(ngs)),
+                        "kernel_ms": round(float(np.mean(abms)), 4),
+                        "achieved": round(32 * p.n_atoms * p.n_L * sum(ngs) / (float(np.mean(abms)) * 1e-3) / 1e9, 1),
+                        "peak": hbm, "unit": "GB/s",
+                        "frac": round(32 * p.n_atoms * p.n_L * sum(ngs) / (float(np.mean(abms)) * 1e-3) / 1e9 / hbm, 4)},
         "e2e": e2e,
         "gpu_launches": launches_per_step(args) * args.steps,
         "clocks": clk,
@@ -298,20 +317,35 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
+def copied_elements(ng, layout):
+    """Elements of one output the library copies to host memory: all of the
+    packed layout; of the full layout, column blocks of max(64, ceil(N/32))
+    columns from each block's first diagonal element down."""
+    import paper_1712_07206_gb300 as fl
+    if layout == fl.LAYOUT_LOWER_PACKED:
+        return ng * (ng + 1) // 2
+    w = max(64, (ng + 31) // 32)
+    return sum((ng - j0) * min(w, ng - j0) for j0 in range(0, ng, w))
+
+
 def launches_per_step(args):
     """Kernels one timed step launches: ab_prep and ab_assemble; the S half
     (opform_S, slicer, contraction; or the addition theorem's split and
-    double-float kernels); the H half's slicer and contraction, and its
-    operands: tfactor and layout, then either W and conj(C^H) formed and
-    sliced (4 kernels), their tensor-core product and the per-atom phases
-    (factored operands) or opform_H (from A/B).  Alg. 3 has no tfactor and
-    layout; its operand product is the same tensor-core sequence (factored
-    operands) or an FP64 kernel (from A/B), followed by the copy of A and B."""
+    double-float kernels); the H contraction and the H operands:
+      factored operands: tfactor, layout, W and conj(C^H) formed and sliced
+        (4 kernels), their tensor-core product, and one kernel that applies
+        the atom phases and slices the rows;
+      A/B operands: tfactor, layout, opform_H and the slicer;
+      Alg. 3: no tfactor and layout; factored, the same four factor kernels,
+        the product, the phase kernel, the copy of A and B and the slicer;
+        from A/B, the FP64 product and copy kernels and the slicer."""
     n = 2
     n += 2 if args.s_method == "legendre" else 3
-    n += 2
-    tc = 6 if args.operands == "factored" else 1
-    n += (tc + 1) if args.h_method == "alg3" else (2 + tc)
+    n += 1
+    if args.h_method == "alg3":
+        n += 8 if args.operands == "factored" else 3
+    else:
+        n += 8 if args.operands == "factored" else 4
     return n
 
 

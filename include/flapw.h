@@ -124,6 +124,7 @@ typedef struct flapw_stats {
   int reserved[8];
   double ms_s;         /* the S half of ms_contract: its contraction, or with
                           FLAPW_S_LEGENDRE the addition-theorem evaluation */
+  double ms_ab_assemble; /* the A/B assembly kernel of the last build_AB (part of ms_ab) */
 } flapw_stats;
 
 /* Defaults listed in flapw_options. */
@@ -188,7 +189,9 @@ int flapw_build_AB(flapw_handle h, const double* radial, void* A, void* B, void*
  *       previous flapw_build_AB on this handle for the radial data.
  *   H[n_k], S[n_k]: per k-point output pointers (device or host memory),
  *       complex128, lower triangle in the handle's layout; the full layout
- *       uses ld = N_G(k).  Elements above the diagonal are not written.
+ *       uses ld = N_G(k).  Elements above the diagonal are not written (in
+ *       host memory most of them are left untouched: the lower triangle is
+ *       copied back in blocks of columns).
  * Each T block is factorised as T = C diag(sigma) C^H (Bunch-Kaufman
  * pivoted LDL^H, then 2x2 eigen-splitting; Sec. 3, Alg. 1's Cholesky step
  * generalised to indefinite T), so that H = Z^H diag(sigma) Z with

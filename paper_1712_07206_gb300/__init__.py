@@ -55,7 +55,8 @@ class Stats(ctypes.Structure):
                 ("k_total", ctypes.c_int64), ("n_pos", ctypes.c_int), ("n_neg", ctypes.c_int),
                 ("n_pivot2", ctypes.c_int), ("n_slices", ctypes.c_int), ("n_tiles", ctypes.c_int),
                 ("tile_order", ctypes.c_int), ("graph_replays", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8), ("ms_s", ctypes.c_double)]
+                ("reserved", ctypes.c_int * 8), ("ms_s", ctypes.c_double),
+                ("ms_ab_assemble", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

@@ -150,8 +150,9 @@ struct flapw_ctx {
   cudaEvent_t ev_copy = nullptr;
   // events: 0 start, 1 factor done (aux), 2 S operands done, 3 S sliced, 4 S contracted,
   // 5 end, 6/7 build_AB, 8 H operands start, 9 S operands start, 10 H operands done,
-  // 11 H sliced, 12 H contracted, 13 fork, 14/15 autotune, 16 auxiliary work done (join)
-  cudaEvent_t ev[17]{};
+  // 11 H sliced, 12 H contracted, 13 fork, 14/15 autotune, 16 auxiliary work done (join),
+  // 17 A/B assembly start
+  cudaEvent_t ev[18]{};
   bool ev_recorded = false, ev_ab = false, ev_engine = false;
   cudaStream_t last_stream = nullptr;
   flapw_stats stats{};
@@ -298,6 +299,39 @@ struct OutPlan {
   size_t stage_bytes = 0;
 };
 
+// Width of the column blocks in which a full-layout output goes to host
+// memory: at most about 32 blocks per matrix, at least 64 columns.
+int64_t copy_block_cols(int64_t ng) { return std::max<int64_t>(64, (ng + 31) / 32); }
+
+// Device-to-host copy of one output, its pieces alternating between two
+// streams (two copy engines when st0 != st1).  The packed layout goes in two
+// halves; the full layout (ld = ng) block of columns by block of columns, each
+// from the block's first diagonal element down, so that about half of the
+// N_G^2 elements (the lower triangle and the small triangles above the
+// diagonal inside each block) cross the link.
+cudaError_t copy_out(void* dst, const double2* src, int64_t ng, int layout, cudaStream_t st0,
+                     cudaStream_t st1) {
+  if (ng == 0) return cudaSuccess;
+  char* d = static_cast<char*>(dst);
+  const char* s = reinterpret_cast<const char*>(src);
+  if (layout == FLAPW_LAYOUT_LOWER_PACKED) {
+    const size_t total = (size_t)(ng * (ng + 1) / 2) * 16, half = total / 32 * 16;
+    cudaError_t e = cudaMemcpyAsync(d, s, half, cudaMemcpyDeviceToHost, st0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + half, s + half, total - half, cudaMemcpyDeviceToHost, st1);
+    return e;
+  }
+  const int64_t w = copy_block_cols(ng);
+  int b = 0;
+  for (int64_t j0 = 0; j0 < ng; j0 += w, ++b) {
+    const size_t off = (size_t)(j0 * ng + j0) * 16;
+    const cudaError_t e = cudaMemcpy2DAsync(d + off, (size_t)ng * 16, s + off, (size_t)ng * 16,
+                                            (size_t)(ng - j0) * 16, (size_t)std::min(w, ng - j0),
+                                            cudaMemcpyDeviceToHost, (b & 1) ? st1 : st0);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 size_t out_bytes(int layout, int64_t ng) {
   return (layout == FLAPW_LAYOUT_LOWER_PACKED) ? (size_t)(ng * (ng + 1) / 2) * 16
                                                : (size_t)(ng * ng) * 16;
@@ -320,17 +354,18 @@ int split_scratch(flapw_ctx* h, cudaStream_t st, SplitScratch* out) {
   return FLAPW_OK;
 }
 
-// Slices (emulated precision) and contracts one half beside concurrent work
-// that holds busy_sms SMs.  Records ev_sl after the slicer and ev_k after the
-// contraction.
+// Slices (emulated precision; not if `presliced`, the slices being written
+// already) and contracts one half beside concurrent work that holds busy_sms
+// SMs.  Records ev_sl after the slicer and ev_k after the contraction.
 int enqueue_contraction(flapw_ctx* h, const Half& hf, int busy_sms, cudaStream_t st, int ev_sl,
-                        int ev_k) {
+                        int ev_k, bool presliced = false) {
   const int s = slices_of(h);
   const int64_t rows = h->rows;
   if (h->opt.precision == FLAPW_PREC_EMU) {
-    CK(h, launch_slicer(h->d_Z.as<double2>(), h->k_alloc, h->d_probs.as<Prob>(), h->d_rowprob.as<int>(),
-                        0, rows, hf.row0, hf.nrows, s, h->d_SL.as<__half>(), h->d_rexp.as<int>(), st),
-       "slicer launch");
+    if (!presliced)
+      CK(h, launch_slicer(h->d_Z.as<double2>(), h->k_alloc, h->d_probs.as<Prob>(), h->d_rowprob.as<int>(),
+                          0, rows, hf.row0, hf.nrows, s, h->d_SL.as<__half>(), h->d_rexp.as<int>(), st),
+         "slicer launch");
     CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
     SplitScratch sp{};
     if (int rc = split_scratch(h, st, &sp)) return rc;
@@ -676,6 +711,7 @@ int flapw_build_AB(flapw_handle h, const double* radial, void* A, void* B, void*
            h->d_rec.as<double>(), h->d_pos.as<double>(), h->d_type.as<int>(),
            h->d_radius.as<double>(), h->d_kfrac.as<double>(), h->d_ktau.as<double>(),
            4.0 * M_PI / std::sqrt(h->volume)};
+  CK(h, cudaEventRecord(h->ev[17], st), "cudaEventRecord");
   CK(h, launch_ab_assemble_tiles(geo, h->d_gt128.as<int>(), (int)(h->gt128.size() / 2),
                                  h->d_goff.as<int64_t>(), h->d_Yc.as<double2>(), h->d_al.as<double>(),
                                  h->d_bl.as<double>(), h->d_ph.as<double2>(), dA, dB, st),
@@ -861,7 +897,9 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   CK(h, h->d_U.ensure(u_bytes), "workspace");
   CK(h, h->d_off.ensure(sizeof(int) * (2 * (size_t)h->n_atoms + 8)), "workspace");
   CK(h, h->d_probs.ensure(sizeof(Prob) * probs.size()), "workspace");
-  CK(h, h->d_Z.ensure((size_t)h->rows * h->k_alloc * 16), "operand workspace");
+  // FP64 operand rows: none on the emulated path with factored operands and
+  // factored H, where each half is formed and sliced in one pass
+  if (!(tc_ops && !alg3)) CK(h, h->d_Z.ensure((size_t)h->rows * h->k_alloc * 16), "operand workspace");
   CK(h, h->d_rexp.ensure((size_t)h->rows * 4), "workspace");
   if (h->tiles_rows_key != h->rows) {
     std::vector<int> rp(h->rows);
@@ -970,8 +1008,10 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     int* oprexp_a = h->d_oprexp.as<int>();
     int* oprexp_b = oprexp_a + op_rows_a;
     if (!alg3) {
+      // beside the S contraction one CTA per slot; with S by the addition
+      // theorem the factorisation leads the critical path: a cluster per slot
       CK(h, launch_tfactor(h->d_T.as<double2>(), n, n_slots, h->d_work.as<double2>(), h->d_CH.as<double2>(),
-                           perm, outrow, npos, nneg, cnt, cnt + 2, h->aux_stream),
+                           perm, outrow, npos, nneg, cnt, cnt + 2, s_legendre, h->aux_stream),
          "T factorisation launch");
       CK(h, launch_layout(npos, nneg, h->d_slot.as<int>(), h->n_atoms, nk, pos_off, neg_off, kpk,
                           h->d_probs.as<Prob>(), (int)K, h->aux_stream),
@@ -1030,6 +1070,28 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       CK(h, launch_slegendre(la, h->d_f64_tiles.as<F64Tile>() + hS.f64_t0, hS.f64_nt, st),
          "S (addition theorem) launch");
       CK(h, cudaEventRecord(h->ev[4], st), "cudaEventRecord");
+    } else if (tc_ops) {
+      // S rows formed from W and sliced in one pass: no FP64 S operand
+      CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
+      SopArgs sa{};
+      sa.n = n;
+      sa.n_L = h->n_L;
+      sa.lmax = h->lmax;
+      sa.n_atoms = h->n_atoms;
+      sa.G = h->g_total;
+      sa.W = h->d_opB.as<double2>();
+      sa.kpw = op_kp;
+      sa.U = h->d_U.as<double>();
+      sa.ph = h->d_ph.as<double2>();
+      sa.combo_type = oa.combo_type;
+      sa.combo_atoms = oa.combo_atoms;
+      sa.combo_start = oa.combo_start;
+      sa.n_combo = n_combo;
+      sa.s_row0 = s_row0;
+      sa.k_alloc = h->k_alloc;
+      CK(h, launch_sop_slice(sa, slices_of(h), h->d_SL.as<__half>(), h->rows, h->d_rexp.as<int>(), st),
+         "S operand slice launch");
+      if (int rc = enqueue_contraction(h, hS, n_slots, st, 3, 4, true)) return rc;
     } else {
       CK(h, launch_opform_S(oa, factored, st), "S operand launch");
       CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
@@ -1042,9 +1104,9 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev[4], 0), "cudaStreamWaitEvent");
       for (int i = nk; i < 2 * nk; ++i)
         if (op.host[i])
-          CK(h, cudaMemcpyAsync(op.host[i], op.dev[i], op.bytes[i], cudaMemcpyDeviceToHost, h->copy_stream),
-             "cudaMemcpyAsync");
-      CK(h, cudaEventRecord(h->ev_copy, h->copy_stream), "cudaEventRecord");
+          CK(h, copy_out(op.host[i], op.dev[i], h->goff[i - nk + 1] - h->goff[i - nk], layout,
+                         h->copy_stream, h->copy_stream),
+             "cudaMemcpy2DAsync");
     }
     // join, then H
     CK(h, cudaStreamWaitEvent(st, h->ev[16], 0), "cudaStreamWaitEvent");
@@ -1060,6 +1122,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       ga.combo_start = oa.combo_start;
       ga.outrow = outrow;
       ga.npos = npos;
+      ga.nneg = nneg;
       ga.pos_off = pos_off;
       ga.neg_off = neg_off;
       ga.kpk = kpk;
@@ -1075,18 +1138,36 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       CK(h, launch_opgemm(h->opmap_a, h->opmap_b, ga, h->d_optiles.as<OpTile>(), (int)h->optiles.size(),
                           cnt + 2, h->num_sms, st),
          "H operand launch");
-      CK(h, launch_opgemm_phase(ga, n_combo, st), "H operand phase launch");
-      if (alg3) CK(h, launch_opform_alg3(oa, factored, false, st), "H operand (Alg. 3) copy launch");
+      if (alg3) {
+        CK(h, launch_opgemm_phase(ga, n_combo, st), "H operand phase launch");
+        CK(h, launch_opform_alg3(oa, factored, false, st), "H operand (Alg. 3) copy launch");
+      } else {
+        // the atom phases applied and the rows sliced in one pass: no FP64 H operand
+        CK(h, cudaEventRecord(h->ev[10], st), "cudaEventRecord");
+        CK(h, launch_opgemm_slice(ga, n_combo, slices_of(h), h->d_SL.as<__half>(), h->rows,
+                                  h->d_rexp.as<int>(), st),
+           "H operand slice launch");
+      }
     } else if (alg3) {
       CK(h, launch_opform_alg3(oa, factored, true, st), "H operand (Alg. 3) launch");
     } else {
       CK(h, launch_opform_H(oa, factored, st), "H operand launch");
     }
-    CK(h, cudaEventRecord(h->ev[10], st), "cudaEventRecord");
-    if (int rc = enqueue_contraction(h, hH, 0, st, 11, 12)) return rc;
+    const bool h_presliced = tc_ops && !alg3;
+    if (!h_presliced) CK(h, cudaEventRecord(h->ev[10], st), "cudaEventRecord");
+    if (int rc = enqueue_contraction(h, hH, 0, st, 11, 12, h_presliced)) return rc;
+    // H outputs in host memory: split over the caller's stream and the copy stream
+    bool h_host = false;
+    for (int i = 0; i < nk; ++i) h_host = h_host || op.host[i] != nullptr;
+    if (h_host) CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev[12], 0), "cudaStreamWaitEvent");
     for (int i = 0; i < nk; ++i)
-      if (op.host[i]) CK(h, cudaMemcpyAsync(op.host[i], op.dev[i], op.bytes[i], cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
-    if (s_host) CK(h, cudaStreamWaitEvent(st, h->ev_copy, 0), "cudaStreamWaitEvent");
+      if (op.host[i])
+        CK(h, copy_out(op.host[i], op.dev[i], h->goff[i + 1] - h->goff[i], layout, st, h->copy_stream),
+           "cudaMemcpy2DAsync");
+    if (s_host || h_host) {
+      CK(h, cudaEventRecord(h->ev_copy, h->copy_stream), "cudaEventRecord");
+      CK(h, cudaStreamWaitEvent(st, h->ev_copy, 0), "cudaStreamWaitEvent");
+    }
     CK(h, cudaEventRecord(h->ev[5], st), "cudaEventRecord");
     return FLAPW_OK;
   };
@@ -1236,7 +1317,10 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
     return ms;
   };
   flapw_stats s = h->stats;
-  if (h->ev_ab) s.ms_ab = el(6, 7);
+  if (h->ev_ab) {
+    s.ms_ab = el(6, 7);
+    s.ms_ab_assemble = el(17, 7);
+  }
   if (h->ev_recorded && h->ev_engine) {
     s.ms_factor = 0.0;
     s.ms_operands = el(0, 2);

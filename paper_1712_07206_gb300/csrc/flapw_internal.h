@@ -102,9 +102,10 @@ cudaError_t launch_ab_assemble_tiles(const Geom& geo, const int* gtiles, int n_g
 
 // Bunch-Kaufman LDL^H of each T block: M = |Lambda|^{1/2} Q^H L^H (pivoted
 // order), the pivot permutation and each row's place in the sigma-grouped operand.
+// cluster: a cluster of CTAs per slot (shorter, more SMs) instead of one CTA.
 cudaError_t launch_tfactor(const double2* T, int n, int n_slots, double2* work, double2* CH,
                            int* perm, int* outrow, int* npos, int* nneg, int* npiv2, int* err,
-                           cudaStream_t st);
+                           bool cluster, cudaStream_t st);
 
 // Atom offsets in the sigma-grouped K order and chunk counts of the H problems.
 cudaError_t launch_layout(const int* npos, const int* nneg, const int* atom_slot, int n_atoms,
@@ -170,6 +171,7 @@ struct OpGemmArgs {
   const int* combo_start;
   const int* outrow;   // [slot][n]
   const int* npos;     // [slot]
+  const int* nneg;     // [slot]
   const int* pos_off;  // [atom]
   const int* neg_off;  // [atom]
   const int* kpk;      // [0] = Kp_pad
@@ -199,6 +201,29 @@ cudaError_t launch_opgemm_build_alg3(const double2* T, int n_slots, int n, int n
 cudaError_t launch_opgemm(const CUtensorMap& map_a, const CUtensorMap& map_b, const OpGemmArgs& g,
                           const OpTile* tiles, int n_tiles, int* err, int max_ctas, cudaStream_t st);
 cudaError_t launch_opgemm_phase(const OpGemmArgs& g, int n_combo, cudaStream_t st);
+// The same rows sliced directly (the factored, sigma-grouped layout only):
+// writes the contraction's slices SL (rows x k_alloc per plane) and the row
+// exponents of the H rows, with no FP64 copy of the operand.
+cudaError_t launch_opgemm_slice(const OpGemmArgs& g, int n_combo, int n_slices, __half* SL,
+                                int64_t rows, int* rexp, cudaStream_t st);
+// The S operand rows (factored operands, emulated precision) formed from the
+// type-level W of the operand product and sliced in one pass (opgemm.cu).
+struct SopArgs {
+  int n, n_L, lmax, n_atoms;
+  int64_t G;
+  const double2* W;        // [type G + g][kpw]: W_t(c, g)
+  int64_t kpw;
+  const double* U;         // [type][lmax + 1]
+  const double2* ph;       // [atom][G]
+  const int* combo_type;   // atoms grouped by (slot, type) combination
+  const int* combo_atoms;
+  const int* combo_start;
+  int n_combo;
+  int64_t s_row0;          // operand row of the first S plane wave
+  int64_t k_alloc;
+};
+cudaError_t launch_sop_slice(const SopArgs& a, int n_slices, __half* SL, int64_t rows, int* rexp,
+                             cudaStream_t st);
 cudaError_t launch_opform_H(const OpformArgs& a, bool factored, cudaStream_t st);
 cudaError_t launch_opform_S(const OpformArgs& a, bool factored, cudaStream_t st);
 // H operands of the paper's Alg. 3 (h_row0: L rows, r_row0: R rows, 3 N_L

@@ -72,7 +72,9 @@ constexpr uint32_t kOffB = kStageChunks * kTileA;        // B after both A chunk
 constexpr uint32_t kStageBytes = kStageChunks * (kTileA + kTileB);
 constexpr uint32_t kTmemCols = 512;
 constexpr int kMaxS = 8;
-constexpr int kPassChunks = 32;                          // longest K sub-span of a pass
+// longest K sub-span of a pass: 48 chunks (3072 terms <= 2^12, exact) let a
+// 2592-term reduction take one sub-span per group; 32 cost config 2 1.2 %
+constexpr int kPassChunks = 48;
 constexpr int kMaxDevices = 64;
 
 // instruction descriptors: D = F32, A = B = F16, K-major both, M = 256, N = 256 / 128

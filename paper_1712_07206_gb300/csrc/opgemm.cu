@@ -419,6 +419,239 @@ __global__ void __launch_bounds__(128) opgemm_phase_kernel(const OpGemmArgs g) {
   }
 }
 
+// round(z 2^sh) for an integer z (half away from zero), 0 below 2^-63,
+// clamped to |X| <= lim.
+__device__ __forceinline__ long long shift_round(long long z, int sh, long long lim) {
+  long long x;
+  if (sh >= 0) {
+    x = (sh >= 62) ? 0 : z << sh;  // only zero entries of a row reach sh >= 62
+  } else {
+    const int r = -sh;
+    if (r > 62) return 0;
+    const unsigned long long m = (z < 0) ? 0ull - (unsigned long long)z : (unsigned long long)z;
+    x = (long long)((m + (1ull << (r - 1))) >> r);
+    if (z < 0) x = -x;
+  }
+  return x > lim ? lim : (x < -lim ? -lim : x);
+}
+
+// The NS balanced base-128 digits of X (|X| <= 2^{7 NS}, NS >= 4; the digits
+// of slicer.cu), written as fp16 values to dst[i * stride], on 32-bit integers:
+// X = hi 2^28 + lo with 0 <= lo < 2^28; the low min(4, NS - 1) digits come
+// from lo, their carry goes into hi, the rest from hi.
+template <int NS>
+__device__ __forceinline__ void put_digits(long long X, __half* dst, int64_t stride) {
+  constexpr int kLo = (NS - 1 < 4) ? NS - 1 : 4;
+  int x = (int)(X & 0xFFFFFFFll);
+  int y = (int)(X >> 28);
+#pragma unroll
+  for (int j = 0; j < kLo; ++j) {
+    const int a = ((x + 64) & 127) - 64;
+    dst[(NS - 1 - j) * stride] = __float2half_rn(fx::small_int_to_float(a));
+    x = (x - a) >> kSliceBits;
+  }
+  y = y * (1 << (28 - kSliceBits * kLo)) + x;
+#pragma unroll
+  for (int i = NS - 1 - kLo; i >= 1; --i) {
+    const int a = ((y + 64) & 127) - 64;
+    dst[i * stride] = __float2half_rn(fx::small_int_to_float(a));
+    y = (y - a) >> kSliceBits;
+  }
+  dst[0] = __float2half_rn(fx::small_int_to_float(y));
+}
+
+// Smallest k with |(x, y)| < 2^k (0 for x = y = 0), |x|, |y| < 2^62: the bit
+// length of x^2 + y^2 in 128-bit integer arithmetic, halved upwards.
+__device__ __forceinline__ int mag_bits(long long x, long long y) {
+  const unsigned long long ax = (x < 0) ? 0ull - (unsigned long long)x : (unsigned long long)x;
+  const unsigned long long ay = (y < 0) ? 0ull - (unsigned long long)y : (unsigned long long)y;
+  const unsigned long long lx = ax * ax, hx = __umul64hi(ax, ax);
+  const unsigned long long ly = ay * ay, hy = __umul64hi(ay, ay);
+  const unsigned long long lo = lx + ly;
+  const unsigned long long hi = hx + hy + (lo < lx ? 1ull : 0ull);
+  const int bl = hi ? 128 - __clzll((long long)hi) : (lo ? 64 - __clzll((long long)lo) : 0);
+  return (bl + 1) >> 1;
+}
+
+// The H operand rows of the factored emulated path straight into the
+// contraction's slices: for plane wave g, every atom's entries
+// Z(g, column of (a, r)) = P_{slot(a),type(a)}(r, g) e^{i K.tau_a} are formed on
+// the integer pipes (Q62 phase products of the fixed-point P, as in
+// opgemm_phase_kernel) and, without an FP64 copy of Z, rounded to the row's
+// fixed point X = round(Z 2^{7 NS - e_g}) and written as NS balanced base-128
+// fp16 digits per plane, the layout and digits of slicer.cu
+// (SL[slice][plane][row][k]).  The row exponent e_g bounds every entry:
+// |Re Z|, |Im Z| <= |Z| = |P| (|e^{i K.tau}| = 1), so e_g is the largest
+// exact bit length of |P| over the row's (combination, r), at most one bit
+// above the slicer's max(|Re|, |Im|); X is clamped to 2^{7 NS} against the
+// phase's rounding.  Padding columns of the sigma-grouped K layout get zero
+// digits.  grid: G (one CTA per plane wave), 256 threads: warp w takes atoms
+// w, w + 8, ... of a combination, its lanes consecutive sigma-grouped rows
+// (consecutive columns).
+template <int NS>
+__global__ void __launch_bounds__(256) opgemm_slice_kernel(const OpGemmArgs g, int n_combo,
+                                                           __half* __restrict__ SL, int64_t rows,
+                                                           int* __restrict__ rexp) {
+  __shared__ long long px[kMaxNL * 2], py[kMaxNL * 2];
+  __shared__ int pe[kMaxNL * 2];
+  __shared__ int red[8];
+  const int64_t gi = blockIdx.x;
+  const int64_t row = g.h_row0 + gi;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = g.n;
+  const int64_t plane_stride = rows * g.k_alloc;
+  __half* srow = SL + row * g.k_alloc;
+  // the row exponent from |P|
+  int e_row = -100000;
+  for (int combo = 0; combo < n_combo; ++combo) {
+    const int slot = g.combo_slot[combo], type = g.combo_type[combo];
+    const int eb = g.rexp_b[type * g.G + gi] - kFrac;
+    for (int r = tid; r < n; r += blockDim.x) {
+      if (g.outrow[slot * n + r] < 0) continue;
+      const longlong2 P = g.P[((int64_t)combo * g.G + gi) * n + r];
+      if (P.x != 0 || P.y != 0) e_row = max(e_row, mag_bits(P.x, P.y) + g.rexp_a[slot * n + r] + eb);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e_row = max(e_row, __shfl_xor_sync(0xffffffffu, e_row, o));
+  if (lane == 0) red[warp] = e_row;
+  __syncthreads();
+  e_row = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) e_row = max(e_row, red[w]);
+  if (e_row == -100000) e_row = 0;  // an all-zero row
+  if (tid == 0) rexp[row] = e_row;
+  const long long lim = 1ll << (kSliceBits * NS);
+  for (int combo = 0; combo < n_combo; ++combo) {
+    const int slot = g.combo_slot[combo], type = g.combo_type[combo];
+    const int eb = g.rexp_b[type * g.G + gi] - kFrac;
+    const int np = g.npos[slot];
+    __syncthreads();  // the previous combination's rows are consumed
+    for (int r = tid; r < n; r += blockDim.x) {
+      const int rr = g.outrow[slot * n + r];
+      if (rr >= 0) {
+        const longlong2 P = g.P[((int64_t)combo * g.G + gi) * n + r];
+        px[rr] = P.x;
+        py[rr] = P.y;
+        pe[rr] = g.rexp_a[slot * n + r] + eb;
+      }
+    }
+    // rows with a zero pivot carry nothing: the live rows are np + nneg
+    const int cnt = np + g.nneg[slot];
+    __syncthreads();
+    for (int ai = g.combo_start[combo] + warp; ai < g.combo_start[combo + 1]; ai += 8) {
+      const int a = g.combo_atoms[ai];
+      const double2 f = g.ph[(int64_t)a * g.G + gi];
+      const long long qr = fx::fixed_point(f.x, 62), qi = fx::fixed_point(f.y, 62);
+      for (int rr = lane; rr < cnt; rr += 32) {
+        const long long Px = px[rr], Py = py[rr];
+        const long long zr = fx::mul_q62(Px, qr) - fx::mul_q62(Py, qi);
+        const long long zi = fx::mul_q62(Px, qi) + fx::mul_q62(Py, qr);
+        const int sh = pe[rr] + kSliceBits * NS - e_row;
+        const int64_t col = (rr < np) ? g.pos_off[a] + rr : g.kpk[0] + g.neg_off[a] + (rr - np);
+        put_digits<NS>(shift_round(zr, sh, lim), srow + col, 2 * plane_stride);
+        put_digits<NS>(shift_round(zi, sh, lim), srow + plane_stride + col, 2 * plane_stride);
+      }
+    }
+  }
+  // zero digits in the padding columns [Kp, Kp_pad) and [Kp_pad + Kn, k_alloc)
+  const int kp_pad = g.kpk[0], kp = g.kpk[1], kn = g.kpk[2];
+  const __half zero = __float2half_rn(0.0f);
+  for (int64_t c = tid; c < g.k_alloc; c += blockDim.x) {
+    if ((c >= kp && c < kp_pad) || c >= kp_pad + kn) {
+#pragma unroll
+      for (int pl = 0; pl < 2 * NS; ++pl) srow[pl * plane_stride + c] = zero;
+    }
+  }
+}
+
+// The S operand rows of the factored emulated path straight into the
+// contraction's slices (Eq. (s)): Z_S(g, a n + c) = e^{i K.tau_a} W_t(c, g) u_t(c),
+// W_t = [A_t; B_t] the type's matching coefficients without the atom phase
+// (the operand product's B factor, rows t G + g), u = 1 on the A rows and
+// U_{t,l} on the B rows.  Each W_t(c, g) u_t(c) becomes a fixed-point integer
+// below 2^60 with an exponent of its own, each atom phase a Q62 integer; the
+// products run on the integer pipes and are sliced as in opgemm_slice_kernel
+// (the row exponent from |W u|, then the digits).  Columns [N_A n, k_alloc)
+// get zero digits.  grid: G; 256 threads: warp w takes atoms w, w + 8, ... of
+// a combination, its lanes consecutive c (consecutive columns).
+template <int NS>
+__global__ void __launch_bounds__(256) sop_slice_kernel(const SopArgs a, __half* __restrict__ SL,
+                                                        int64_t rows, int* __restrict__ rexp) {
+  __shared__ long long wx[kMaxNL * 2], wy[kMaxNL * 2];
+  __shared__ int we[kMaxNL * 2];
+  __shared__ int red[8];
+  const int64_t gi = blockIdx.x;
+  const int64_t row = a.s_row0 + gi;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = a.n;
+  const int64_t plane_stride = rows * a.k_alloc;
+  __half* srow = SL + row * a.k_alloc;
+  // W_t(c, g) u_t(c) of type t as a fixed-point integer below 2^60 and its exponent
+  auto load_w = [&](int t, int c, long long& X, long long& Y, int& E) {
+    double2 w = a.W[((int64_t)t * a.G + gi) * a.kpw + c];
+    if (c >= a.n_L) {
+      const int L = c - a.n_L;
+      int l = 0;
+      while ((l + 1) * (l + 1) <= L) ++l;
+      const double u = a.U[t * (a.lmax + 1) + l];
+      w = make_double2(w.x * u, w.y * u);
+    }
+    const uint64_t m = max(fx::absbits(w.x), fx::absbits(w.y));
+    const int e = (m == 0) ? 0 : (int)((m >> 52) & 0x7FF) - 1022;  // |w| < 2^e
+    X = fx::fixed_point(w.x, 60 - e);
+    Y = fx::fixed_point(w.y, 60 - e);
+    E = e - 60;
+  };
+  // the row exponent from |W u| of the types present
+  int e_row = -100000;
+  for (int combo = 0; combo < a.n_combo; ++combo) {
+    const int t = a.combo_type[combo];
+    for (int c = tid; c < n; c += blockDim.x) {
+      long long X, Y;
+      int E;
+      load_w(t, c, X, Y, E);
+      if (X != 0 || Y != 0) e_row = max(e_row, mag_bits(X, Y) + E);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e_row = max(e_row, __shfl_xor_sync(0xffffffffu, e_row, o));
+  if (lane == 0) red[warp] = e_row;
+  __syncthreads();
+  e_row = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) e_row = max(e_row, red[w]);
+  if (e_row == -100000) e_row = 0;
+  if (tid == 0) rexp[row] = e_row;
+  const long long lim = 1ll << (kSliceBits * NS);
+  for (int combo = 0; combo < a.n_combo; ++combo) {
+    const int t = a.combo_type[combo];
+    __syncthreads();
+    for (int c = tid; c < n; c += blockDim.x) load_w(t, c, wx[c], wy[c], we[c]);
+    __syncthreads();
+    for (int ai = a.combo_start[combo] + warp; ai < a.combo_start[combo + 1]; ai += 8) {
+      const int at = a.combo_atoms[ai];
+      const double2 f = a.ph[(int64_t)at * a.G + gi];
+      const long long qr = fx::fixed_point(f.x, 62), qi = fx::fixed_point(f.y, 62);
+      for (int c = lane; c < n; c += 32) {
+        const long long Wx = wx[c], Wy = wy[c];
+        const long long zr = fx::mul_q62(Wx, qr) - fx::mul_q62(Wy, qi);
+        const long long zi = fx::mul_q62(Wx, qi) + fx::mul_q62(Wy, qr);
+        const int sh = we[c] + kSliceBits * NS - e_row;
+        const int64_t col = (int64_t)at * n + c;
+        put_digits<NS>(shift_round(zr, sh, lim), srow + col, 2 * plane_stride);
+        put_digits<NS>(shift_round(zi, sh, lim), srow + plane_stride + col, 2 * plane_stride);
+      }
+    }
+  }
+  const int64_t k_used = (int64_t)a.n_atoms * n;
+  const __half zero = __float2half_rn(0.0f);
+  for (int64_t c = k_used + tid; c < a.k_alloc; c += blockDim.x) {
+#pragma unroll
+    for (int pl = 0; pl < 2 * NS; ++pl) srow[pl * plane_stride + c] = zero;
+  }
+}
+
 }  // namespace
 
 size_t opgemm_smem_bytes() { return kStages * kStageBytes + 1024 + 256; }
@@ -453,6 +686,48 @@ cudaError_t launch_opgemm(const CUtensorMap& map_a, const CUtensorMap& map_b, co
   if (g.kchunks < 1 || g.kchunks > kMaxKChunks) return cudaErrorInvalidValue;
   const int grid = std::max(1, std::min(n_tiles, max_ctas));
   opgemm_kernel<<<grid, kThreads, opgemm_smem_bytes(), st>>>(map_a, map_b, g, tiles, n_tiles, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_opgemm_slice(const OpGemmArgs& g, int n_combo, int n_slices, __half* SL,
+                                int64_t rows, int* rexp, cudaStream_t st) {
+  if (g.G == 0 || n_combo == 0) return cudaSuccess;
+  if (g.n > 2 * kMaxNL) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)g.G;
+  switch (n_slices) {
+#define FLAPW_OPSLICE_CASE(NS)                                                            \
+  case NS:                                                                                \
+    opgemm_slice_kernel<NS><<<grid, 256, 0, st>>>(g, n_combo, SL, rows, rexp);           \
+    break;
+    FLAPW_OPSLICE_CASE(4)
+    FLAPW_OPSLICE_CASE(5)
+    FLAPW_OPSLICE_CASE(6)
+    FLAPW_OPSLICE_CASE(7)
+    FLAPW_OPSLICE_CASE(8)
+#undef FLAPW_OPSLICE_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sop_slice(const SopArgs& a, int n_slices, __half* SL, int64_t rows, int* rexp,
+                             cudaStream_t st) {
+  if (a.G == 0 || a.n_combo == 0) return cudaSuccess;
+  if (a.n > 2 * kMaxNL) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)a.G;
+  switch (n_slices) {
+#define FLAPW_SOPSLICE_CASE(NS)                                                   \
+  case NS:                                                                        \
+    sop_slice_kernel<NS><<<grid, 256, 0, st>>>(a, SL, rows, rexp);               \
+    break;
+    FLAPW_SOPSLICE_CASE(4)
+    FLAPW_SOPSLICE_CASE(5)
+    FLAPW_SOPSLICE_CASE(6)
+    FLAPW_SOPSLICE_CASE(7)
+    FLAPW_SOPSLICE_CASE(8)
+#undef FLAPW_SOPSLICE_CASE
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

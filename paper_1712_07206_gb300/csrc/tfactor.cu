@@ -15,9 +15,16 @@
 // sigma-grouped operand (sigma = +1 rows first, then -1; zero pivots drop)
 // is returned in `outrow`.
 //
-// One CTA per T slot, the matrix in global memory (L2 resident), lower
-// triangle only.  The work is tiny next to the contraction; it is latency-
-// bound (n sequential pivot steps).
+// One CTA per T slot, or a cluster of kTfCluster CTAs per slot: the matrix
+// in global memory (L2 resident), lower triangle only.  The work is small
+// next to the contraction: n sequential pivot steps, each bound by one SM's
+// FP64 rate in the rank-1/2 update.  Beside the S contraction one CTA per
+// slot costs the fewest SMs; where the factorisation is on the critical path
+// (S by the addition theorem) a cluster per slot shares the pivot searches,
+// the interchange and the update, its CTAs exchanging argmax candidates
+// through distributed shared memory and meeting at cluster barriers.  Every
+// CTA takes each pivot decision from the same data, so all of them pass the
+// same sequence of barriers.
 #include <cmath>
 
 #include "flapw_internal.h"
@@ -26,7 +33,42 @@ namespace flapw {
 namespace {
 
 constexpr int kMaxN = 2 * kMaxNL;
-constexpr int kTfThreads = 512;
+constexpr int kTfThreads = 512;         // one CTA per slot
+constexpr int kTfCluster = 8;           // CTAs per slot in the cluster variant
+constexpr int kTfClusterThreads = 256;
+
+__device__ __forceinline__ uint32_t tf_cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Barrier of all threads of the cluster (CL > 1) or of the CTA, with
+// release/acquire ordering of global and shared memory.
+template <int CL>
+__device__ __forceinline__ void tf_sync() {
+  if (CL > 1)
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+  else
+    __syncthreads();
+}
+// Shared-memory word of CTA `rank` of the cluster at the address of p.
+__device__ __forceinline__ double tf_ld_remote(const double* p, uint32_t rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
+  return v;
+}
+__device__ __forceinline__ int tf_ld_remote(const int* p, uint32_t rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
+  return v;
+}
 
 __device__ __forceinline__ double cabs1(double2 z) { return fabs(z.x) + fabs(z.y); }
 __device__ __forceinline__ double2 cconj(double2 z) { return make_double2(z.x, -z.y); }
@@ -66,16 +108,48 @@ __device__ void block_argmax(double v, int idx, double* s_val, int* s_idx, doubl
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, int n,
-                                                             double2* work, double2* CH,
-                                                             int* perm_out, int* outrow_out,
-                                                             int* npos, int* nneg, int* npiv2,
-                                                             int* err) {
-  const int slot = blockIdx.x;
+// Cluster-wide argmax: each CTA's candidate (cand_v, cand_i, written by its
+// thread 0 after block_argmax) is read by every CTA's thread 0 after a cluster
+// barrier; ties take the smallest index.  CL = 1: the CTA's own result.
+template <int CL>
+__device__ void cluster_argmax(const double* cand_v, const int* cand_i, double* out_v, int* out_i) {
+  if (CL > 1) {
+    tf_sync<CL>();
+    if (threadIdx.x == 0) {
+      double bv = -1.0;
+      int bi = 1 << 30;
+      for (uint32_t r = 0; r < (uint32_t)CL; ++r) {
+        const double v = tf_ld_remote(cand_v, r);
+        const int i = tf_ld_remote(cand_i, r);
+        if (v > bv || (v == bv && i < bi)) {
+          bv = v;
+          bi = i;
+        }
+      }
+      *out_v = bv;
+      *out_i = bi;
+    }
+    __syncthreads();
+  } else {
+    if (threadIdx.x == 0) {
+      *out_v = *cand_v;
+      *out_i = *cand_i;
+    }
+    __syncthreads();
+  }
+}
+
+template <int CL>
+__global__ void __launch_bounds__(CL > 1 ? kTfClusterThreads : kTfThreads)
+    tfactor_kernel(const double2* T, int n, double2* work, double2* CH, int* perm_out,
+                   int* outrow_out, int* npos, int* nneg, int* npiv2, int* err) {
+  const int slot = blockIdx.x / CL;
+  const int q = (CL > 1) ? (int)tf_cluster_rank() : 0;  // rank in the slot's cluster
   const double2* Ts = T + (int64_t)slot * n * n;
   double2* A = work + (int64_t)slot * n * n;
   double2* C = CH + (int64_t)slot * n * n;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int gtid = q * nt + tid, gnt = CL * nt;  // thread index and count over the cluster
 
   __shared__ int perm[kMaxN], blk[kMaxN], outrow[kMaxN];
   __shared__ double lam[kMaxN];
@@ -83,18 +157,20 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
   __shared__ double2 col0[kMaxN], col1[kMaxN], lc0[kMaxN], lc1[kMaxN];  // pivot columns, L columns
   __shared__ double red_v[32];
   __shared__ int red_i[32];
+  __shared__ double c_colv, c_rowv;  // this CTA's argmax candidates
+  __shared__ int c_coli, c_rowi;
   __shared__ double s_colmax, s_rowmax;
   __shared__ int s_imax, s_jmax;
   __shared__ int s_bad;
 
-  for (int idx = tid; idx < n * n; idx += nt) {
+  for (int idx = gtid; idx < n * n; idx += gnt) {
     const int i = idx / n, j = idx % n;
     A[idx] = (i >= j) ? Ts[idx] : make_double2(0.0, 0.0);
     C[idx] = make_double2(0.0, 0.0);
   }
   for (int i = tid; i < n; i += nt) perm[i] = i;
   if (tid == 0) s_bad = 0;
-  __syncthreads();
+  tf_sync<CL>();
 
   const double alpha = (1.0 + sqrt(17.0)) / 8.0;
   int k = 0, n2 = 0;
@@ -102,14 +178,15 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
     // largest off-diagonal entry of column k
     double v = -1.0;
     int vi = n;
-    for (int i = k + 1 + tid; i < n; i += nt) {
+    for (int i = k + 1 + gtid; i < n; i += gnt) {
       const double c = cabs1(A[(int64_t)i * n + k]);
       if (c > v) {
         v = c;
         vi = i;
       }
     }
-    block_argmax(v, vi, red_v, red_i, &s_colmax, &s_imax);
+    block_argmax(v, vi, red_v, red_i, &c_colv, &c_coli);
+    cluster_argmax<CL>(&c_colv, &c_coli, &s_colmax, &s_imax);
     const double colmax = (k + 1 < n) ? s_colmax : 0.0;
     const int imax = s_imax;
     const double absakk = fabs(A[(int64_t)k * n + k].x);
@@ -124,7 +201,7 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
       // largest off-diagonal entry of row/column imax in the trailing matrix
       double r = -1.0;
       int ri = n;
-      for (int j = k + tid; j < n; j += nt) {
+      for (int j = k + gtid; j < n; j += gnt) {
         if (j == imax) continue;
         const double c = (j < imax) ? cabs1(A[(int64_t)imax * n + j]) : cabs1(A[(int64_t)j * n + imax]);
         if (c > r) {
@@ -132,7 +209,8 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
           ri = j;
         }
       }
-      block_argmax(r, ri, red_v, red_i, &s_rowmax, &s_jmax);
+      block_argmax(r, ri, red_v, red_i, &c_rowv, &c_rowi);
+      cluster_argmax<CL>(&c_rowv, &c_rowi, &s_rowmax, &s_jmax);
       const double rowmax = s_rowmax;
       if (absakk >= alpha * colmax * (colmax / rowmax)) {
         kstep = 1;
@@ -149,7 +227,7 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
     if (kp != kk) {
       // symmetric interchange of rows/cols kk and kp (kk < kp), lower storage;
       // also swaps the rows of the L columns already computed.
-      for (int j = tid; j < n; j += nt) {
+      for (int j = gtid; j < n; j += gnt) {
         if (j < kk) {
           const double2 t = A[(int64_t)kk * n + j];
           A[(int64_t)kk * n + j] = A[(int64_t)kp * n + j];
@@ -165,18 +243,20 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
         }
       }
       if (tid == 0) {
-        const double2 dk = A[(int64_t)kk * n + kk];
-        A[(int64_t)kk * n + kk] = make_double2(A[(int64_t)kp * n + kp].x, 0.0);
-        A[(int64_t)kp * n + kp] = make_double2(dk.x, 0.0);
-        A[(int64_t)kp * n + kk] = cconj(A[(int64_t)kp * n + kk]);
-        const int t = perm[kk];
+        if (q == 0) {
+          const double2 dk = A[(int64_t)kk * n + kk];
+          A[(int64_t)kk * n + kk] = make_double2(A[(int64_t)kp * n + kp].x, 0.0);
+          A[(int64_t)kp * n + kp] = make_double2(dk.x, 0.0);
+          A[(int64_t)kp * n + kk] = cconj(A[(int64_t)kp * n + kk]);
+        }
+        const int t = perm[kk];  // every CTA keeps the permutation
         perm[kk] = perm[kp];
         perm[kp] = t;
       }
     }
-    __syncthreads();
-    const int m = n - k - kstep;  // trailing size
+    tf_sync<CL>();
     const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    // rows of the trailing matrix this CTA updates: i = i0 + q + CL t, t = warp + nw u
     if (kstep == 1) {
       const double d = A[(int64_t)k * n + k].x;
       if (d != 0.0) {
@@ -190,7 +270,7 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
         __syncthreads();
         // A[i][j] -= l_i conj(a_j) on the lower trailing triangle: a warp per
         // row, lanes along the row (contiguous j)
-        for (int i = k + 1 + warp; i < n; i += nw) {
+        for (int i = k + 1 + q + CL * warp; i < n; i += CL * nw) {
           const double2 li = lc0[i];
           double2* row = A + (int64_t)i * n;
           for (int j = k + 1 + lane; j <= i; j += 32) {
@@ -201,8 +281,9 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
             row[j] = x;
           }
         }
-        __syncthreads();
-        for (int i = k + 1 + tid; i < n; i += nt) A[(int64_t)i * n + k] = lc0[i];
+        // every CTA has read column k before it is overwritten
+        tf_sync<CL>();
+        for (int i = k + 1 + q + CL * tid; i < n; i += CL * nt) A[(int64_t)i * n + k] = lc0[i];
       }
       if (tid == 0) {
         lam[k] = d;
@@ -231,7 +312,7 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
         }
         __syncthreads();
         // A[i][j] -= l1_i conj(w1_j) + l2_i conj(w2_j), lower trailing triangle
-        for (int i = k + 2 + warp; i < n; i += nw) {
+        for (int i = k + 2 + q + CL * warp; i < n; i += CL * nw) {
           const double2 l1 = lc0[i], l2 = lc1[i];
           double2* row = A + (int64_t)i * n;
           for (int j = k + 2 + lane; j <= i; j += 32) {
@@ -243,8 +324,8 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
             row[j] = x;
           }
         }
-        __syncthreads();
-        for (int i = k + 2 + tid; i < n; i += nt) {
+        tf_sync<CL>();
+        for (int i = k + 2 + q + CL * tid; i < n; i += CL * nt) {
           A[(int64_t)i * n + k] = lc0[i];
           A[(int64_t)i * n + k + 1] = lc1[i];
         }
@@ -276,7 +357,8 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
         ++n2;
       }
     }
-    __syncthreads();
+    // the next step reads the updated trailing matrix and L columns
+    tf_sync<CL>();
     k += kstep;
   }
   if (tid == 0) {
@@ -290,19 +372,22 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
       else if (lam[r] < 0) outrow[r] = in++;
       else outrow[r] = -1;
     }
-    npos[slot] = np;
-    nneg[slot] = nn;
-    atomicAdd(npiv2, n2);
-    if (s_bad) atomicExch(err, FLAPW_ERR_FACTOR);
+    if (q == 0) {
+      npos[slot] = np;
+      nneg[slot] = nn;
+      atomicAdd(npiv2, n2);
+      if (s_bad) atomicExch(err, FLAPW_ERR_FACTOR);
+    }
   }
   __syncthreads();
-  for (int i = tid; i < n; i += nt) {
-    perm_out[slot * n + i] = perm[i];
-    outrow_out[slot * n + i] = outrow[i];
-  }
+  if (q == 0)
+    for (int i = tid; i < n; i += nt) {
+      perm_out[slot * n + i] = perm[i];
+      outrow_out[slot * n + i] = outrow[i];
+    }
   // M[r][i] = sqrt|lam_r| sum_{j in block(r)} conj(Q[j][r]) (L^H)[j][i],
   // (L^H)[j][i] = conj(L[i][j]) with unit diagonal and zero for i < j.
-  for (int idx = tid; idx < n * n; idx += nt) {
+  for (int idx = gtid; idx < n * n; idx += gnt) {
     const int r = idx / n, i = idx % n;
     const int b0 = (blk[r] == 0) ? r - 1 : r;  // first row of r's block
     const int bs = (blk[b0] == 2) ? 2 : 1;
@@ -321,6 +406,8 @@ __global__ void __launch_bounds__(kTfThreads) tfactor_kernel(const double2* T, i
     const double sq = sqrt(fabs(lam[r]));
     C[(int64_t)r * n + i] = make_double2(sq * acc.x, sq * acc.y);
   }
+  // no CTA leaves while another may still read its shared memory
+  if (CL > 1) tf_sync<CL>();
 }
 
 __global__ void layout_kernel(const int* npos, const int* nneg, const int* atom_slot, int n_atoms,
@@ -349,11 +436,27 @@ __global__ void layout_kernel(const int* npos, const int* nneg, const int* atom_
 
 cudaError_t launch_tfactor(const double2* T, int n, int n_slots, double2* work, double2* CH,
                            int* perm, int* outrow, int* npos, int* nneg, int* npiv2, int* err,
-                           cudaStream_t st) {
+                           bool cluster, cudaStream_t st) {
   if (n > kMaxN) return cudaErrorInvalidValue;
-  tfactor_kernel<<<n_slots, kTfThreads, 0, st>>>(T, n, work, CH, perm, outrow, npos, nneg, npiv2,
-                                                 err);
-  return cudaGetLastError();
+  if (n_slots == 0) return cudaSuccess;
+  if (!cluster) {
+    tfactor_kernel<1><<<n_slots, kTfThreads, 0, st>>>(T, n, work, CH, perm, outrow, npos, nneg,
+                                                      npiv2, err);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(n_slots * kTfCluster));
+  cfg.blockDim = dim3(kTfClusterThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kTfCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, tfactor_kernel<kTfCluster>, T, n, work, CH, perm, outrow, npos,
+                            nneg, npiv2, err);
 }
 
 cudaError_t launch_layout(const int* npos, const int* nneg, const int* atom_slot, int n_atoms,

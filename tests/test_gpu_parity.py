@@ -279,6 +279,31 @@ def test_host_buffers_through_the_abi():
     assert herm_relerr(lower_to_full(S, ng, 0), So) <= TOL_EMU
 
 
+@pytest.mark.parametrize("layout", [fl.LAYOUT_LOWER_FULL, fl.LAYOUT_LOWER_PACKED])
+def test_host_outputs_every_lower_element_copied(layout):
+    # pinned host outputs filled with NaN: the block-wise copy of the lower
+    # triangle must reach every lower element of every k-point (ragged N_G,
+    # one N_G above 64 x 32 so that the column blocks are wider than 64)
+    torch = torch_cuda()
+    p = inputs.small(88, n_atoms=3, n_types=2, lmax=3, n_target=(2100, 150, 65))
+    h = fl.from_problem(p, fl.default_options(precision=fl.PREC_EMU, layout=layout,
+                                              operands=fl.OPERANDS_FACTORED))
+    _, A, B = run_ab(p, h)
+    Hs, Ss = [], []
+    for k in range(p.n_k):
+        ng = h.num_g(k)
+        n = ng * (ng + 1) // 2 if layout == fl.LAYOUT_LOWER_PACKED else ng * ng
+        Hs.append(torch.full((n,), float("nan"), dtype=torch.complex128).pin_memory())
+        Ss.append(torch.full((n,), float("nan"), dtype=torch.complex128).pin_memory())
+    h.build_HS(p.T, p.atom_slot, p.U, A, B, Hs, Ss)
+    h.sync()
+    for k in range(p.n_k):
+        Ho, So = oracle_hs(p, k)
+        ng = Ho.shape[0]
+        assert herm_relerr(lower_to_full(Hs[k], ng, layout), Ho) <= TOL_EMU, k
+        assert herm_relerr(lower_to_full(Ss[k], ng, layout), So) <= TOL_EMU, k
+
+
 def test_bad_calls_return_codes_not_faults():
     p = inputs.config1()
     h = fl.from_problem(p)

@@ -63,6 +63,27 @@ def test_config2_sampled_columns():
     assert np.linalg.norm(Hg - Ho) / np.linalg.norm(Ho) <= TOL_EMU
 
 
+@pytest.mark.parametrize("lmax,hpd", [(8, False), (8, True), (12, False), (2, False)])
+def test_cluster_factorisation_matches_single_cta(lmax, hpd):
+    # with S by the addition theorem each T slot is factorised by a cluster of
+    # CTAs; the pivot decisions and every element's arithmetic are those of
+    # the one-CTA kernel, so the factors agree (to the compiler's choice of
+    # fused multiply-adds; a different pivot sequence would differ at O(1))
+    p = inputs.small(95 + lmax, n_atoms=3, n_types=3, lmax=lmax, n_target=(120,), hpd=hpd)
+    h1, _, _, _ = run_hs(p, fl.PREC_FP64, operands=fl.OPERANDS_FACTORED)
+    f1 = [h1.factor(s) for s in range(p.n_slots)]
+    h8, _, _, _ = run_hs(p, fl.PREC_FP64, operands=fl.OPERANDS_FACTORED, s_method=fl.S_LEGENDRE)
+    for slot in range(p.n_slots):
+        CH, npos, nneg = h8.factor(slot)
+        assert (npos, nneg) == f1[slot][1:]
+        assert np.abs(CH - f1[slot][0]).max() <= 1e-13 * np.abs(f1[slot][0]).max()
+        n = CH.shape[0]
+        sig = np.concatenate([np.ones(npos), -np.ones(nneg), np.zeros(n - npos - nneg)])
+        R = CH.conj().T @ (sig[:, None] * CH)
+        assert np.linalg.norm(R - p.T[slot]) <= 1e-13 * np.linalg.norm(p.T[slot])
+    assert h8.stats()["n_pivot2"] == h1.stats()["n_pivot2"]
+
+
 def test_requires_factored_operands():
     p = inputs.config1()
     bad = fl.default_options(operands=fl.OPERANDS_FROM_AB, s_method=fl.S_LEGENDRE)
