@@ -203,8 +203,11 @@ __global__ void __launch_bounds__(128) slegendre_split_kernel(SLegArgs a) {
   for (int c = 0; c < 3; ++c) kh[3 * gi + c] = dfl::split(a.khat[3 * gi + c]);
 }
 
-// slegendre_kernel in double-float.
-__global__ void __launch_bounds__(256) slegendre_df_kernel(SLegArgs a, const F64Tile* __restrict__ tiles) {
+// slegendre_kernel in double-float: 512 threads of 2 x 4 elements (the double-float
+// accumulators of 4 x 4 per thread allowed one CTA of 8 warps per SM).
+constexpr int kDfRows = 2, kDfCols = 4;
+constexpr int kDfThreads = (kT / kDfRows) * (kT / kDfCols);
+__global__ void __launch_bounds__(kDfThreads) slegendre_df_kernel(SLegArgs a, const F64Tile* __restrict__ tiles) {
   using dfl::df;
   __shared__ float2 kh[2][kT][3];
   __shared__ float2 rad[4][kL1][kT];
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(256) slegendre_df_kernel(SLegArgs a, const F64
   const int64_t ng = P.n_g;
   const int64_t g0 = P.row_base - a.s_row0;
   const int r0 = T.ib * kT, c0 = T.jb * kT;
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int tid = threadIdx.x, ty = tid / (kT / kDfCols), tx = tid % (kT / kDfCols);
   const int L1 = a.lmax + 1;
   const int64_t G = a.g_total;
   const int64_t nr = (int64_t)a.n_types * L1 * G;
@@ -227,34 +230,34 @@ __global__ void __launch_bounds__(256) slegendre_df_kernel(SLegArgs a, const F64
     rec_ab[tid][0] = dfl::split((double)(2 * tid + 1) / (double)(tid + 1));
     rec_ab[tid][1] = dfl::split((double)tid / (double)(tid + 1));
   }
-  for (int i = tid; i < 2 * kT * 3; i += 256) {
+  for (int i = tid; i < 2 * kT * 3; i += kDfThreads) {
     const int w = i / (kT * 3), e = i % (kT * 3), g = e / 3, c = e % 3;
     const int64_t gl = (w == 0 ? r0 : c0) + g;
     kh[w][g][c] = (gl < ng) ? khg[3 * (g0 + gl) + c] : zero2;
   }
-  df Sr[4][4], Si[4][4];
+  df Sr[kDfRows][kDfCols], Si[kDfRows][kDfCols];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < kDfRows; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) Sr[i][j] = Si[i][j] = df{0.f, 0.f};
+    for (int j = 0; j < kDfCols; ++j) Sr[i][j] = Si[i][j] = df{0.f, 0.f};
 
   for (int t = 0; t < a.n_types; ++t) {
     __syncthreads();
-    for (int i = tid; i < 4 * L1 * kT; i += 256) {
+    for (int i = tid; i < 4 * L1 * kT; i += kDfThreads) {
       const int w = i / (L1 * kT), e = i % (L1 * kT), l = e / kT, g = e % kT;
       const int64_t gl = ((w < 2) ? r0 : c0) + g;
       rad[w][l][g] = (gl < ng) ? radg[w * nr + ((int64_t)t * L1 + l) * G + g0 + gl] : zero2;
     }
-    df rr[4][4], ri[4][4];  // rho_t
+    df rr[kDfRows][kDfCols], ri[kDfRows][kDfCols];  // rho_t
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < kDfRows; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) rr[i][j] = ri[i][j] = df{0.f, 0.f};
+      for (int j = 0; j < kDfCols; ++j) rr[i][j] = ri[i][j] = df{0.f, 0.f};
     const int a0 = a.type_start[t], a1 = a.type_start[t + 1];
     for (int ab = a0; ab < a1; ab += kChunkAtoms) {
       const int na = min(kChunkAtoms, a1 - ab);
       __syncthreads();
-      for (int i = tid; i < 2 * kChunkAtoms * kT; i += 256) {
+      for (int i = tid; i < 2 * kChunkAtoms * kT; i += kDfThreads) {
         const int w = i / (kChunkAtoms * kT), e = i % (kChunkAtoms * kT), q = e / kT, g = e % kT;
         const int64_t gl = (w == 0 ? r0 : c0) + g;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -263,17 +266,16 @@ __global__ void __launch_bounds__(256) slegendre_df_kernel(SLegArgs a, const F64
       }
       __syncthreads();
       for (int q = 0; q < na; ++q) {
-        float4 pr[4], pc[4];
+        float4 pr[kDfRows], pc[kDfCols];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          pr[i] = phs[0][q][ty * 4 + i];
-          pc[i] = phs[1][q][tx * 4 + i];
-        }
+        for (int i = 0; i < kDfRows; ++i) pr[i] = phs[0][q][ty * kDfRows + i];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int j = 0; j < kDfCols; ++j) pc[j] = phs[1][q][tx * kDfCols + j];
+#pragma unroll
+        for (int i = 0; i < kDfRows; ++i) {
           const df ar{pr[i].x, pr[i].y}, ai{pr[i].z, pr[i].w};
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {  // conj(pr) pc
+          for (int j = 0; j < kDfCols; ++j) {  // conj(pr) pc
             const df br{pc[j].x, pc[j].y}, bi{pc[j].z, pc[j].w};
             rr[i][j] = dfl::fma(ar, br, dfl::fma(ai, bi, rr[i][j]));
             ri[i][j] = dfl::fma(ar, bi, dfl::fma(dfl::neg(ai), br, ri[i][j]));
@@ -283,11 +285,11 @@ __global__ void __launch_bounds__(256) slegendre_df_kernel(SLegArgs a, const F64
     }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int rw = ty * 4 + i;
+    for (int i = 0; i < kDfRows; ++i) {
+      const int rw = ty * kDfRows + i;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int cl = tx * 4 + j;
+      for (int j = 0; j < kDfCols; ++j) {
+        const int cl = tx * kDfCols + j;
         const df x = dfl::fma(dfl::make(kh[0][rw][0]), dfl::make(kh[1][cl][0]),
                               dfl::fma(dfl::make(kh[0][rw][1]), dfl::make(kh[1][cl][1]),
                                        dfl::mul(dfl::make(kh[0][rw][2]), dfl::make(kh[1][cl][2]))));
@@ -310,11 +312,11 @@ __global__ void __launch_bounds__(256) slegendre_df_kernel(SLegArgs a, const F64
   }
   double* outd = reinterpret_cast<double*>(P.out);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t gr = r0 + ty * 4 + i;
+  for (int i = 0; i < kDfRows; ++i) {
+    const int64_t gr = r0 + ty * kDfRows + i;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t gc = c0 + tx * 4 + j;
+    for (int j = 0; j < kDfCols; ++j) {
+      const int64_t gc = c0 + tx * kDfCols + j;
       if (gr < ng && gc <= gr) {
         const int64_t o = (P.layout == FLAPW_LAYOUT_LOWER_PACKED) ? gc * ng - gc * (gc - 1) / 2 + (gr - gc)
                                                                    : gc * P.ld + gr;
@@ -342,7 +344,7 @@ cudaError_t launch_slegendre(const SLegArgs& a, const F64Tile* tiles, int n_tile
   if (a.lmax < 0 || a.lmax > kMaxLmax) return cudaErrorInvalidValue;
   if (a.dfw) {
     slegendre_split_kernel<<<(unsigned)((a.g_total + 127) / 128), 128, 0, st>>>(a);
-    slegendre_df_kernel<<<n_tiles, 256, 0, st>>>(a, tiles);
+    slegendre_df_kernel<<<n_tiles, kDfThreads, 0, st>>>(a, tiles);
   } else {
     slegendre_kernel<<<n_tiles, 256, 0, st>>>(a, tiles);
   }

@@ -115,19 +115,28 @@ template <int CL>
 __device__ void cluster_argmax(const double* cand_v, const int* cand_i, double* out_v, int* out_i) {
   if (CL > 1) {
     tf_sync<CL>();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+      // lane r reads CTA r's candidate: the remote loads overlap
+      const int lane = threadIdx.x;
       double bv = -1.0;
       int bi = 1 << 30;
-      for (uint32_t r = 0; r < (uint32_t)CL; ++r) {
-        const double v = tf_ld_remote(cand_v, r);
-        const int i = tf_ld_remote(cand_i, r);
-        if (v > bv || (v == bv && i < bi)) {
-          bv = v;
-          bi = i;
+      if (lane < CL) {
+        bv = tf_ld_remote(cand_v, (uint32_t)lane);
+        bi = tf_ld_remote(cand_i, (uint32_t)lane);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) {
+          bv = ov;
+          bi = oi;
         }
       }
-      *out_v = bv;
-      *out_i = bi;
+      if (lane == 0) {
+        *out_v = bv;
+        *out_i = bi;
+      }
     }
     __syncthreads();
   } else {
