@@ -59,7 +59,7 @@ def max_over_ranks(x: float) -> float:
 # (profiles/herk_emu_c2_ortho16_l8_ng3990_full.md); keyed by workload, slices,
 # S method and H method.  Other shapes report null.
 MEASURED_TRAFFIC = {
-    ("c2_ortho_16at_l8_ng4000", 7, "contraction", "factored"): 4.8165e9,
+    ("c2_ortho_16at_l8_ng4000", 7, "contraction", "factored"): 2.4109e9,
 }
 
 

@@ -92,7 +92,8 @@ typedef struct flapw_options {
                     arguments repeat (default 0) */
   int autotune;  /* 1: time the contraction's tile-order variants once per shape and
                     keep the fastest (default 0: fixed choice) */
-  int tile_order; /* 0: library default; k+1 forces tile order k of the emulated
+  int tile_order; /* 0: library default (bands of 8 row blocks for N_G <= 8192,
+                     else bands of 2); k+1 forces tile order k of the emulated
                      contraction (0 row-major, 1 column-major, 2/3/4 bands of
                      4/2/8 row blocks of 256), ignored when autotune is on */
   int s_method;   /* FLAPW_S_CONTRACTION (default): S = Z_S^H Z_S like H;

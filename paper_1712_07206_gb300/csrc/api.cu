@@ -134,6 +134,7 @@ struct flapw_ctx {
   int64_t k_terms = 0;           // most products summed into one output element
   int n_emu_tiles = 0, n_f64_tiles = 0, split_emu = 0, split_f64 = 0, tiles_order = -1;
   int tile_order = 3;            // emulated tile order in use (see make_tiles)
+  int default_order = 3;         // the order for this crystal's sizes (default_tile_order)
   int64_t tuned_key = -1;        // shape the autotuner last ran on
   int64_t tiles_rows_key = -1;
   int tiles_pairs = -1;          // pair counts the tile lists' last waves were split for
@@ -442,6 +443,13 @@ int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int6
   return FLAPW_OK;
 }
 
+// Library default tile order for the largest N_G: bands of 8 row blocks for
+// N_G <= 8192, else bands of 2.  Measured on the contraction (GB300): N_G 3990
+// bands of 8 / 4 / 2: 6.03 / 6.04 / 6.12 ms; N_G 11996: 363 / 326 / 320 ms;
+// N_G 23993: 4584 / 4153 / 3739 ms.  Larger problems need the operand rows
+// of the concurrently running tiles to overlap more in L2.
+int default_tile_order(int64_t max_ng) { return max_ng <= 8192 ? 4 : 3; }
+
 // Times the emulated contraction under every tile order on the slices the
 // last build left in place (the outputs are rewritten with the same values)
 // and keeps the fastest order for this shape.
@@ -569,6 +577,10 @@ int flapw_hs_create(const double lattice[9], int n_atoms, const double* pos_frac
   }
   h->g_total = h->goff[n_k];
   if (h->g_total > (int64_t)1 << 30) return fail(nullptr, FLAPW_ERR_UNSUPPORTED, "too many plane waves");
+  int64_t max_ng = 0;
+  for (int k = 0; k < n_k; ++k) max_ng = std::max<int64_t>(max_ng, h->goff[k + 1] - h->goff[k]);
+  h->default_order = default_tile_order(max_ng);
+  if (!(h->opt.tile_order > 0 && !h->opt.autotune)) h->tile_order = h->default_order;
   h->ktau.resize((size_t)n_k * n_atoms);
   for (int k = 0; k < n_k; ++k)
     for (int a = 0; a < n_atoms; ++a)
@@ -632,6 +644,7 @@ int flapw_set_options(flapw_handle h, const flapw_options* opt) {
   if (int rc = check_options(h, *opt)) return rc;
   h->opt = *opt;
   if (opt->tile_order > 0 && !opt->autotune) h->tile_order = opt->tile_order - 1;
+  else if (!opt->autotune) h->tile_order = h->default_order;
   return FLAPW_OK;
 }
 
