@@ -84,6 +84,31 @@ def test_cluster_factorisation_matches_single_cta(lmax, hpd):
     assert h8.stats()["n_pivot2"] == h1.stats()["n_pivot2"]
 
 
+def test_zero_pivots_dropped_in_both_factorisations():
+    # T with two zero rows and columns: the elimination meets zero columns
+    # (zero pivots, rows dropped from the operand) in the one-CTA and the
+    # cluster factorisation alike; H still equals the oracle's
+    p = inputs.small(93, n_atoms=3, n_types=2, lmax=8, n_target=(140,))
+    T = p.T.copy()
+    for slot in range(p.n_slots):
+        for i in (5, 97):
+            T[slot][i, :] = 0
+            T[slot][:, i] = 0
+    p.T = T
+    h1, H1, _, _ = run_hs(p, fl.PREC_FP64, operands=fl.OPERANDS_FACTORED)
+    h8, H8, _, _ = run_hs(p, fl.PREC_FP64, operands=fl.OPERANDS_FACTORED, s_method=fl.S_LEGENDRE)
+    n = 2 * p.n_L
+    for slot in range(p.n_slots):
+        CH1, np1, nn1 = h1.factor(slot)
+        CH8, np8, nn8 = h8.factor(slot)
+        assert (np8, nn8) == (np1, nn1) and np1 + nn1 == n - 2
+        assert np.abs(CH8 - CH1).max() <= 1e-13 * np.abs(CH1).max()
+    Ho, _ = oracle_hs(p)
+    ng = Ho.shape[0]
+    for H in (H1, H8):
+        assert herm_relerr(lower_to_full(H[0], ng, 0), Ho) <= TOL_F64
+
+
 def test_requires_factored_operands():
     p = inputs.config1()
     bad = fl.default_options(operands=fl.OPERANDS_FROM_AB, s_method=fl.S_LEGENDRE)
