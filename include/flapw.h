@@ -94,8 +94,9 @@ typedef struct flapw_options {
                     keep the fastest (default 0: fixed choice) */
   int tile_order; /* 0: library default (bands of 8 row blocks for N_G <= 8192,
                      else bands of 2); k+1 forces tile order k of the emulated
-                     contraction (0 row-major, 1 column-major, 2/3/4 bands of
-                     4/2/8 row blocks of 256), ignored when autotune is on */
+                     contraction (0 row-major, 1 column-major, 2/3/4/5 bands of
+                     4/2/8/3 row blocks of 256, 6 bands of 2 with alternating
+                     column direction), ignored when autotune is on */
   int s_method;   /* FLAPW_S_CONTRACTION (default): S = Z_S^H Z_S like H;
                      FLAPW_S_LEGENDRE: S by the addition theorem (requires
                      FLAPW_OPERANDS_FACTORED; in FP64 on the FP64 path, in

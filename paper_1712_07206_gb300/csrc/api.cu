@@ -17,7 +17,7 @@ using namespace flapw;
 namespace {
 
 std::string g_last_error;  // errors of calls without a handle
-constexpr int kNumTileOrders = 5;  // emulated tile orders, see make_tiles
+constexpr int kNumTileOrders = 7;  // emulated tile orders, see make_tiles
 
 // Device buffer that grows on demand.
 struct DevBuf {
@@ -205,7 +205,7 @@ int check_options(flapw_ctx* h, const flapw_options& o) {
   if (o.operands != FLAPW_OPERANDS_FROM_AB && o.operands != FLAPW_OPERANDS_FACTORED)
     return fail(h, FLAPW_ERR_ARG, "options.operands is not a FLAPW_OPERANDS_* value");
   if (o.tile_order < 0 || o.tile_order > kNumTileOrders)
-    return fail(h, FLAPW_ERR_ARG, "options.tile_order must be in 0..5");
+    return fail(h, FLAPW_ERR_ARG, "options.tile_order must be in 0..7");
   if (o.s_method != FLAPW_S_CONTRACTION && o.s_method != FLAPW_S_LEGENDRE)
     return fail(h, FLAPW_ERR_ARG, "options.s_method is not a FLAPW_S_* value");
   if (o.s_method == FLAPW_S_LEGENDRE && o.operands != FLAPW_OPERANDS_FACTORED)
@@ -242,8 +242,9 @@ int upload(flapw_ctx* h, DevBuf& d, const std::vector<T>& v) {
 // emulated tiles decides which operand rows the ~75 concurrently running
 // tiles share in L2:
 //   order 0: row blocks outer, column blocks inner;  1: column blocks outer;
-//   order 2/3/4: grouped raster -- bands of 4/2/8 row blocks, and within a
-//   band column by column, so the concurrent tiles touch a compact set of rows.
+//   order 2/3/4/5: grouped raster -- bands of 4/2/8/3 row blocks, and within a
+//   band column by column, so the concurrent tiles touch a compact set of rows;
+//   order 6: bands of 2, the column direction alternating from band to band.
 void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order, int pairs,
                 std::vector<EmuTile>* emu, std::vector<F64Tile>* f64, int* n_split_ids) {
   const size_t emu0 = emu->size();
@@ -260,11 +261,13 @@ void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order, int p
         for (int ib = 0; ib < nib; ++ib)
           if (valid(ib, jb)) emu->push_back(EmuTile{p, ib, jb, 0});
     } else {
-      const int band = (order == 2) ? 4 : (order == 3) ? 2 : 8;
-      for (int i0 = 0; i0 < nib; i0 += band)
-        for (int jb = 0; jb < njb; ++jb)
+      const int band = (order == 2) ? 4 : (order == 3 || order == 6) ? 2 : (order == 4) ? 8 : 3;
+      for (int i0 = 0, b = 0; i0 < nib; i0 += band, ++b)
+        for (int jj = 0; jj < njb; ++jj) {
+          const int jb = (order == 6 && (b & 1)) ? njb - 1 - jj : jj;
           for (int ib = i0; ib < std::min(nib, i0 + band); ++ib)
             if (valid(ib, jb)) emu->push_back(EmuTile{p, ib, jb, 0});
+        }
     }
     const int nb = (ng + 63) / 64;
     for (int ib = 0; ib < nb; ++ib)

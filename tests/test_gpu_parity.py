@@ -231,10 +231,24 @@ def test_autotune_keeps_results_and_picks_an_order():
     h.build_HS(p.T, p.atom_slot, p.U, A, B, [H], [S])
     h.sync()
     st = h.stats()
-    assert 0 <= st["tile_order"] <= 4
+    assert 0 <= st["tile_order"] <= 6
     Ho, So = oracle_hs(p)
     assert herm_relerr(lower_to_full(H, ng, 0), Ho) <= TOL_EMU
     assert herm_relerr(lower_to_full(S, ng, 0), So) <= TOL_EMU
+
+
+@pytest.mark.parametrize("order", range(7))
+def test_every_tile_order(order):
+    # the order only schedules the tiles: every one must give the oracle's H and S
+    # (2 k-points, ragged N_G, more row blocks than any band)
+    p = inputs.small(19, n_atoms=3, n_types=2, lmax=4, n_target=(2300, 700))
+    h, Hs, Ss, _ = run_hs(p, fl.PREC_EMU, operands=fl.OPERANDS_FACTORED, tile_order=order + 1)
+    assert h.stats()["tile_order"] == order
+    for k in range(p.n_k):
+        Ho, So = oracle_hs(p, k)
+        ng = Ho.shape[0]
+        assert herm_relerr(lower_to_full(Hs[k], ng, 0), Ho) <= TOL_EMU, (order, k)
+        assert herm_relerr(lower_to_full(Ss[k], ng, 0), So) <= TOL_EMU, (order, k)
 
 
 @pytest.mark.parametrize("precision", [fl.PREC_FP64, fl.PREC_EMU])
