@@ -139,6 +139,8 @@ struct flapw_ctx {
   int64_t tiles_rows_key = -1;
   int tiles_pairs = -1;          // pair counts the tile lists' last waves were split for
   int split_ids = 0;             // split tiles of a half (scratch slots)
+  bool tiles_split = false;      // the first half's list is in two parts (H to host memory)
+  int split_emu_b = 0, split_f64_b = 0;  // start of the first half's second part
   DevBuf d_split;                // their partial sums and completion counts
   SliceMaps tmap{};
   void* tmap_base = nullptr;
@@ -152,8 +154,8 @@ struct flapw_ctx {
   // events: 0 start, 1 factor done (aux), 2 S operands done, 3 S sliced, 4 S contracted,
   // 5 end, 6/7 build_AB, 8 H operands start, 9 S operands start, 10 H operands done,
   // 11 H sliced, 12 H contracted, 13 fork, 14/15 autotune, 16 auxiliary work done (join),
-  // 17 A/B assembly start
-  cudaEvent_t ev[18]{};
+  // 17 A/B assembly start, 18 first part of a split H contraction done
+  cudaEvent_t ev[19]{};
   bool ev_recorded = false, ev_ab = false, ev_engine = false;
   cudaStream_t last_stream = nullptr;
   flapw_stats stats{};
@@ -237,6 +239,13 @@ int upload(flapw_ctx* h, DevBuf& d, const std::vector<T>& v) {
   return FLAPW_OK;
 }
 
+// First column block of the second part of a split H contraction: the last
+// ~20 % of the lower-triangle tiles lie right of column 0.55 N_G.  With the
+// output going to host memory at ~190 GB/s, that part's run time (~20 % of
+// the launch) covers the copy of the first part's columns (~80 % of the
+// bytes) on config-2-like shapes.
+int h_split_block(int ng) { return (int)(0.55 * ((ng + 63) / 64)); }
+
 // Emulated contraction tiles (256 x 64, one per CTA pair) and FP64 tiles
 // (64 x 64) of the lower triangles of problems [p0, p1).  The order of the
 // emulated tiles decides which operand rows the ~75 concurrently running
@@ -245,13 +254,22 @@ int upload(flapw_ctx* h, DevBuf& d, const std::vector<T>& v) {
 //   order 2/3/4/5: grouped raster -- bands of 4/2/8/3 row blocks, and within a
 //   band column by column, so the concurrent tiles touch a compact set of rows;
 //   order 6: bands of 2, the column direction alternating from band to band.
+// part 0 takes every tile; 1 the column blocks below h_split_block(N_G), 2 the
+// rest (an H contraction in two launches, so that the first part's columns
+// can go to host memory while the second part runs).
 void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order, int pairs,
-                std::vector<EmuTile>* emu, std::vector<F64Tile>* f64, int* n_split_ids) {
+                std::vector<EmuTile>* emu, std::vector<F64Tile>* f64, int* n_split_ids,
+                int part = 0) {
   const size_t emu0 = emu->size();
   for (int p = p0; p < p1; ++p) {
     const int ng = probs[p].n_g;
     const int nib = (ng + 255) / 256, njb = (ng + 63) / 64;
-    auto valid = [&](int ib, int jb) { return jb * 64 <= ib * 256 + 255; };
+    const int j1 = h_split_block(ng);
+    auto valid = [&](int ib, int jb) {
+      if (part == 1 && jb >= j1) return false;
+      if (part == 2 && jb < j1) return false;
+      return jb * 64 <= ib * 256 + 255;
+    };
     if (order == 0) {
       for (int ib = 0; ib < nib; ++ib)
         for (int jb = 0; jb < njb; ++jb)
@@ -271,7 +289,8 @@ void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order, int p
     }
     const int nb = (ng + 63) / 64;
     for (int ib = 0; ib < nb; ++ib)
-      for (int jb = 0; jb <= ib; ++jb) f64->push_back(F64Tile{p, ib, jb, 0});
+      for (int jb = 0; jb <= ib; ++jb)
+        if (part == 0 || (part == 1) == (jb < j1)) f64->push_back(F64Tile{p, ib, jb, 0});
   }
   // The pairs take the tiles round-robin, so the last rem = n mod pairs tiles
   // form a partly empty last wave.  Each of them becomes f K parts (f pairs
@@ -307,30 +326,29 @@ struct OutPlan {
 // memory: at most about 32 blocks per matrix, at least 64 columns.
 int64_t copy_block_cols(int64_t ng) { return std::max<int64_t>(64, (ng + 31) / 32); }
 
-// Device-to-host copy of one output, its pieces alternating between two
-// streams (two copy engines when st0 != st1).  The packed layout goes in two
-// halves; the full layout (ld = ng) block of columns by block of columns, each
-// from the block's first diagonal element down, so that about half of the
-// N_G^2 elements (the lower triangle and the small triangles above the
-// diagonal inside each block) cross the link.
-cudaError_t copy_out(void* dst, const double2* src, int64_t ng, int layout, cudaStream_t st0,
-                     cudaStream_t st1) {
-  if (ng == 0) return cudaSuccess;
+// Device-to-host copy of columns [c0, c1) of one output's lower triangle.
+// The packed layout is one contiguous range; the full layout (ld = ng) goes
+// block of columns by block of columns, each from the block's first diagonal
+// element down, so that about half of the N_G^2 elements (the lower triangle
+// and the small triangles above the diagonal inside each block) cross the
+// link.  (The link to pinned host memory runs at ~190 GB/s on this part with
+// one stream or two alike.)
+cudaError_t copy_out(void* dst, const double2* src, int64_t ng, int layout, int64_t c0, int64_t c1,
+                     cudaStream_t st) {
+  if (c1 <= c0) return cudaSuccess;
   char* d = static_cast<char*>(dst);
   const char* s = reinterpret_cast<const char*>(src);
   if (layout == FLAPW_LAYOUT_LOWER_PACKED) {
-    const size_t total = (size_t)(ng * (ng + 1) / 2) * 16, half = total / 32 * 16;
-    cudaError_t e = cudaMemcpyAsync(d, s, half, cudaMemcpyDeviceToHost, st0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d + half, s + half, total - half, cudaMemcpyDeviceToHost, st1);
-    return e;
+    const size_t o0 = (size_t)(c0 * ng - c0 * (c0 - 1) / 2) * 16;
+    const size_t o1 = (size_t)(c1 * ng - c1 * (c1 - 1) / 2) * 16;
+    return cudaMemcpyAsync(d + o0, s + o0, o1 - o0, cudaMemcpyDeviceToHost, st);
   }
   const int64_t w = copy_block_cols(ng);
-  int b = 0;
-  for (int64_t j0 = 0; j0 < ng; j0 += w, ++b) {
+  for (int64_t j0 = c0; j0 < c1; j0 += w) {
     const size_t off = (size_t)(j0 * ng + j0) * 16;
     const cudaError_t e = cudaMemcpy2DAsync(d + off, (size_t)ng * 16, s + off, (size_t)ng * 16,
-                                            (size_t)(ng - j0) * 16, (size_t)std::min(w, ng - j0),
-                                            cudaMemcpyDeviceToHost, (b & 1) ? st1 : st0);
+                                            (size_t)(ng - j0) * 16, (size_t)std::min(w, c1 - j0),
+                                            cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -360,7 +378,7 @@ int split_scratch(flapw_ctx* h, cudaStream_t st, SplitScratch* out) {
 
 // Slices (emulated precision; not if `presliced`, the slices being written
 // already) and contracts one half beside concurrent work that holds busy_sms
-// SMs.  Records ev_sl after the slicer and ev_k after the contraction.
+// SMs.  Records ev_sl (if >= 0) after the slicer and ev_k after the contraction.
 int enqueue_contraction(flapw_ctx* h, const Half& hf, int busy_sms, cudaStream_t st, int ev_sl,
                         int ev_k, bool presliced = false) {
   const int s = slices_of(h);
@@ -370,7 +388,7 @@ int enqueue_contraction(flapw_ctx* h, const Half& hf, int busy_sms, cudaStream_t
       CK(h, launch_slicer(h->d_Z.as<double2>(), h->k_alloc, h->d_probs.as<Prob>(), h->d_rowprob.as<int>(),
                           0, rows, hf.row0, hf.nrows, s, h->d_SL.as<__half>(), h->d_rexp.as<int>(), st),
          "slicer launch");
-    CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
+    if (ev_sl >= 0) CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
     SplitScratch sp{};
     if (int rc = split_scratch(h, st, &sp)) return rc;
     CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf.emu_t0,
@@ -378,7 +396,7 @@ int enqueue_contraction(flapw_ctx* h, const Half& hf, int busy_sms, cudaStream_t
                           h->d_cnt.as<int>() + 2, busy_sms, sp, st),
        "emulated contraction launch");
   } else {
-    CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
+    if (ev_sl >= 0) CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
     CK(h, launch_herk_f64(h->d_Z.as<double2>(), h->k_alloc, h->d_probs.as<Prob>(),
                           h->d_f64_tiles.as<F64Tile>() + hf.f64_t0, hf.f64_nt, st),
        "FP64 contraction launch");
@@ -406,9 +424,12 @@ int ensure_slices(flapw_ctx* h) {
 }
 
 // Tile lists of problems [0, n_first) then [n_first, n_prob), the first half
-// contracted beside busy_first busy SMs, the second beside busy_second.
+// contracted beside busy_first busy SMs, the second beside busy_second.  With
+// split_first the first half is two lists (make_tiles parts 1 and 2):
+// *first, then *first_b.
 int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int64_t key,
-                 Half* first, Half* second, int busy_first = 0, int busy_second = 0) {
+                 Half* first, Half* second, int busy_first = 0, int busy_second = 0,
+                 bool split_first = false, Half* first_b = nullptr) {
   const int order = h->tile_order;
   int pf = 0, ps = 0;
   if (h->opt.precision == FLAPW_PREC_EMU) {
@@ -416,11 +437,16 @@ int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int6
     pf = herk_emu_pairs(busy_first);
     ps = herk_emu_pairs(busy_second);
   }
-  if (h->tiles_rows_key != key || h->tiles_order != order || h->tiles_pairs != pf * 1024 + ps) {
+  if (h->tiles_rows_key != key || h->tiles_order != order || h->tiles_pairs != pf * 1024 + ps ||
+      h->tiles_split != split_first) {
     std::vector<EmuTile> emu;
     std::vector<F64Tile> f64;
-    int ids_first = 0, ids_second = 0;
-    make_tiles(probs, 0, n_first, order, pf, &emu, &f64, &ids_first);
+    int ids_first = 0, ids_second = 0, ids_b = 0;
+    make_tiles(probs, 0, n_first, order, pf, &emu, &f64, &ids_first, split_first ? 1 : 0);
+    h->split_emu_b = (int)emu.size();
+    h->split_f64_b = (int)f64.size();
+    if (split_first) make_tiles(probs, 0, n_first, order, pf, &emu, &f64, &ids_b, 2);
+    ids_first = std::max(ids_first, ids_b);
     h->split_emu = (int)emu.size();
     h->split_f64 = (int)f64.size();
     make_tiles(probs, n_first, (int)probs.size(), order, ps, &emu, &f64, &ids_second);
@@ -434,11 +460,18 @@ int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int6
     h->tiles_rows_key = key;
     h->tiles_order = order;
     h->tiles_pairs = pf * 1024 + ps;
+    h->tiles_split = split_first;
   }
   first->emu_t0 = 0;
-  first->emu_nt = h->split_emu;
+  first->emu_nt = h->split_emu_b;
   first->f64_t0 = 0;
-  first->f64_nt = h->split_f64;
+  first->f64_nt = h->split_f64_b;
+  if (first_b) {
+    first_b->emu_t0 = h->split_emu_b;
+    first_b->emu_nt = h->split_emu - h->split_emu_b;
+    first_b->f64_t0 = h->split_f64_b;
+    first_b->f64_nt = h->split_f64 - h->split_f64_b;
+  }
   second->emu_t0 = h->split_emu;
   second->emu_nt = h->n_emu_tiles - h->split_emu;
   second->f64_t0 = h->split_f64;
@@ -926,8 +959,14 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       }
     if (upload(h, h->d_rowprob, rp)) return FLAPW_ERR_CUDA;
   }
-  Half hH, hS;
-  if (int rc = ensure_tiles(h, probs, nk, h->rows, &hH, &hS, 0, n_slots)) return rc;
+  // H to host memory: the H contraction in two launches split by columns, the
+  // first part's columns copied while the second runs (not with the autotuner,
+  // which times whole halves)
+  bool h_host = false;
+  for (int k = 0; k < nk; ++k) h_host = h_host || op.host[k] != nullptr;
+  const bool h_split = h_host && !h->opt.autotune;
+  Half hH, hHb, hS;
+  if (int rc = ensure_tiles(h, probs, nk, h->rows, &hH, &hS, 0, n_slots, h_split, &hHb)) return rc;
   hH.row0 = 0;
   hH.nrows = alg3 ? 2 * h->g_total : h->g_total;
   hS.row0 = s_row0;
@@ -1120,8 +1159,8 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev[4], 0), "cudaStreamWaitEvent");
       for (int i = nk; i < 2 * nk; ++i)
         if (op.host[i])
-          CK(h, copy_out(op.host[i], op.dev[i], h->goff[i - nk + 1] - h->goff[i - nk], layout,
-                         h->copy_stream, h->copy_stream),
+          CK(h, copy_out(op.host[i], op.dev[i], h->goff[i - nk + 1] - h->goff[i - nk], layout, 0,
+                         h->goff[i - nk + 1] - h->goff[i - nk], h->copy_stream),
              "cudaMemcpy2DAsync");
     }
     // join, then H
@@ -1171,14 +1210,27 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     }
     const bool h_presliced = tc_ops && !alg3;
     if (!h_presliced) CK(h, cudaEventRecord(h->ev[10], st), "cudaEventRecord");
-    if (int rc = enqueue_contraction(h, hH, 0, st, 11, 12, h_presliced)) return rc;
-    // H outputs in host memory: split over the caller's stream and the copy stream
-    bool h_host = false;
-    for (int i = 0; i < nk; ++i) h_host = h_host || op.host[i] != nullptr;
+    if (int rc = enqueue_contraction(h, hH, 0, st, 11, h_split ? 18 : 12, h_presliced)) return rc;
+    // H outputs in host memory: with the split, columns [0, c1) go back while
+    // the second part runs, the rest after it
+    auto h_c1 = [&](int k) -> int64_t {
+      const int64_t ng = h->goff[k + 1] - h->goff[k];
+      return h_split ? std::min<int64_t>(ng, 64 * (int64_t)h_split_block((int)ng)) : 0;
+    };
+    if (h_split) {
+      CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev[18], 0), "cudaStreamWaitEvent");
+      for (int k = 0; k < nk; ++k)
+        if (op.host[k])
+          CK(h, copy_out(op.host[k], op.dev[k], h->goff[k + 1] - h->goff[k], layout, 0, h_c1(k),
+                         h->copy_stream),
+             "cudaMemcpy2DAsync");
+      if (int rc = enqueue_contraction(h, hHb, 0, st, -1, 12, true)) return rc;
+    }
     if (h_host) CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev[12], 0), "cudaStreamWaitEvent");
-    for (int i = 0; i < nk; ++i)
-      if (op.host[i])
-        CK(h, copy_out(op.host[i], op.dev[i], h->goff[i + 1] - h->goff[i], layout, st, h->copy_stream),
+    for (int k = 0; k < nk; ++k)
+      if (op.host[k])
+        CK(h, copy_out(op.host[k], op.dev[k], h->goff[k + 1] - h->goff[k], layout, h_c1(k),
+                       h->goff[k + 1] - h->goff[k], h->copy_stream),
            "cudaMemcpy2DAsync");
     if (s_host || h_host) {
       CK(h, cudaEventRecord(h->ev_copy, h->copy_stream), "cudaEventRecord");
