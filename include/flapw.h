@@ -102,7 +102,10 @@ typedef struct flapw_options {
                      FLAPW_OPERANDS_FACTORED; in FP64 on the FP64 path, in
                      double-float FP32 pairs on the emulated path) */
   int h_method;   /* FLAPW_H_FACTORED (default) or FLAPW_H_ALG3 */
-  int reserved[7];
+  int pipeline;   /* emulated contraction's load pipeline: 0 by size (5 stages of one
+                     64-wide K chunk above N_G 8192, else 3 stages of two), 1 the
+                     3-stage shape, 2 the 5-stage shape; results are identical */
+  int reserved[6];
 } flapw_options;
 
 typedef struct flapw_stats {

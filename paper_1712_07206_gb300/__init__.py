@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_slices", ctypes.c_int), ("layout", ctypes.c_int),
                 ("operands", ctypes.c_int), ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("tile_order", ctypes.c_int), ("s_method", ctypes.c_int), ("h_method", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("pipeline", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class Stats(ctypes.Structure):

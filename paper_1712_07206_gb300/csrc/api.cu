@@ -135,6 +135,7 @@ struct flapw_ctx {
   int n_emu_tiles = 0, n_f64_tiles = 0, split_emu = 0, split_f64 = 0, tiles_order = -1;
   int tile_order = 3;            // emulated tile order in use (see make_tiles)
   int default_order = 3;         // the order for this crystal's sizes (default_tile_order)
+  bool deep_pipe = false;        // the contraction's deep pipeline (herk_emu_deep of the largest N_G)
   int64_t tuned_key = -1;        // shape the autotuner last ran on
   int64_t tiles_rows_key = -1;
   int tiles_pairs = -1;          // pair counts the tile lists' last waves were split for
@@ -214,6 +215,7 @@ int check_options(flapw_ctx* h, const flapw_options& o) {
     return fail(h, FLAPW_ERR_ARG, "options.s_method FLAPW_S_LEGENDRE needs FLAPW_OPERANDS_FACTORED");
   if (o.h_method != FLAPW_H_FACTORED && o.h_method != FLAPW_H_ALG3)
     return fail(h, FLAPW_ERR_ARG, "options.h_method is not a FLAPW_H_* value");
+  if (o.pipeline < 0 || o.pipeline > 2) return fail(h, FLAPW_ERR_ARG, "options.pipeline must be in 0..2");
   return FLAPW_OK;
 }
 
@@ -366,6 +368,11 @@ struct Half {
   int emu_t0, emu_nt, f64_t0, f64_nt;
 };
 
+// The contraction's pipeline shape: the option, or by size.
+bool use_deep_pipe(const flapw_ctx* h) {
+  return h->opt.pipeline == 2 || (h->opt.pipeline == 0 && h->deep_pipe);
+}
+
 // Split-tile scratch of the handle; its counts are zeroed on `st` first.
 int split_scratch(flapw_ctx* h, cudaStream_t st, SplitScratch* out) {
   const size_t counts = (size_t)std::max(1, h->split_ids) * 2 * 8 * 4;
@@ -393,7 +400,7 @@ int enqueue_contraction(flapw_ctx* h, const Half& hf, int busy_sms, cudaStream_t
     if (int rc = split_scratch(h, st, &sp)) return rc;
     CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf.emu_t0,
                           hf.emu_nt, h->d_rexp.as<int>(), s, fixed_frac_bits(h->k_terms),
-                          h->d_cnt.as<int>() + 2, busy_sms, sp, st),
+                          h->d_cnt.as<int>() + 2, busy_sms, sp, use_deep_pipe(h), st),
        "emulated contraction launch");
   } else {
     if (ev_sl >= 0) CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
@@ -508,7 +515,7 @@ int autotune_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, in
         if (int rc = split_scratch(h, st, &sp)) return rc;
         CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf->emu_t0,
                               hf->emu_nt, h->d_rexp.as<int>(), s, fixed_frac_bits(h->k_terms),
-                              h->d_cnt.as<int>() + 2, 0, sp, st),
+                              h->d_cnt.as<int>() + 2, 0, sp, use_deep_pipe(h), st),
            "emulated contraction launch");
       }
       CK(h, cudaEventRecord(h->ev[15], st), "cudaEventRecord");
@@ -616,6 +623,7 @@ int flapw_hs_create(const double lattice[9], int n_atoms, const double* pos_frac
   int64_t max_ng = 0;
   for (int k = 0; k < n_k; ++k) max_ng = std::max<int64_t>(max_ng, h->goff[k + 1] - h->goff[k]);
   h->default_order = default_tile_order(max_ng);
+  h->deep_pipe = herk_emu_deep(max_ng);
   if (!(h->opt.tile_order > 0 && !h->opt.autotune)) h->tile_order = h->default_order;
   h->ktau.resize((size_t)n_k * n_atoms);
   for (int k = 0; k < n_k; ++k)
@@ -1321,6 +1329,7 @@ int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const i
   h->rows = N;
   h->k_alloc = k_alloc;
   h->k_terms = K;
+  h->deep_pipe = herk_emu_deep(N);
   if (upload(h, h->d_kmap, kmap) || upload(h, h->d_probs, probs)) return FLAPW_ERR_CUDA;
   std::vector<int> rp(N, 0);
   if (upload(h, h->d_rowprob, rp)) return FLAPW_ERR_CUDA;

@@ -295,13 +295,16 @@ bool make_tmap_4d(CUtensorMap* map, void* base, int64_t k_alloc, int64_t rows, i
 // (host side; call outside stream capture before the first launch).
 cudaError_t herk_emu_init();
 // Launches persistent CTA pairs: min(n_tiles, co-resident pairs - busy_sms),
-// where busy_sms is the number of SMs that concurrent work holds.
+// where busy_sms is the number of SMs that concurrent work holds.  deep: the
+// pipeline of 5 one-chunk stages (large N_G) instead of 3 two-chunk stages.
 cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuTile* tiles,
                             int n_tiles, const int* rexp, int n_slices, int frac, int* err,
-                            int busy_sms, const SplitScratch& split, cudaStream_t st);
+                            int busy_sms, const SplitScratch& split, bool deep, cudaStream_t st);
 // The pair count a launch beside busy_sms busy SMs gets (0 before herk_emu_init).
 int herk_emu_pairs(int busy_sms);
-size_t herk_emu_smem_bytes();
+size_t herk_emu_smem_bytes(bool deep);
+// The pipeline for problems of at most max_ng plane waves: deep above 8192.
+inline bool herk_emu_deep(int64_t max_ng) { return max_ng > 8192; }
 
 // ---- host G enumeration ----------------------------------------------------
 int enumerate_g(const double lat[9], const double k[3], double kmax, std::vector<int>* n3);

@@ -63,14 +63,26 @@ namespace {
 
 using namespace tc;
 
-constexpr int kStages = 3;
 constexpr int kThreads = 320;
-constexpr int kStageChunks = 2;                          // 64-wide K chunks per stage
 constexpr uint32_t kTileA = 128 * 128;                   // A: 128 rows x 128 B, one chunk
 constexpr uint32_t kTileB = 128 * 128;                   // this CTA's B half: <= 128 rows
-constexpr uint32_t kOffB = kStageChunks * kTileA;        // B after both A chunks
-constexpr uint32_t kStageBytes = kStageChunks * (kTileA + kTileB);
 constexpr uint32_t kTmemCols = 512;
+// Two pipeline shapes, both about 192 KB of shared memory: 3 stages of two
+// 64-wide K chunks (fewer stage hand-offs per MMA) and 5 stages of one chunk
+// (more loads in flight to hide DRAM latency when the operand rows of the
+// concurrent tiles outgrow L2).  Config 2 (N_G 3990): 6.06 against 6.48 ms;
+// config 3 (N_G 11996): 314.8 against 303.2 ms.
+template <int STAGES, int CHUNKS>
+struct Pipe {
+  static constexpr int kStages = STAGES;
+  static constexpr int kStageChunks = CHUNKS;                       // 64-wide K chunks per stage
+  static constexpr uint32_t kOffB = CHUNKS * kTileA;               // B after the A chunks
+  static constexpr uint32_t kStageBytes = CHUNKS * (kTileA + kTileB);
+  static constexpr size_t kSmemBytes = (size_t)STAGES * kStageBytes + 1024 + 256;
+  static_assert(2 * STAGES + 5 <= 16, "the mbarriers share 128 bytes before the TMEM slot");
+};
+using PipeShallow = Pipe<3, 2>;
+using PipeDeep = Pipe<5, 1>;
 constexpr int kMaxS = 8;
 // longest K sub-span of a pass: 48 chunks (3072 terms <= 2^12, exact) let a
 // 2592-term reduction take one sub-span per group; 32 cost config 2 1.2 %
@@ -229,10 +241,15 @@ struct Sched {
   }
 };
 
+template <class PP>
 __global__ void __launch_bounds__(kThreads, 1)
     herk_emu_kernel(const __grid_constant__ SliceMaps maps, const Prob* __restrict__ probs,
                     const EmuTile* __restrict__ tiles, int n_tiles, const int* __restrict__ rexp,
                     int n_slices, int frac, int* __restrict__ err, SplitScratch split) {
+  constexpr int kStages = PP::kStages;
+  constexpr int kStageChunks = PP::kStageChunks;
+  constexpr uint32_t kOffB = PP::kOffB;
+  constexpr uint32_t kStageBytes = PP::kStageBytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
@@ -490,7 +507,7 @@ DevState g_state[kMaxDevices];
 
 }  // namespace
 
-size_t herk_emu_smem_bytes() { return kStages * kStageBytes + 1024 + 256; }
+size_t herk_emu_smem_bytes(bool deep) { return deep ? PipeDeep::kSmemBytes : PipeShallow::kSmemBytes; }
 
 // partial sums: [id][cta][drain warp][part][64][32] int64; counts: [id][cta][drain warp]
 size_t split_scratch_bytes(int n_ids) {
@@ -511,8 +528,12 @@ cudaError_t herk_emu_init() {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_state_mutex);
   if (g_state[dev].ready) return cudaSuccess;
-  const size_t smem = herk_emu_smem_bytes();
-  e = cudaFuncSetAttribute(herk_emu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = PipeShallow::kSmemBytes;
+  e = cudaFuncSetAttribute(herk_emu_kernel<PipeShallow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(herk_emu_kernel<PipeDeep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)PipeDeep::kSmemBytes);
   if (e != cudaSuccess) return e;
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -528,11 +549,14 @@ cudaError_t herk_emu_init() {
   cfg.dynamicSmemBytes = smem;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  int n = 0;
-  e = cudaOccupancyMaxActiveClusters(&n, herk_emu_kernel, &cfg);
+  int n = 0, nd = 0;
+  e = cudaOccupancyMaxActiveClusters(&n, herk_emu_kernel<PipeShallow>, &cfg);
   if (e != cudaSuccess) return e;
-  if (n < 1) return cudaErrorInvalidConfiguration;
-  g_state[dev].max_pairs = n;
+  cfg.dynamicSmemBytes = PipeDeep::kSmemBytes;
+  e = cudaOccupancyMaxActiveClusters(&nd, herk_emu_kernel<PipeDeep>, &cfg);
+  if (e != cudaSuccess) return e;
+  if (n < 1 || nd < 1) return cudaErrorInvalidConfiguration;
+  g_state[dev].max_pairs = std::min(n, nd);  // one pair per 2 SMs in both shapes
   g_state[dev].ready = true;
   return cudaSuccess;
 }
@@ -545,7 +569,7 @@ int herk_emu_pairs(int busy_sms) {
 
 cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuTile* tiles,
                             int n_tiles, const int* rexp, int n_slices, int frac, int* err,
-                            int busy_sms, const SplitScratch& split, cudaStream_t st) {
+                            int busy_sms, const SplitScratch& split, bool deep, cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   if (n_slices < 1 || n_slices > kMaxS || frac < 40 || frac > 50) return cudaErrorInvalidValue;
   cudaError_t e = herk_emu_init();
@@ -565,12 +589,16 @@ cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuT
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(2 * pairs);
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = herk_emu_smem_bytes();
+  cfg.dynamicSmemBytes = herk_emu_smem_bytes(deep);
   cfg.stream = st;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, herk_emu_kernel, maps, probs, tiles, n_tiles, rexp, n_slices, frac, err,
-                         split);
+  if (deep)
+    e = cudaLaunchKernelEx(&cfg, herk_emu_kernel<PipeDeep>, maps, probs, tiles, n_tiles, rexp, n_slices,
+                           frac, err, split);
+  else
+    e = cudaLaunchKernelEx(&cfg, herk_emu_kernel<PipeShallow>, maps, probs, tiles, n_tiles, rexp,
+                           n_slices, frac, err, split);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -78,6 +78,13 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
     bad = fl.default_options(n_slices=3)
     with pytest.raises(fl.FlapwError):
         fl.hs_create(p.lattice, p.pos_frac, p.atom_type, p.mt_radius, 4, p.k_frac, p.kmax, bad)
+    # option values outside their ranges are rejected before any device work
+    for kw in (dict(pipeline=3), dict(h_method=2), dict(s_method=2), dict(tile_order=8),
+               dict(operands=fl.OPERANDS_FROM_AB, s_method=fl.S_LEGENDRE)):
+        with pytest.raises(fl.FlapwError) as e:
+            fl.hs_create(p.lattice, p.pos_frac, p.atom_type, p.mt_radius, 4, p.k_frac, p.kmax,
+                         fl.default_options(**kw))
+        assert e.value.code == -1, kw
 
 
 def test_structs_match_header_layout(tmp_path):

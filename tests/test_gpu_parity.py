@@ -204,9 +204,11 @@ def test_herk_integer_data_bit_exact(K):
 # ------------------------------------------------ larger configs, sampled
 
 @pytest.mark.parametrize("precision,tol", [(fl.PREC_FP64, TOL_F64), (fl.PREC_EMU, TOL_EMU)])
-def test_hs_config2_sampled_columns(precision, tol):
+@pytest.mark.parametrize("operands", [fl.OPERANDS_FROM_AB, fl.OPERANDS_FACTORED])
+def test_hs_config2_sampled_columns(precision, tol, operands):
+    # the factored emulated case is the configuration bench.py times
     p = inputs.config2()
-    h, Hs, Ss, _ = run_hs(p, precision)
+    h, Hs, Ss, _ = run_hs(p, precision, operands=operands)
     n3 = h.gvectors(0)
     ng = len(n3)
     cols = [0, 1, 63, 64, 127, 128, 1000, 2047, ng - 65, ng - 1]
@@ -249,6 +251,26 @@ def test_every_tile_order(order):
         ng = Ho.shape[0]
         assert herm_relerr(lower_to_full(Hs[k], ng, 0), Ho) <= TOL_EMU, (order, k)
         assert herm_relerr(lower_to_full(Ss[k], ng, 0), So) <= TOL_EMU, (order, k)
+
+
+@pytest.mark.parametrize("h_method", [fl.H_FACTORED, fl.H_ALG3])
+def test_pipeline_shapes_identical(h_method):
+    # the 3-stage and the 5-stage load pipelines run the same MMAs and drains:
+    # bit-identical H and S (the 5-stage one is the default above N_G 8192)
+    p = inputs.small(23, n_atoms=3, n_types=2, lmax=5, n_target=(1500, 333))
+    h, H1, S1, AB = run_hs(p, fl.PREC_EMU, operands=fl.OPERANDS_FACTORED, h_method=h_method,
+                           pipeline=1)
+    H1 = [x.clone() for x in H1]
+    S1 = [x.clone() for x in S1]
+    _, H2, S2, _ = run_hs(p, fl.PREC_EMU, operands=fl.OPERANDS_FACTORED, h_method=h_method,
+                          pipeline=2, h=h, AB=AB)
+    for k in range(p.n_k):
+        ng = h.num_g(k)
+        assert np.array_equal(lower_to_full(H1[k], ng, 0), lower_to_full(H2[k], ng, 0)), k
+        assert np.array_equal(lower_to_full(S1[k], ng, 0), lower_to_full(S2[k], ng, 0)), k
+        Ho, So = oracle_hs(p, k)
+        assert herm_relerr(lower_to_full(H2[k], ng, 0), Ho) <= TOL_EMU
+        assert herm_relerr(lower_to_full(S2[k], ng, 0), So) <= TOL_EMU
 
 
 @pytest.mark.parametrize("precision", [fl.PREC_FP64, fl.PREC_EMU])
