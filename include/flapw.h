@@ -92,7 +92,7 @@ typedef struct flapw_options {
                     arguments repeat (default 0) */
   int autotune;  /* 1: time the contraction's tile-order variants once per shape and
                     keep the fastest (default 0: fixed choice) */
-  int tile_order; /* 0: library default (bands of 8 row blocks for N_G <= 8192,
+  int tile_order; /* 0: library default (bands of 8 row blocks for N_G <= 16384,
                      else bands of 2); k+1 forces tile order k of the emulated
                      contraction (0 row-major, 1 column-major, 2/3/4/5 bands of
                      4/2/8/3 row blocks of 256, 6 bands of 2 with alternating

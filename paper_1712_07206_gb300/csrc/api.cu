@@ -487,11 +487,12 @@ int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int6
 }
 
 // Library default tile order for the largest N_G: bands of 8 row blocks for
-// N_G <= 8192, else bands of 2.  Measured on the contraction (GB300): N_G 3990
-// bands of 8 / 4 / 2: 6.03 / 6.04 / 6.12 ms; N_G 11996: 363 / 326 / 320 ms;
-// N_G 23993: 4584 / 4153 / 3739 ms.  Larger problems need the operand rows
-// of the concurrently running tiles to overlap more in L2.
-int default_tile_order(int64_t max_ng) { return max_ng <= 8192 ? 4 : 3; }
+// N_G <= 16384, else bands of 2.  Measured on the contraction (GB300), bands of
+// 8 / 2: N_G 3990 (3-stage pipeline) 6.03 / 6.12 ms; N_G 11996 (5-stage)
+// 299.7 / 307.9 ms; N_G 23993 (5-stage) 4256 / 3556 ms: the largest problems
+// need the operand rows of the concurrently running tiles to overlap more in
+// L2 than a band of 8 row blocks allows.
+int default_tile_order(int64_t max_ng) { return max_ng <= 16384 ? 4 : 3; }
 
 // Times the emulated contraction under every tile order on the slices the
 // last build left in place (the outputs are rewritten with the same values)
