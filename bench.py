@@ -393,7 +393,16 @@ def cpu_baseline(p, h, H, S, layout, ngs, args, H64=None, S64=None):
     n3 = h.gvectors(0)
     ng = ngs[0]
     rng = np.random.default_rng(0)
-    cols = np.unique(np.concatenate([[0, ng - 1], rng.integers(0, ng, size=args.cpu_cols - 2)]))
+    n_cols = args.cpu_cols
+    if n_cols <= 0:
+        # a bounded sample of about --cpu-seconds of oracle work, sized on 32
+        # columns after a warm-up call (thread start-up)
+        oracle.hs_columns(p, 0, n3, np.arange(min(4, ng)))
+        t0 = time.perf_counter()
+        oracle.hs_columns(p, 0, n3, np.arange(min(32, ng)))
+        per_col = (time.perf_counter() - t0) / min(32, ng)
+        n_cols = int(min(ng, max(16, args.cpu_seconds / max(per_col, 1e-9))))
+    cols = np.unique(np.concatenate([[0, ng - 1], rng.integers(0, ng, size=max(0, n_cols - 2))]))
     t0 = time.perf_counter()
     Ho, So = oracle.hs_columns(p, 0, n3, cols)
     dt = time.perf_counter() - t0
@@ -465,7 +474,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-cols", type=int, default=48)
+    ap.add_argument("--cpu-cols", type=int, default=0,
+                    help="oracle columns of the CPU baseline (0: as many as --cpu-seconds allow)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--refined-cols", type=int, default=1024,
                     help="columns of the host-BLAS Alg. 3 comparator")
     ap.add_argument("--h-method", choices=["factored", "alg3"], default="factored",
