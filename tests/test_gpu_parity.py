@@ -316,13 +316,15 @@ def test_host_buffers_through_the_abi():
 
 
 @pytest.mark.parametrize("layout", [fl.LAYOUT_LOWER_FULL, fl.LAYOUT_LOWER_PACKED])
-def test_host_outputs_every_lower_element_copied(layout):
+@pytest.mark.parametrize("precision,tol", [(fl.PREC_EMU, TOL_EMU), (fl.PREC_FP64, TOL_F64)])
+def test_host_outputs_every_lower_element_copied(layout, precision, tol):
     # pinned host outputs filled with NaN: the block-wise copy of the lower
     # triangle must reach every lower element of every k-point (ragged N_G,
-    # one N_G above 64 x 32 so that the column blocks are wider than 64)
+    # one N_G above 64 x 32 so that the column blocks are wider than 64), with
+    # H contracted in two launches split by column (both precisions)
     torch = torch_cuda()
     p = inputs.small(88, n_atoms=3, n_types=2, lmax=3, n_target=(2100, 150, 65))
-    h = fl.from_problem(p, fl.default_options(precision=fl.PREC_EMU, layout=layout,
+    h = fl.from_problem(p, fl.default_options(precision=precision, layout=layout,
                                               operands=fl.OPERANDS_FACTORED))
     _, A, B = run_ab(p, h)
     Hs, Ss = [], []
@@ -336,8 +338,8 @@ def test_host_outputs_every_lower_element_copied(layout):
     for k in range(p.n_k):
         Ho, So = oracle_hs(p, k)
         ng = Ho.shape[0]
-        assert herm_relerr(lower_to_full(Hs[k], ng, layout), Ho) <= TOL_EMU, k
-        assert herm_relerr(lower_to_full(Ss[k], ng, layout), So) <= TOL_EMU, k
+        assert herm_relerr(lower_to_full(Hs[k], ng, layout), Ho) <= tol, k
+        assert herm_relerr(lower_to_full(Ss[k], ng, layout), So) <= tol, k
 
 
 def test_bad_calls_return_codes_not_faults():
