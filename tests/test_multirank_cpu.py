@@ -1,7 +1,7 @@
 """The benchmark's multi-rank logic on CPU: the max-over-ranks timing
 reduction with two gloo ranks, and the reference arm under torchrun with two
 ranks (rank 0 alone runs the oracle and prints one line, both exit 0).
-Every GPU run of this build uses one GPU; these cover the N > 1 host paths."""
+They cover the host paths of N > 1 ranks without any GPU."""
 import json
 import os
 import socket
