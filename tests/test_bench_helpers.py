@@ -56,3 +56,59 @@ def test_peaks_and_traffic_table(bench):
     for (name, slices, s_method, h_method), v in bench.MEASURED_TRAFFIC.items():
         assert 4 <= slices <= 8 and s_method in ("contraction", "legendre")
         assert h_method in ("factored", "alg3") and v > 0
+
+
+class _Handle:
+    """Stand-in for the library handle: only the plane-wave list is read."""
+
+    def __init__(self, n3):
+        self.n3 = n3
+
+    def gvectors(self, k):
+        return self.n3
+
+
+def _lower(X, layout, fl):
+    """Lower triangle of a full Hermitian matrix in the library's host layouts."""
+    import numpy as np
+    ng = X.shape[0]
+    if layout == fl.LAYOUT_LOWER_PACKED:
+        return np.concatenate([X[j:, j] for j in range(ng)])
+    return X.T.reshape(-1).copy()  # column j holds rows 0..ng-1
+
+
+@pytest.mark.parametrize("layout_name", ["LAYOUT_LOWER_FULL", "LAYOUT_LOWER_PACKED"])
+def test_cpu_baseline_calibrates_and_measures_parity(bench, layout_name):
+    """The CPU baseline sizes its sample from a timed warm-up (cpu_cols 0),
+    always samples the first and last column, and its relative errors are
+    zero for exact results and large for a planted error."""
+    import numpy as np
+    import oracle
+    import paper_1712_07206_gb300 as fl
+    from paper_1712_07206_gb300 import inputs
+
+    layout = getattr(fl, layout_name)
+    p = inputs.CONFIGS[1]()
+    oracle.build()
+    n3 = oracle.gvectors(p.lattice, p.k_frac[0], p.kmax[0])
+    ng = len(n3)
+    Hf, Sf = oracle.hs_full(p, 0, n3)
+    H, S = [_lower(Hf, layout, fl)], [_lower(Sf, layout, fl)]
+
+    class A:
+        cpu_cols, cpu_seconds = 0, 0.05
+
+    out = bench.cpu_baseline(p, _Handle(n3), H, S, layout, [ng], A, H64=H, S64=S)
+    n = int(out["sample"].split()[0])
+    assert 16 <= n <= ng and out["sample"].endswith(" s")
+    assert out["kind"] == "oracle" and out["cores"] >= 1 and out["value"] > 0
+    for key in ("parity_rel_err", "parity_rel_err_fp64_path"):
+        assert out[key]["H"] < 1e-15 and out[key]["S"] < 1e-15
+
+    A.cpu_cols = 20
+    Hbad = [H[0].copy()]
+    Hbad[0][0] += 1.0  # H(0,0), in column 0, which every sample holds
+    out = bench.cpu_baseline(p, _Handle(n3), Hbad, S, layout, [ng], A)
+    assert int(out["sample"].split()[0]) <= 20
+    assert out["parity_rel_err"]["H"] > 1e-6 and out["parity_rel_err"]["S"] < 1e-15
+    assert "parity_rel_err_fp64_path" not in out
