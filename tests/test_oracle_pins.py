@@ -199,10 +199,8 @@ def test_gvector_set_is_the_kmax_ball():
 
 # ------------------------------------------------------------- H and S
 
-def test_brute_force_quadruple_sum():
+def brute_force_hs(p, n3):
     """Eqs. (def_overlap), (def_hamilton) as literal loops over G', G, a, L', L."""
-    p = inputs.small(13, n_atoms=2, n_types=2, lmax=2, n_target=(24,))
-    n3 = oracle.gvectors(p.lattice, p.k_frac[0], p.kmax[0])
     ng, nl = len(n3), p.n_L
     assert ng <= 40
     A, B = ab_scipy(p, 0, n3)
@@ -223,6 +221,30 @@ def test_brute_force_quadruple_sum():
                         h += np.conj(B[a, Lp, gp]) * T[nl + Lp, L] * A[a, L, g]
                         h += np.conj(B[a, Lp, gp]) * T[nl + Lp, nl + L] * B[a, L, g]
             H[gp, g], S[gp, g] = h, s
+    return H, S
+
+
+def test_brute_force_quadruple_sum():
+    p = inputs.small(13, n_atoms=2, n_types=2, lmax=2, n_target=(24,))
+    n3 = oracle.gvectors(p.lattice, p.k_frac[0], p.kmax[0])
+    H, S = brute_force_hs(p, n3)
+    Ho, So = oracle.hs_full(p, 0, n3)
+    assert relerr(Ho, H) < 1e-13
+    assert relerr(So, S) < 1e-13
+
+
+def test_gamma_point_with_the_k0_plane_wave():
+    """k = 0: the plane wave G = 0 has K = 0, where K_hat is undefined and only
+    l = 0 survives (j_l(0) = 0 for l >= 1, K j_l'(K R) = 0); the oracle agrees
+    with the brute-force sums there, and its G = 0 row of A, B is zero for l >= 1."""
+    p = inputs.small(29, n_atoms=2, n_types=2, lmax=2, n_target=(24,))
+    p.k_frac = np.zeros_like(p.k_frac)
+    n3 = oracle.gvectors(p.lattice, p.k_frac[0], p.kmax[0])
+    assert np.array_equal(n3[0], [0, 0, 0])
+    A, B = oracle.build_ab(p, 0, n3)
+    assert np.all(A[:, 1:, 0] == 0) and np.all(B[:, 1:, 0] == 0)
+    assert np.all(A[:, 0, 0] != 0)
+    H, S = brute_force_hs(p, n3)
     Ho, So = oracle.hs_full(p, 0, n3)
     assert relerr(Ho, H) < 1e-13
     assert relerr(So, S) < 1e-13
