@@ -29,7 +29,8 @@
  * records a message readable with flapw_last_error(handle) (or with a NULL
  * handle for calls that have none).  Work is enqueued asynchronously on the
  * given CUDA stream; errors detected on the device (a bounded wait that ran
- * out) are reported by flapw_sync().  A handle is not thread-safe.
+ * out, a singular 2x2 pivot of a T block) are reported by flapw_sync().  A
+ * handle is not thread-safe.
  */
 #ifndef FLAPW_H
 #define FLAPW_H
@@ -204,8 +205,11 @@ int flapw_build_AB(flapw_handle h, const double* radial, void* A, void* B, void*
  * lower-triangle rank-K contraction each, K = 2 N_A N_L (Fig. agg stacking).
  * With options.h_method = FLAPW_H_ALG3 H is formed without the factorisation
  * as described at FLAPW_H_ALG3.
- * Errors: FLAPW_ERR_FACTOR if a block is singular in a way the pivoting
- * cannot handle; FLAPW_ERR_OOM if the workspaces do not fit. */
+ * A zero 1x1 pivot (a column that is zero on and below the diagonal after
+ * the previous steps) contributes nothing and its row is dropped from Z.
+ * Errors: FLAPW_ERR_OOM if the workspaces do not fit (returned here); a
+ * 2x2 pivot with a zero determinant is found on the device and reported by
+ * the next flapw_sync() as FLAPW_ERR_FACTOR. */
 int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom_slot,
                    const double* U, const void* A, const void* B, void* const* H,
                    void* const* S, void* stream);
