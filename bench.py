@@ -459,13 +459,20 @@ def run_reference(args):
     }), flush=True)
 
 
+def inputs_configs():
+    """Workload number -> what it is (the input generator's description)."""
+    from paper_1712_07206_gb300 import inputs
+    return {c: (f.__doc__ or "").strip().rstrip(".") for c, f in inputs.CONFIGS.items()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", type=int, default=2, choices=sorted(inputs_configs()),
+                    help="workload: " + "; ".join(f"{c}: {d}" for c, d in sorted(inputs_configs().items())))
     ap.add_argument("--operands", choices=["factored", "from_ab"], default="factored")
     ap.add_argument("--slices", type=int, default=7)
     ap.add_argument("--tile-order", type=int, default=0,
