@@ -20,7 +20,8 @@ __all__ = ["FlapwError", "Options", "Stats", "Handle", "load", "library_path", "
            "default_options", "enumerate_g", "hs_create", "engine_create", "herk_noalloc",
            "declared_symbols",
            "PREC_FP64", "PREC_EMU", "LAYOUT_LOWER_FULL", "LAYOUT_LOWER_PACKED",
-           "OPERANDS_FROM_AB", "OPERANDS_FACTORED"]
+           "OPERANDS_FROM_AB", "OPERANDS_FACTORED", "S_CONTRACTION", "S_LEGENDRE",
+           "H_FACTORED", "H_ALG3"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _HEADER = os.path.join(os.path.dirname(_HERE), "include", "flapw.h")
