@@ -64,6 +64,37 @@ def test_enumerate_g_errors():
     assert b"NULL" in lib.flapw_last_error(None)
 
 
+def test_enumerate_g_writes_at_most_max_g():
+    """The count is always the full one; only the first max_g triples are written."""
+    lib = fl.load()
+    lat = np.ascontiguousarray(np.eye(3) * 7.0)
+    k = np.array([0.1, 0.2, 0.3])
+    full = fl.enumerate_g(lat, k, 3.1)
+    assert len(full) > 10
+    buf = np.full((len(full), 3), -99, dtype=np.int32)
+    n = ctypes.c_int()
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.flapw_enumerate_g(dp(lat), dp(k), 3.1, 5, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                 ctypes.byref(n)) == 0
+    assert n.value == len(full)
+    assert np.array_equal(buf[:5], full[:5]) and np.all(buf[5:] == -99)
+
+
+def test_herk_noalloc_rejects_bad_arguments_before_touching_the_device():
+    """Argument checks that come before any CUDA call (the pointers are never
+    dereferenced: each case fails first)."""
+    lib = fl.load()
+    Z = H = 4096
+    good = dict(Z=Z, ldz=8, K=8, N=4, sigma=None, H=H, ldh=4, layout=fl.LAYOUT_LOWER_FULL, n_slices=0)
+    bad = [dict(Z=None), dict(H=None), dict(K=0), dict(N=0), dict(ldz=7),
+           dict(layout=2), dict(ldh=3), dict(n_slices=3), dict(n_slices=9)]
+    for change in bad:
+        a = dict(good, **change)
+        rc = lib.flapw_herk_noalloc(a["Z"], a["ldz"], a["K"], a["N"], a["sigma"], a["H"], a["ldh"],
+                                    a["layout"], a["n_slices"], None)
+        assert rc == -1, change
+
+
 def test_create_rejects_bad_arguments_before_touching_the_device():
     p = inputs.config1()
     with pytest.raises(fl.FlapwError) as e:
