@@ -144,7 +144,7 @@ void flapw_default_options(flapw_options* opt);
 int flapw_enumerate_g(const double lattice[9], const double k_frac[3], double kmax, int max_g,
                       int* n3, int* n_g);
 
-/* Creates a handle for one crystal (Sec. 2; sizes as in Sec. 3, "typical values").
+/* Creates a handle for one crystal (Sec. 2; the paper's matrix sizes are those of Sec. 3).
  *   n_atoms, pos_frac[n_atoms*3]  fractional atom positions (copied)
  *   atom_type[n_atoms]            type index in [0, n_types) (copied)
  *   mt_radius[n_types]            muffin-tin radius per type, > 0
