@@ -27,10 +27,10 @@
  *
  * Errors: every call returns FLAPW_OK (0) or a negative FLAPW_ERR_* code and
  * records a message readable with flapw_last_error(handle) (or with a NULL
- * handle for calls that have none).  Work is enqueued asynchronously on the
- * given CUDA stream; errors detected on the device (a bounded wait that ran
- * out, a singular 2x2 pivot of a T block) are reported by flapw_sync().  A
- * handle is not thread-safe.
+ * handle for calls that have none: the calling thread's last such message).
+ * Work is enqueued asynchronously on the given CUDA stream; errors detected
+ * on the device (a bounded wait that ran out, a singular 2x2 pivot of a T
+ * block) are reported by flapw_sync().  A handle is not thread-safe.
  */
 #ifndef FLAPW_H
 #define FLAPW_H
@@ -258,7 +258,8 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st);
  * FLAPW_H_ALG3 (no factorisation). */
 int flapw_get_factor(flapw_handle h, int slot, double* CH, int* n_pos, int* n_neg);
 
-/* Message for the last error on h (or of the last handle-less call if h is NULL). */
+/* Message for the last error on h (or of the calling thread's last handle-less call
+ * if h is NULL). */
 const char* flapw_last_error(flapw_handle h);
 
 /* Releases the handle and every device workspace it owns. */

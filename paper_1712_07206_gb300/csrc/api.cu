@@ -16,7 +16,7 @@ using namespace flapw;
 
 namespace {
 
-std::string g_last_error;  // errors of calls without a handle
+thread_local std::string g_last_error;  // errors of calls without a handle, per thread
 constexpr int kNumTileOrders = 7;  // emulated tile orders, see make_tiles
 
 // Device buffer that grows on demand.

@@ -80,6 +80,37 @@ def test_enumerate_g_writes_at_most_max_g():
     assert np.array_equal(buf[:5], full[:5]) and np.all(buf[5:] == -99)
 
 
+def test_handleless_errors_are_per_thread():
+    """Each thread reads the message of its own last handle-less call."""
+    import threading
+    lib = fl.load()
+    lat = np.ascontiguousarray(np.zeros(9))
+    k = np.zeros(3)
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    go = threading.Barrier(2)
+    seen = {}
+
+    def null_args():
+        assert lib.flapw_enumerate_g(None, None, 1.0, 0, None, None) == -1
+        go.wait()
+        go.wait()
+        seen["null"] = lib.flapw_last_error(None)
+
+    def singular():
+        go.wait()
+        n = ctypes.c_int()
+        assert lib.flapw_enumerate_g(dp(lat), dp(k), 1.0, 0, None, ctypes.byref(n)) == -1
+        go.wait()
+        seen["singular"] = lib.flapw_last_error(None)
+
+    threads = [threading.Thread(target=f) for f in (null_args, singular)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert b"NULL" in seen["null"] and b"singular" in seen["singular"], seen
+
+
 def test_herk_noalloc_rejects_bad_arguments_before_touching_the_device():
     """Argument checks that come before any CUDA call (the pointers are never
     dereferenced: each case fails first)."""
