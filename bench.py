@@ -55,12 +55,76 @@ def max_over_ranks(x: float) -> float:
 
 
 # DRAM bytes (read + write) per herk_emu_kernel launch, mean of the S and the
-# H launch of one step, from an ncu --set full capture of the current kernel
-# (profiles/herk_emu_c2_ortho16_l8_ng3990_full.md); keyed by workload, slices,
-# S method and H method.  Other shapes report null.
+# H launch of one step, from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum; profiles/herk_emu_*), keyed by workload, slices, S
+# method, H method, tile cover, tile order and load pipeline, with the hash of
+# the kernel sources it was taken on (kernel_source_hash).  A capture of other
+# sources, or of another shape or configuration, reports null.
 MEASURED_TRAFFIC = {
-    ("c2_ortho_16at_l8_ng4000", 7, "contraction", "factored"): 2.4109e9,
+    ("c2_ortho_16at_l8_ng4000", 7, "contraction", "factored", 1, 0, 1):
+        {"bytes": 2.2001e9, "kernel_sha": "5eec19f62de98072"},
 }
+
+KERNEL_SOURCES = ("herk_emu.cu", "tc_common.cuh", "tiles.cuh", "fixed64.cuh")
+
+
+def kernel_source_hash():
+    """First 16 hex digits of the SHA-256 of the emulated contraction's sources
+    (the kernel, its device helpers and the tile cover that orders its work)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1712_07206_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload, slices, s_method, h_method, cover, order, pipeline):
+    rec = MEASURED_TRAFFIC.get((workload, slices, s_method, h_method, cover, order, pipeline))
+    if rec and rec["kernel_sha"] == kernel_source_hash():
+        return rec["bytes"]
+    return None
+
+
+def fp64_peak_tflops():
+    """Measured FP64 peak of this GPU: best of 5 cuBLAS DGEMMs (torch.matmul,
+    float64, 4096^3, 2 N^3 flops each), CUDA events on the current stream."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = torch.empty_like(a)
+    torch.matmul(a, b, out=c)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b, c
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def columns_from_lower(x, ng, layout, cols):
+    """Full columns cols[c] of a Hermitian matrix given as the library's lower
+    triangle (full layout, ld = ng, or LAPACK packed), as [len(cols)][ng]."""
+    x = x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+    packed = layout == 1
+    out = np.zeros((len(cols), ng), complex)
+    i = np.arange(ng)
+    for c, g in enumerate(cols):
+        lo = i >= g
+        hi = i[~lo]
+        if packed:
+            out[c, lo] = x[g * ng - g * (g - 1) // 2 + (i[lo] - g)]
+            out[c, ~lo] = np.conj(x[hi * ng - hi * (hi - 1) // 2 + (g - hi)])
+        else:
+            out[c, lo] = x[g * ng + i[lo]]
+            out[c, ~lo] = np.conj(x[hi * ng + g])
+    return out
 
 
 def peaks():
@@ -147,7 +211,8 @@ def run_ours(args):
     operands = fl.OPERANDS_FACTORED if args.operands == "factored" else fl.OPERANDS_FROM_AB
     layout = fl.LAYOUT_LOWER_PACKED if p.layout == "packed" else fl.LAYOUT_LOWER_FULL
     opt = fl.default_options(precision=fl.PREC_EMU, layout=layout, operands=operands, n_slices=args.slices,
-                             tile_order=args.tile_order, use_graph=1 if args.graph else 0,
+                             tile_order=args.tile_order, pipeline=args.pipeline, tile_cover=args.cover,
+                             autotune=1 if args.autotune else 0, use_graph=1 if args.graph else 0,
                              s_method=fl.S_LEGENDRE if args.s_method == "legendre" else fl.S_CONTRACTION,
                              h_method=fl.H_ALG3 if args.h_method == "alg3" else fl.H_FACTORED)
     h = fl.from_problem(p, opt)
@@ -227,7 +292,7 @@ def run_ours(args):
         h.set_options(fl.default_options(precision=fl.PREC_FP64, layout=layout, operands=operands,
                                          use_graph=1 if args.graph else 0, s_method=opt.s_method,
                                          h_method=opt.h_method))
-        f_ms = []
+        f_ms, f_kms = [], []
         for i in range(args.fp64_steps + 1):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -238,7 +303,11 @@ def run_ours(args):
             torch.cuda.synchronize()
             if i > 0:
                 f_ms.append(e0.elapsed_time(e1))
+                h.sync()
+                f_kms.append(h.stats()["ms_contract"])
         f64_ms = float(np.mean(f_ms))
+        f64_kms = float(np.mean(f_kms))
+        fp64_peak = fp64_peak_tflops()
         h.set_options(opt)
     # end-to-end through the C ABI: the step's inputs (radial data, T, U, slots)
     # from host memory and its results H and S into pinned host buffers, copies
@@ -277,21 +346,41 @@ def run_ours(args):
                    "layout": p.layout, "l2": "256 MB L2 flush between steps; A/B 166 MB and operands exceed L2",
                    "flops_per_step": flops, "graph_replay": bool(args.graph), "s_method": args.s_method,
                    "h_method": args.h_method,
+                   # the contraction's tile cover (1 cyclic, 2 aligned), tile order and
+                   # load pipeline (1: 3 stages of two K chunks, 2: 5 of one) in use,
+                   # chosen by the library's autotuner unless forced
+                   "autotune": bool(args.autotune), "tile_cover": st["tile_cover"],
+                   "tile_order": st["tile_order"], "pipeline": st["pipeline"],
                    "parallelism": f"replicas{ws}"},
         "fp64_path": None if f64_ms is None else {
             "value": round(flops / (f64_ms * 1e-3) / 1e12 * ws, 4), "unit": "TFLOP/s",
-            "ms_per_step": round(f64_ms, 3), "steps": args.fp64_steps},
+            "ms_per_step": round(f64_ms, 3), "steps": args.fp64_steps,
+            # the FP64 contraction kernel (DMMA) against the GPU's measured FP64
+            # peak: cuBLAS DGEMM on the same device, in the same run
+            "roofline": {"bound": "fp64", "kernel": "herk_f64_kernel (S and H launches)",
+                         "kernel_ms": round(f64_kms, 3),
+                         "achieved": round(flops / (f64_kms * 1e-3) / 1e12, 4),
+                         "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                         "frac": round(flops / (f64_kms * 1e-3) / 1e12 / fp64_peak, 4),
+                         "peak_source": "measured in this run: best of 5 cuBLAS DGEMM 4096^3 "
+                                        "(torch.matmul float64)"}},
         "speedup_emu_vs_fp64": None if f64_ms is None else round(f64_ms / ms, 2),
         "stages_ms": stage,
-        "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak,
-                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+        # achieved: the slice-product work the method needs (s(s+1)/2 pairs x
+        # 4 K N_G^2 per matrix, no tile or K padding) per kernel second;
+        # achieved_executed counts the MMAs the kernel issues
+        "roofline": {"bound": "tensor", "achieved": round(achieved_alg, 2), "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(achieved_alg / peak, 4),
+                     "achieved_executed": round(achieved, 2),
+                     "frac_executed": round(achieved / peak, 4),
                      "traffic": args.traffic if args.traffic is not None else
-                     MEASURED_TRAFFIC.get((p.name, args.slices, args.s_method, args.h_method)),
+                     measured_traffic(p.name, args.slices, args.s_method, args.h_method,
+                                      st["tile_cover"], st["tile_order"], st["pipeline"]),
+                     "kernel_source_hash": kernel_source_hash(),
                      "kernel": "herk_emu_kernel (" + ("H launch; S by the addition theorem"
                                                       if args.s_method == "legendre" else "S and H launches")
                                + ("; H as Alg. 3's L^H R" if args.h_method == "alg3" else "") + ")",
                      "kernel_ms": round(k_ms, 4),
-                     "achieved_algorithmic": round(achieved_alg, 2),
                      "peak_source": f"{src} bf16 {peak_kind} x 1.0 (fp16 = bf16 nominal rate)"},
         # the A/B assembly (HBM store-bound): 32 bytes stored per (atom, L, G)
         "roofline_ab": {"bound": "hbm", "kernel": "ab_assemble_kernel",
@@ -386,9 +475,6 @@ def cpu_baseline(p, h, H, S, layout, ngs, args, H64=None, S64=None):
     Frobenius error over the sampled full columns)."""
     import oracle
 
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from helpers import columns_from_lower
-
     oracle.build()
     n3 = h.gvectors(0)
     ng = ngs[0]
@@ -477,6 +563,14 @@ def main():
     ap.add_argument("--slices", type=int, default=7)
     ap.add_argument("--tile-order", type=int, default=0,
                     help="0: library default; k+1 forces emulated tile order k")
+    ap.add_argument("--cover", type=int, default=0, choices=[0, 1, 2],
+                    help="contraction tile cover: 0 by size, 1 cyclic, 2 aligned 256-row blocks")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="fixed tile cover, order and pipeline (by size or as forced) instead of the "
+                         "library's autotuner")
+    ap.add_argument("--pipeline", type=int, default=0, choices=[0, 1, 2],
+                    help="contraction load pipeline: 0 by size, 1 three stages of two K chunks, "
+                         "2 five stages of one")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
@@ -497,6 +591,8 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per contraction launch from an ncu capture")
     args = ap.parse_args()
+    if args.tile_order or args.pipeline or args.cover:
+        args.autotune = False  # a forced choice is measured as given
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -91,13 +91,18 @@ typedef struct flapw_options {
   int operands;  /* FLAPW_OPERANDS_FROM_AB (default) or FLAPW_OPERANDS_FACTORED */
   int use_graph; /* 1: capture build_HS into a CUDA graph and replay it while the
                     arguments repeat (default 0) */
-  int autotune;  /* 1: time the contraction's tile-order variants once per shape and
-                    keep the fastest (default 0: fixed choice) */
-  int tile_order; /* 0: library default (bands of 8 row blocks for N_G <= 16384,
-                     else bands of 2); k+1 forces tile order k of the emulated
-                     contraction (0 row-major, 1 column-major, 2/3/4/5 bands of
-                     4/2/8/3 row blocks of 256, 6 bands of 2 with alternating
-                     column direction), ignored when autotune is on */
+  int autotune;  /* 1: once per problem shape, time the emulated contraction's tile
+                    cover, tile order and load pipeline (coordinate descent over the
+                    three, on the slices of the first call) and keep the fastest; the
+                    choice is kept for the process and, if the environment variable
+                    FLAPW_AUTOTUNE_CACHE names a file, read from and appended to it
+                    (one line per shape).  Default 0: the fixed choices by size. */
+  int tile_order; /* 0: library default (cyclic cover: strip by strip;
+                     aligned cover: bands of 32 row blocks of 64 for N_G <= 16384,
+                     else bands of 8); k+1 forces tile order k of the emulated
+                     contraction (0 strip by strip, 1..5 bands of 4/8/16/32/64
+                     row blocks of 64, strip by strip within a band), ignored
+                     when autotune is on */
   int s_method;   /* FLAPW_S_CONTRACTION (default): S = Z_S^H Z_S like H;
                      FLAPW_S_LEGENDRE: S by the addition theorem (requires
                      FLAPW_OPERANDS_FACTORED; in FP64 on the FP64 path, in
@@ -106,7 +111,15 @@ typedef struct flapw_options {
   int pipeline;   /* emulated contraction's load pipeline: 0 by size (5 stages of one
                      64-wide K chunk above N_G 8192, else 3 stages of two), 1 the
                      3-stage shape, 2 the 5-stage shape; results are identical */
-  int reserved[6];
+  int tile_cover; /* how the emulated contraction's CTA-pair tiles (a 64-column
+                     strip against four 64-row blocks) cover the lower triangle:
+                     0 by size (cyclic up to N_G 8192, aligned above), 1 cyclic
+                     (each strip takes a cyclic window of row blocks; blocks above
+                     its diagonal are written conjugate-transposed, so every
+                     64 x 64 block is computed once), 2 aligned (256-row blocks
+                     aligned to 256; the upper parts of diagonal tiles are computed
+                     and not written); results agree to rounding */
+  int reserved[5];
 } flapw_options;
 
 typedef struct flapw_stats {
@@ -127,7 +140,9 @@ typedef struct flapw_stats {
   int n_tiles;         /* output tiles of the last contraction launch */
   int tile_order;      /* tile-order variant in use */
   int graph_replays;   /* build_HS calls served by CUDA-graph replay */
-  int reserved[8];
+  int tile_cover;      /* tile cover in use for the largest problem (1 cyclic, 2 aligned) */
+  int pipeline;        /* load pipeline in use (1: 3 stages of two chunks, 2: 5 of one) */
+  int reserved[6];
   double ms_s;         /* the S half of ms_contract: its contraction, or with
                           FLAPW_S_LEGENDRE the addition-theorem evaluation */
   double ms_ab_assemble; /* the A/B assembly kernel of the last build_AB (part of ms_ab) */

@@ -45,7 +45,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_slices", ctypes.c_int), ("layout", ctypes.c_int),
                 ("operands", ctypes.c_int), ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("tile_order", ctypes.c_int), ("s_method", ctypes.c_int), ("h_method", ctypes.c_int),
-                ("pipeline", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("pipeline", ctypes.c_int), ("tile_cover", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class Stats(ctypes.Structure):
@@ -56,7 +57,8 @@ class Stats(ctypes.Structure):
                 ("k_total", ctypes.c_int64), ("n_pos", ctypes.c_int), ("n_neg", ctypes.c_int),
                 ("n_pivot2", ctypes.c_int), ("n_slices", ctypes.c_int), ("n_tiles", ctypes.c_int),
                 ("tile_order", ctypes.c_int), ("graph_replays", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8), ("ms_s", ctypes.c_double),
+                ("tile_cover", ctypes.c_int), ("pipeline", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6), ("ms_s", ctypes.c_double),
                 ("ms_ab_assemble", ctypes.c_double)]
 
     def as_dict(self):

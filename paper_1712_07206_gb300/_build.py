@@ -35,6 +35,7 @@ def _deps():
                                                        os.path.join(SRC, "fixed64.cuh"),
                                                        os.path.join(SRC, "dfloat.cuh"),
                                                        os.path.join(SRC, "alg3.cuh"),
+                                                       os.path.join(SRC, "tiles.cuh"),
                                                        os.path.join(ROOT, "include", "flapw.h")]
     return max(os.path.getmtime(f) for f in files)
 

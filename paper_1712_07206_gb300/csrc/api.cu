@@ -4,20 +4,25 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
 #include "flapw_internal.h"
+#include "tiles.cuh"
 
 using namespace flapw;
 
 namespace {
 
 thread_local std::string g_last_error;  // errors of calls without a handle, per thread
-constexpr int kNumTileOrders = 7;  // emulated tile orders, see make_tiles
+constexpr int kNumTileOrders = cover::kNumOrders;  // emulated tile orders (tiles.cuh)
 
 // Device buffer that grows on demand.
 struct DevBuf {
@@ -87,6 +92,10 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
+namespace flapw {
+void set_thread_error(const char* msg) { g_last_error = msg ? msg : ""; }
+}  // namespace flapw
+
 struct flapw_ctx {
   std::string err;
   flapw_options opt{};
@@ -133,10 +142,15 @@ struct flapw_ctx {
   int64_t k_alloc = 0, rows = 0;
   int64_t k_terms = 0;           // most products summed into one output element
   int n_emu_tiles = 0, n_f64_tiles = 0, split_emu = 0, split_f64 = 0, tiles_order = -1;
-  int tile_order = 3;            // emulated tile order in use (see make_tiles)
-  int default_order = 3;         // the order for this crystal's sizes (default_tile_order)
+  int tile_order = 4;            // emulated tile order in use (tiles.cuh)
+  int64_t max_ng = 0;            // largest N_G of the handle's problems (default tile order)
+  std::vector<int> emu_tiles_per_prob;  // whole emulated tiles of each problem
+  int tile_cover = 0;            // emulated tile cover in use (tiles.cuh; 0 by N_G)
+  int tiles_cover = -1;          // cover of the uploaded lists
   bool deep_pipe = false;        // the contraction's deep pipeline (herk_emu_deep of the largest N_G)
-  int64_t tuned_key = -1;        // shape the autotuner last ran on
+  std::string tuned_shape;       // shape the autotuner's choice in use belongs to
+  int pipe_choice = 0;           // autotuner's load pipeline (1 shallow, 2 deep; 0 none)
+  std::string device_name;       // for the autotuner's shape key
   int64_t tiles_rows_key = -1;
   int tiles_pairs = -1;          // pair counts the tile lists' last waves were split for
   int split_ids = 0;             // split tiles of a half (scratch slots)
@@ -208,7 +222,7 @@ int check_options(flapw_ctx* h, const flapw_options& o) {
   if (o.operands != FLAPW_OPERANDS_FROM_AB && o.operands != FLAPW_OPERANDS_FACTORED)
     return fail(h, FLAPW_ERR_ARG, "options.operands is not a FLAPW_OPERANDS_* value");
   if (o.tile_order < 0 || o.tile_order > kNumTileOrders)
-    return fail(h, FLAPW_ERR_ARG, "options.tile_order must be in 0..7");
+    return fail(h, FLAPW_ERR_ARG, "options.tile_order must be in 0..6");
   if (o.s_method != FLAPW_S_CONTRACTION && o.s_method != FLAPW_S_LEGENDRE)
     return fail(h, FLAPW_ERR_ARG, "options.s_method is not a FLAPW_S_* value");
   if (o.s_method == FLAPW_S_LEGENDRE && o.operands != FLAPW_OPERANDS_FACTORED)
@@ -216,6 +230,7 @@ int check_options(flapw_ctx* h, const flapw_options& o) {
   if (o.h_method != FLAPW_H_FACTORED && o.h_method != FLAPW_H_ALG3)
     return fail(h, FLAPW_ERR_ARG, "options.h_method is not a FLAPW_H_* value");
   if (o.pipeline < 0 || o.pipeline > 2) return fail(h, FLAPW_ERR_ARG, "options.pipeline must be in 0..2");
+  if (o.tile_cover < 0 || o.tile_cover > 2) return fail(h, FLAPW_ERR_ARG, "options.tile_cover must be in 0..2");
   return FLAPW_OK;
 }
 
@@ -225,6 +240,13 @@ int device_setup(flapw_ctx* h) {
   CK(h, cudaGetDevice(&h->device), "cudaGetDevice");
   CK(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device),
      "cudaDeviceGetAttribute");
+  {
+    cudaDeviceProp prop;
+    CK(h, cudaGetDeviceProperties(&prop, h->device), "cudaGetDeviceProperties");
+    h->device_name = prop.name;
+    for (char& c : h->device_name)
+      if (c == ' ' || c == '/') c = '_';
+  }
   for (auto& e : h->ev) CK(h, cudaEventCreate(&e), "cudaEventCreate");
   CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
   CK(h, cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking), "cudaStreamCreate");
@@ -248,47 +270,43 @@ int upload(flapw_ctx* h, DevBuf& d, const std::vector<T>& v) {
 // bytes) on config-2-like shapes.
 int h_split_block(int ng) { return (int)(0.55 * ((ng + 63) / 64)); }
 
-// Emulated contraction tiles (256 x 64, one per CTA pair) and FP64 tiles
-// (64 x 64) of the lower triangles of problems [p0, p1).  The order of the
-// emulated tiles decides which operand rows the ~75 concurrently running
-// tiles share in L2:
-//   order 0: row blocks outer, column blocks inner;  1: column blocks outer;
-//   order 2/3/4/5: grouped raster -- bands of 4/2/8/3 row blocks, and within a
-//   band column by column, so the concurrent tiles touch a compact set of rows;
-//   order 6: bands of 2, the column direction alternating from band to band.
-// part 0 takes every tile; 1 the column blocks below h_split_block(N_G), 2 the
-// rest (an H contraction in two launches, so that the first part's columns
-// can go to host memory while the second part runs).
-void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order, int pairs,
+// Emulated contraction tiles (one per CTA pair: a 64-column strip against four
+// 64-row blocks, the cyclic cover of tiles.cuh) and FP64 tiles (64 x 64) of the
+// lower triangles of problems [p0, p1).  The order of the emulated tiles
+// decides which operand rows the ~75 concurrently running tiles share in L2:
+// order 0 strip by strip; orders 1..5 bands of 4/8/16/32/64 row blocks of 64,
+// strip by strip within a band.  cover_opt is the cyclic or the aligned cover
+// (tiles.cuh), one for every problem of the handle (one kernel instantiation
+// per launch).  part 0 takes every tile; 1 the strips below
+// h_split_block(N_G), 2 the rest (an H contraction in two launches, so that the
+// first part's columns can go to host memory while the second part runs; the
+// cover is then cut at that strip, so the first part writes exactly the
+// columns below it).  per_prob[p] counts the whole tiles of problem p.
+void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order, int cover_opt, int pairs,
                 std::vector<EmuTile>* emu, std::vector<F64Tile>* f64, int* n_split_ids,
-                int part = 0) {
+                std::vector<int>* per_prob, int part = 0) {
   const size_t emu0 = emu->size();
+  const int band = cover::order_band(order);
   for (int p = p0; p < p1; ++p) {
     const int ng = probs[p].n_g;
-    const int nib = (ng + 255) / 256, njb = (ng + 63) / 64;
+    const int ncb = (ng + 63) / 64;
     const int j1 = h_split_block(ng);
-    auto valid = [&](int ib, int jb) {
-      if (part == 1 && jb >= j1) return false;
-      if (part == 2 && jb < j1) return false;
-      return jb * 64 <= ib * 256 + 255;
+    const int s0 = (part == 2) ? j1 : 0, s1 = (part == 1) ? j1 : ncb;
+    std::vector<EmuTile> pt;
+    auto emit = [&](int jb, int mask, int r0, int r1, int r2, int r3) {
+      pt.push_back(EmuTile{p, jb, 0, mask, {r0, r1, r2, r3}});
     };
-    if (order == 0) {
-      for (int ib = 0; ib < nib; ++ib)
-        for (int jb = 0; jb < njb; ++jb)
-          if (valid(ib, jb)) emu->push_back(EmuTile{p, ib, jb, 0});
-    } else if (order == 1) {
-      for (int jb = 0; jb < njb; ++jb)
-        for (int ib = 0; ib < nib; ++ib)
-          if (valid(ib, jb)) emu->push_back(EmuTile{p, ib, jb, 0});
-    } else {
-      const int band = (order == 2) ? 4 : (order == 3 || order == 6) ? 2 : (order == 4) ? 8 : 3;
-      for (int i0 = 0, b = 0; i0 < nib; i0 += band, ++b)
-        for (int jj = 0; jj < njb; ++jj) {
-          const int jb = (order == 6 && (b & 1)) ? njb - 1 - jj : jj;
-          for (int ib = i0; ib < std::min(nib, i0 + band); ++ib)
-            if (valid(ib, jb)) emu->push_back(EmuTile{p, ib, jb, 0});
-        }
-    }
+    if (cover_opt == cover::kCoverCyclic)
+      cover::for_each_tile(ncb, part ? j1 : ncb, s0, s1, emit);
+    else
+      cover::for_each_aligned_tile(ncb, s0, s1, emit);
+    if (band > 0)
+      std::stable_sort(pt.begin(), pt.end(), [band](const EmuTile& x, const EmuTile& y) {
+        const int bx = x.rb[0] / band, by = y.rb[0] / band;
+        return bx != by ? bx < by : x.jb < y.jb;
+      });
+    if (per_prob) (*per_prob)[p] += (int)pt.size();
+    emu->insert(emu->end(), pt.begin(), pt.end());
     const int nb = (ng + 63) / 64;
     for (int ib = 0; ib < nb; ++ib)
       for (int jb = 0; jb <= ib; ++jb)
@@ -370,6 +388,7 @@ struct Half {
 
 // The contraction's pipeline shape: the option, or by size.
 bool use_deep_pipe(const flapw_ctx* h) {
+  if (h->opt.autotune && h->pipe_choice) return h->pipe_choice == 2;
   return h->opt.pipeline == 2 || (h->opt.pipeline == 0 && h->deep_pipe);
 }
 
@@ -400,7 +419,8 @@ int enqueue_contraction(flapw_ctx* h, const Half& hf, int busy_sms, cudaStream_t
     if (int rc = split_scratch(h, st, &sp)) return rc;
     CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf.emu_t0,
                           hf.emu_nt, h->d_rexp.as<int>(), s, fixed_frac_bits(h->k_terms),
-                          h->d_cnt.as<int>() + 2, busy_sms, sp, use_deep_pipe(h), st),
+                          h->d_cnt.as<int>() + 2, busy_sms, sp, use_deep_pipe(h),
+                          h->tiles_cover == cover::kCoverCyclic, st),
        "emulated contraction launch");
   } else {
     if (ev_sl >= 0) CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
@@ -438,25 +458,30 @@ int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int6
                  Half* first, Half* second, int busy_first = 0, int busy_second = 0,
                  bool split_first = false, Half* first_b = nullptr) {
   const int order = h->tile_order;
+  int max_ng = 0;
+  for (const Prob& p : probs) max_ng = std::max(max_ng, p.n_g);
+  const int cover_opt = cover::cover_for(h->tile_cover, max_ng);
   int pf = 0, ps = 0;
   if (h->opt.precision == FLAPW_PREC_EMU) {
     CK(h, herk_emu_init(), "contraction kernel setup");
     pf = herk_emu_pairs(busy_first);
     ps = herk_emu_pairs(busy_second);
   }
-  if (h->tiles_rows_key != key || h->tiles_order != order || h->tiles_pairs != pf * 1024 + ps ||
-      h->tiles_split != split_first) {
+  if (h->tiles_rows_key != key || h->tiles_order != order || h->tiles_cover != cover_opt ||
+      h->tiles_pairs != pf * 1024 + ps || h->tiles_split != split_first) {
     std::vector<EmuTile> emu;
     std::vector<F64Tile> f64;
     int ids_first = 0, ids_second = 0, ids_b = 0;
-    make_tiles(probs, 0, n_first, order, pf, &emu, &f64, &ids_first, split_first ? 1 : 0);
+    std::vector<int>* pp = &h->emu_tiles_per_prob;
+    pp->assign(probs.size(), 0);
+    make_tiles(probs, 0, n_first, order, cover_opt, pf, &emu, &f64, &ids_first, pp, split_first ? 1 : 0);
     h->split_emu_b = (int)emu.size();
     h->split_f64_b = (int)f64.size();
-    if (split_first) make_tiles(probs, 0, n_first, order, pf, &emu, &f64, &ids_b, 2);
+    if (split_first) make_tiles(probs, 0, n_first, order, cover_opt, pf, &emu, &f64, &ids_b, pp, 2);
     ids_first = std::max(ids_first, ids_b);
     h->split_emu = (int)emu.size();
     h->split_f64 = (int)f64.size();
-    make_tiles(probs, n_first, (int)probs.size(), order, ps, &emu, &f64, &ids_second);
+    make_tiles(probs, n_first, (int)probs.size(), order, cover_opt, ps, &emu, &f64, &ids_second, pp);
     h->n_emu_tiles = (int)emu.size();
     h->n_f64_tiles = (int)f64.size();
     if (upload(h, h->d_emu_tiles, emu)) return FLAPW_ERR_CUDA;
@@ -466,6 +491,7 @@ int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int6
     CK(h, h->d_split.ensure(split_scratch_bytes(std::max(1, h->split_ids))), "split-tile scratch");
     h->tiles_rows_key = key;
     h->tiles_order = order;
+    h->tiles_cover = cover_opt;
     h->tiles_pairs = pf * 1024 + ps;
     h->tiles_split = split_first;
   }
@@ -486,29 +512,97 @@ int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int6
   return FLAPW_OK;
 }
 
-// Library default tile order for the largest N_G: bands of 8 row blocks for
-// N_G <= 16384, else bands of 2.  Measured on the contraction (GB300), bands of
-// 8 / 2: N_G 3990 (3-stage pipeline) 6.03 / 6.12 ms; N_G 11996 (5-stage)
-// 299.7 / 307.9 ms; N_G 23993 (5-stage) 4256 / 3556 ms: the largest problems
-// need the operand rows of the concurrently running tiles to overlap more in
-// L2 than a band of 8 row blocks allows.
-int default_tile_order(int64_t max_ng) { return max_ng <= 16384 ? 4 : 3; }
+// Library default tile order for the handle's cover and largest N_G (tiles.cuh).
+int default_tile_order(const flapw_ctx* h) { return cover::default_order(h->tile_cover, h->max_ng); }
 
-// Times the emulated contraction under every tile order on the slices the
-// last build left in place (the outputs are rewritten with the same values)
-// and keeps the fastest order for this shape.
+// The tile order in use unless the autotuner picks it: the forced one, else
+// the default for the cover.
+void set_tile_order(flapw_ctx* h) {
+  if (h->opt.tile_order > 0 && !h->opt.autotune) h->tile_order = h->opt.tile_order - 1;
+  else h->tile_order = default_tile_order(h);
+}
+
+// Autotuner choices by problem shape: kept for the process and, if the
+// environment variable FLAPW_AUTOTUNE_CACHE names a file, read from it once
+// and appended to it, one line "shape cover order pipeline" per shape.
+struct Tuned {
+  int cover, order, pipe;
+};
+std::mutex g_tune_mutex;
+std::map<std::string, Tuned> g_tuned;
+bool g_tune_file_read = false;
+
+const char* tune_file() {
+  const char* f = std::getenv("FLAPW_AUTOTUNE_CACHE");
+  return (f && *f) ? f : nullptr;
+}
+
+// The shape key: GPU, slice count, H and S methods, K of the H contraction
+// and every problem's N_G (hashed).
+std::string shape_key(const flapw_ctx* h, const std::vector<Prob>& probs) {
+  uint64_t x = 1469598103934665603ull;  // FNV-1a over the N_G list
+  for (const Prob& p : probs) {
+    x ^= (uint64_t)p.n_g;
+    x *= 1099511628211ull;
+  }
+  std::ostringstream o;
+  o << h->device_name << "/sm" << h->num_sms << "/s" << slices_of(h) << "/h" << h->opt.h_method << "/s"
+    << h->opt.s_method << "/k" << h->k_terms << "/p" << probs.size() << "/" << std::hex << x;
+  return o.str();
+}
+
+bool tuned_lookup(const std::string& key, Tuned* t) {
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  if (!g_tune_file_read) {
+    g_tune_file_read = true;
+    if (const char* f = tune_file()) {
+      std::ifstream in(f);
+      std::string k;
+      Tuned v;
+      while (in >> k >> v.cover >> v.order >> v.pipe)
+        if (v.cover >= 1 && v.cover <= 2 && v.order >= 0 && v.order < kNumTileOrders && v.pipe >= 1 &&
+            v.pipe <= 2)
+          g_tuned[k] = v;
+    }
+  }
+  auto it = g_tuned.find(key);
+  if (it == g_tuned.end()) return false;
+  *t = it->second;
+  return true;
+}
+
+void tuned_store(const std::string& key, const Tuned& t) {
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  g_tuned[key] = t;
+  if (const char* f = tune_file()) {
+    std::ofstream out(f, std::ios::app);
+    out << key << " " << t.cover << " " << t.order << " " << t.pipe << "\n";
+  }
+}
+
+void apply_tuned(flapw_ctx* h, const Tuned& t) {
+  h->tile_cover = t.cover;
+  h->tile_order = t.order;
+  h->pipe_choice = t.pipe;
+}
+
+// Times the emulated contraction (both halves) on the slices the last build
+// left in place, the outputs rewritten with the same values, and picks the
+// tile cover, the tile order and the load pipeline by coordinate descent from
+// the size-based defaults: the pipeline, then the other cover (with its default
+// order), then every order.
 int autotune_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int64_t key,
-                   int n_slots, cudaStream_t st) {
+                   int n_slots, const std::string& shape, cudaStream_t st) {
   CK(h, cudaStreamSynchronize(st), "cudaStreamSynchronize");
   CK(h, cudaStreamSynchronize(h->aux_stream), "cudaStreamSynchronize");
   const int s = slices_of(h);
-  float best = 1e30f;
-  int best_o = h->tile_order;
-  for (int o = 0; o < kNumTileOrders; ++o) {
-    h->tile_order = o;
+  int max_ng = 0;
+  for (const Prob& p : probs) max_ng = std::max(max_ng, p.n_g);
+  auto time_cfg = [&](const Tuned& c, float* out) -> int {
+    apply_tuned(h, c);
     Half a, b;
     if (int rc = ensure_tiles(h, probs, n_first, key, &a, &b, 0, n_slots)) return rc;
-    float t_best = 1e30f;
+    float best = 1e30f;
     for (int rep = 0; rep < 2; ++rep) {
       CK(h, cudaEventRecord(h->ev[14], st), "cudaEventRecord");
       for (const Half* hf : {&b, &a}) {
@@ -516,24 +610,44 @@ int autotune_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, in
         if (int rc = split_scratch(h, st, &sp)) return rc;
         CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf->emu_t0,
                               hf->emu_nt, h->d_rexp.as<int>(), s, fixed_frac_bits(h->k_terms),
-                              h->d_cnt.as<int>() + 2, 0, sp, use_deep_pipe(h), st),
+                              h->d_cnt.as<int>() + 2, 0, sp, use_deep_pipe(h),
+                              h->tiles_cover == cover::kCoverCyclic, st),
            "emulated contraction launch");
       }
       CK(h, cudaEventRecord(h->ev[15], st), "cudaEventRecord");
       CK(h, cudaEventSynchronize(h->ev[15]), "cudaEventSynchronize");
       float ms = 0.f;
       CK(h, cudaEventElapsedTime(&ms, h->ev[14], h->ev[15]), "cudaEventElapsedTime");
-      t_best = std::min(t_best, ms);
+      best = std::min(best, ms);
+      if (ms > 200.f) break;  // long launches: one repetition is enough
     }
-    if (t_best < best) {
-      best = t_best;
-      best_o = o;
+    *out = best;
+    return FLAPW_OK;
+  };
+  const int cov0 = cover::cover_for(cover::kCoverAuto, max_ng);
+  Tuned cur{cov0, cover::default_order(cov0, max_ng), herk_emu_deep(max_ng) ? 2 : 1};
+  float t_cur = 0.f;
+  if (int rc = time_cfg(cur, &t_cur)) return rc;
+  auto try_cfg = [&](Tuned c) -> int {
+    float t = 0.f;
+    if (int rc = time_cfg(c, &t)) return rc;
+    if (t < t_cur) {
+      t_cur = t;
+      cur = c;
     }
-  }
-  h->tile_order = best_o;
+    return FLAPW_OK;
+  };
+  if (int rc = try_cfg(Tuned{cur.cover, cur.order, 3 - cur.pipe})) return rc;
+  if (int rc = try_cfg(Tuned{3 - cur.cover, cover::default_order(3 - cur.cover, max_ng), cur.pipe})) return rc;
+  const int o0 = cur.order;
+  for (int o = 0; o < kNumTileOrders; ++o)
+    if (o != o0)
+      if (int rc = try_cfg(Tuned{cur.cover, o, cur.pipe})) return rc;
+  apply_tuned(h, cur);
   Half a, b;
   if (int rc = ensure_tiles(h, probs, n_first, key, &a, &b, 0, n_slots)) return rc;
-  h->tuned_key = key;
+  tuned_store(shape, cur);
+  h->tuned_shape = shape;
   return FLAPW_OK;
 }
 
@@ -569,7 +683,8 @@ int flapw_engine_create(const flapw_options* opt, flapw_handle* out) {
   flapw_default_options(&h->opt);
   if (opt) h->opt = *opt;
   if (check_options(nullptr, h->opt)) return FLAPW_ERR_ARG;
-  if (h->opt.tile_order > 0 && !h->opt.autotune) h->tile_order = h->opt.tile_order - 1;
+  h->tile_cover = h->opt.tile_cover;
+  set_tile_order(h.get());
   h->engine_only = true;
   if (int rc = device_setup(h.get())) {
     g_last_error = h->err;
@@ -595,7 +710,7 @@ int flapw_hs_create(const double lattice[9], int n_atoms, const double* pos_frac
   flapw_default_options(&h->opt);
   if (opt) h->opt = *opt;
   if (check_options(nullptr, h->opt)) return FLAPW_ERR_ARG;
-  if (h->opt.tile_order > 0 && !h->opt.autotune) h->tile_order = h->opt.tile_order - 1;
+  h->tile_cover = h->opt.tile_cover;
   std::memcpy(h->lat, lattice, sizeof(h->lat));
   double det;
   reciprocal(h->lat, h->rec, &det);
@@ -623,9 +738,9 @@ int flapw_hs_create(const double lattice[9], int n_atoms, const double* pos_frac
   if (h->g_total > (int64_t)1 << 30) return fail(nullptr, FLAPW_ERR_UNSUPPORTED, "too many plane waves");
   int64_t max_ng = 0;
   for (int k = 0; k < n_k; ++k) max_ng = std::max<int64_t>(max_ng, h->goff[k + 1] - h->goff[k]);
-  h->default_order = default_tile_order(max_ng);
+  h->max_ng = max_ng;
   h->deep_pipe = herk_emu_deep(max_ng);
-  if (!(h->opt.tile_order > 0 && !h->opt.autotune)) h->tile_order = h->default_order;
+  set_tile_order(h.get());
   h->ktau.resize((size_t)n_k * n_atoms);
   for (int k = 0; k < n_k; ++k)
     for (int a = 0; a < n_atoms; ++a)
@@ -688,8 +803,12 @@ int flapw_set_options(flapw_handle h, const flapw_options* opt) {
   if (!h || !opt) return fail(h, FLAPW_ERR_ARG, "NULL argument");
   if (int rc = check_options(h, *opt)) return rc;
   h->opt = *opt;
-  if (opt->tile_order > 0 && !opt->autotune) h->tile_order = opt->tile_order - 1;
-  else if (!opt->autotune) h->tile_order = h->default_order;
+  if (!opt->autotune) {
+    h->tile_cover = opt->tile_cover;
+    h->pipe_choice = 0;
+    h->tuned_shape.clear();
+    set_tile_order(h);
+  }
   return FLAPW_OK;
 }
 
@@ -973,7 +1092,26 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   // which times whole halves)
   bool h_host = false;
   for (int k = 0; k < nk; ++k) h_host = h_host || op.host[k] != nullptr;
-  const bool h_split = h_host && !h->opt.autotune;
+  // autotuner: a shape seen before runs with its choice; a new one runs with
+  // the size-based defaults and is tuned after the enqueue below
+  const bool tune = h->opt.autotune && h->opt.precision == FLAPW_PREC_EMU;
+  std::string shape;
+  if (tune) {
+    shape = shape_key(h, probs);
+    Tuned t;
+    if (h->tuned_shape != shape) {
+      if (tuned_lookup(shape, &t)) {
+        apply_tuned(h, t);
+        h->tuned_shape = shape;
+      } else {
+        h->tile_cover = h->opt.tile_cover;
+        h->tile_order = default_tile_order(h);
+        h->pipe_choice = 0;
+      }
+    }
+  }
+  // (the call that tunes times whole halves: no split there)
+  const bool h_split = h_host && !(tune && h->tuned_shape != shape);
   Half hH, hHb, hS;
   if (int rc = ensure_tiles(h, probs, nk, h->rows, &hH, &hS, 0, n_slots, h_split, &hHb)) return rc;
   hH.row0 = 0;
@@ -1254,8 +1392,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   h->last_stream = user_st;
   if (!h->opt.use_graph) {
     if (int rc = enqueue(user_st)) return rc;
-    if (h->opt.autotune && h->opt.precision == FLAPW_PREC_EMU && h->tuned_key != h->rows)
-      return autotune_tiles(h, probs, nk, h->rows, n_slots, user_st);
+    if (tune && h->tuned_shape != shape) return autotune_tiles(h, probs, nk, h->rows, n_slots, shape, user_st);
     return FLAPW_OK;
   }
 
@@ -1331,6 +1468,8 @@ int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const i
   h->k_alloc = k_alloc;
   h->k_terms = K;
   h->deep_pipe = herk_emu_deep(N);
+  h->max_ng = N;
+  set_tile_order(h);
   if (upload(h, h->d_kmap, kmap) || upload(h, h->d_probs, probs)) return FLAPW_ERR_CUDA;
   std::vector<int> rp(N, 0);
   if (upload(h, h->d_rowprob, rp)) return FLAPW_ERR_CUDA;
@@ -1416,6 +1555,13 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
   s.n_slices = slices_of(h);
   s.n_tiles = (h->opt.precision == FLAPW_PREC_EMU) ? h->n_emu_tiles : h->n_f64_tiles;
   s.tile_order = h->tiles_order;
+  {
+    int64_t max_ng = 0;
+    for (int k = 0; k < h->n_k; ++k) max_ng = std::max<int64_t>(max_ng, h->goff[k + 1] - h->goff[k]);
+    if (h->engine_only) max_ng = h->rows;
+    s.tile_cover = h->tiles_cover >= 0 ? h->tiles_cover : cover::cover_for(h->tile_cover, max_ng);
+    s.pipeline = use_deep_pipe(h) ? 2 : 1;
+  }
   if (!h->engine_only) {
     s.k_total = (int64_t)h->n_atoms * (h->last_alg3 ? 3 : 2) * h->n_L;
     double ng2 = 0;
@@ -1440,21 +1586,21 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
       s.n_pivot2 = c[0];
       s.n_pos = kpk[1];
       s.n_neg = kpk[2];
-      // tensor flops: per 256 x 64 tile, slice pairs x chunks x 2 passes x 4 x (2*256*128*16)
+      // tensor flops executed: per tile, slice pair and 16-wide K step of
+      // the 64-wide chunks (each sign block padded to whole chunks), an R and
+      // an I pass of M = 256, N = 128, K = 16 MMAs
       const int S_ = slices_of(h);
       const double pairs = S_ * (S_ + 1) / 2.0;
-      const double chH = std::ceil(kpk[1] / 64.0) + std::ceil(kpk[2] / 64.0);
-      const double chS = (h->opt.s_method == FLAPW_S_LEGENDRE)
+      const double ksH = 4.0 * (std::ceil(kpk[1] / 64.0) + std::ceil(kpk[2] / 64.0));
+      const double ksS = (h->opt.s_method == FLAPW_S_LEGENDRE)
                              ? 0.0
-                             : std::ceil((double)h->n_atoms * 2 * h->n_L / 64.0);
+                             : 4.0 * std::ceil((double)h->n_atoms * 2 * h->n_L / 64.0);
       double tf = 0;
-      for (int k = 0; k < h->n_k; ++k) {
-        const int ng = (int)(h->goff[k + 1] - h->goff[k]);
-        const int nib = (ng + 255) / 256, njb = (ng + 63) / 64;
-        double nt = 0;
-        for (int ib = 0; ib < nib; ++ib) nt += std::min(njb, 4 * ib + 4);
-        tf += nt * pairs * (chH + chS) * 2.0 * 4.0 * (2.0 * 256 * 128 * 16);
-      }
+      const int nk = h->n_k;
+      if ((int)h->emu_tiles_per_prob.size() == 2 * nk)
+        for (int k = 0; k < nk; ++k)
+          tf += pairs * 2.0 * (2.0 * 256 * 128 * 16) *
+                (h->emu_tiles_per_prob[k] * ksH + h->emu_tiles_per_prob[nk + k] * ksS);
       s.flops_tensor = tf;
     } else {
       (void)cudaGetLastError();

@@ -35,15 +35,21 @@ struct Prob {
   double2* out;   // lower triangle, complex128
 };
 
-// Output tile of the emulated contraction: 256 rows (G') x 64 columns (G),
-// computed by a CTA pair.  `split` is 0 for a whole tile, or, for one of the
-// `parts` K parts of a tile of the last wave, parts | part << 4 | id << 8
-// (id: the split tile's scratch slot).
+// Output tile of the emulated contraction, computed by a CTA pair: the 64
+// columns of strip jb (64-column block) against four 64-row blocks rb[0..3]
+// (CTA 0 rb[0], rb[1]; CTA 1 rb[2], rb[3]); see tiles.cuh for the cover.
+// Bit b of wmask: block rb[b] is written (clear for padding).  A block
+// below the strip's diagonal (rb > jb) is written in place, the diagonal
+// block (rb == jb) on and below the diagonal, a block above it (rb < jb)
+// conjugate-transposed into the lower triangle.  `split` is 0 for a whole
+// tile, or, for one of the `parts` K parts of a tile of the last wave,
+// parts | part << 4 | id << 8 (id: the split tile's scratch slot).
 struct EmuTile {
   int prob;
-  int ib;  // row block (256)
-  int jb;  // column block (64)
+  int jb;
   int split;
+  int wmask;
+  int rb[4];
 };
 constexpr int kMaxSplit = 4;  // K parts of a split tile
 __host__ __device__ inline int split_parts(int s) { return (s & 15) ? (s & 15) : 1; }
@@ -297,14 +303,19 @@ cudaError_t herk_emu_init();
 // Launches persistent CTA pairs: min(n_tiles, co-resident pairs - busy_sms),
 // where busy_sms is the number of SMs that concurrent work holds.  deep: the
 // pipeline of 5 one-chunk stages (large N_G) instead of 3 two-chunk stages.
+// cyclic: the tiles are of the cyclic cover (tiles.cuh), else of the aligned one.
 cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuTile* tiles,
                             int n_tiles, const int* rexp, int n_slices, int frac, int* err,
-                            int busy_sms, const SplitScratch& split, bool deep, cudaStream_t st);
+                            int busy_sms, const SplitScratch& split, bool deep, bool cyclic,
+                            cudaStream_t st);
 // The pair count a launch beside busy_sms busy SMs gets (0 before herk_emu_init).
 int herk_emu_pairs(int busy_sms);
 size_t herk_emu_smem_bytes(bool deep);
 // The pipeline for problems of at most max_ng plane waves: deep above 8192.
 inline bool herk_emu_deep(int64_t max_ng) { return max_ng > 8192; }
+
+// Message of the calling thread's last handle-less error (flapw_last_error(NULL)).
+void set_thread_error(const char* msg);
 
 // ---- host G enumeration ----------------------------------------------------
 int enumerate_g(const double lat[9], const double k[3], double kmax, std::vector<int>* n3);

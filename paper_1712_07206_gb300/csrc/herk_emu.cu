@@ -23,7 +23,11 @@
 //
 // The kernel runs on CTA pairs (a 2-CTA cluster, tcgen05 cta_group::2).  A
 // pair owns an output tile of 256 rows (G') x 64 columns (G) of complex
-// output; CTA r of the pair holds rows 128r..128r+127 and their accumulators.
+// output: the 64 columns of one strip against four 64-row blocks, CTA r
+// holding blocks rb[2r], rb[2r+1] (one 128-row load when they are adjacent,
+// two 64-row loads otherwise) and their accumulators.  The blocks form the
+// cyclic cover of tiles.cuh: blocks above the strip's diagonal are written
+// conjugate-transposed, so every lower 64 x 64 block is computed once.
 // Slice pairs are taken in groups (i; j, j+1) sharing the row slice i.  Per
 // 128-wide K stage each CTA loads with TMA (128-byte swizzle), for two 64-wide
 // K chunks, one plane of slice i for its 128 rows (the MMA's A) and its half
@@ -44,8 +48,12 @@
 // both signs in the same sums and has the schedule of S.
 //
 // Warp roles (both CTAs): warp 0 TMA producer, warp 1 TMEM allocator (and in
-// CTA 0 the MMA issuer), warps 2..9 drain/epilogue (warp w reads TMEM lanes
-// 32*(w%4)..+31; warps 2-5 own Re, 6-9 own Im).  Stage and accumulator
+// CTA 0 the MMA issuer), warps 2-3 idle, warps 4..11 drain/epilogue (warp w
+// reads TMEM lanes 32*(w%4)..+31; warps 4-7 own Re, 8-11 own Im).  The first
+// warpgroup hands registers to the two drain warpgroups (setmaxnreg), whose
+// 64 fixed-point accumulators per thread then fit with the loop state; with
+// one budget for all roles the spills the compiler placed landed in the
+// producer and MMA loops and lengthened every stage hand-off.  Stage and accumulator
 // barriers live in CTA 0 (full, tempty) or in both CTAs (empty, tfull,
 // signalled by multicast commits).  Persistent pairs walk the tile list.
 // Every wait is bounded by a wall-clock limit; on expiry the CTA records an
@@ -63,7 +71,13 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 320;
+constexpr int kThreads = 384;      // three warpgroups
+constexpr int kDrainWarp0 = 4;     // first drain warp (warpgroups 1 and 2)
+// Registers per thread after the split: 384 threads x 168 at launch = 64512;
+// 128 x 80 + 256 x 208 = 63488 fits (per SM sub-partition: one warp of the
+// first warpgroup and two drain warps, 32 x (80 + 2 x 208) = 15872 of 16384).
+constexpr int kRegsCtl = 80;
+constexpr int kRegsDrain = 208;
 constexpr uint32_t kTileA = 128 * 128;                   // A: 128 rows x 128 B, one chunk
 constexpr uint32_t kTileB = 128 * 128;                   // this CTA's B half: <= 128 rows
 constexpr uint32_t kTmemCols = 512;
@@ -241,7 +255,97 @@ struct Sched {
   }
 };
 
-template <class PP>
+// This thread's row of a finished tile into the lower triangle: in place
+// below the strip's diagonal (on and below it in the diagonal block),
+// conjugate-transposed above it (element (gr, gc) to (gc, gr); Hermitian
+// result).  Element n goes to offset o_n, o_{n+1} = o_n + step_n,
+// step_{n+1} = step_n + dstep (the packed layout's columns shorten by one).
+// Out of line: it runs once per tile, and kept inline it changed how the
+// compiler laid out the MMA and load loops (measured 5-10 % on the contraction).
+__device__ __noinline__ void write_tile_row(const EmuTile& T, const Prob& P, uint32_t rank, int m, int h,
+                                           const long long (&acc)[64], const int* rexp, int frac) {
+  const int blk = 2 * (int)rank + (m >> 6);
+  const int rbk = (blk & 2) ? ((blk & 1) ? T.rb[3] : T.rb[2]) : ((blk & 1) ? T.rb[1] : T.rb[0]);
+  const int64_t ng = P.n_g;
+  const int64_t gr = (int64_t)rbk * 64 + (m & 63);
+  const int64_t gc0 = (int64_t)T.jb * 64;
+  if (!(((T.wmask >> blk) & 1) && gr < ng)) return;
+  const bool packed = P.layout == FLAPW_LAYOUT_LOWER_PACKED;
+  const bool trans = rbk < T.jb;
+  int64_t o, step, dstep = 0;
+  if (trans) {
+    o = (packed ? gr * ng - gr * (gr - 1) / 2 - gr : gr * P.ld) + gc0;
+    step = 1;
+  } else if (packed) {
+    o = gc0 * ng - gc0 * (gc0 - 1) / 2 + (gr - gc0);
+    step = ng - 1 - gc0;
+    dstep = -1;
+  } else {
+    o = gc0 * P.ld + gr;
+    step = P.ld;
+  }
+  const int64_t lim = trans ? ng - gc0 : min(ng - gc0, gr - gc0 + 1);
+  const int nlim = lim < 64 ? (int)lim : 64;
+  const bool neg = trans && h;
+  const int er = rexp[P.row_base + gr] - frac;
+  const int* ec = rexp + P.col_base + gc0;
+  double* outd = reinterpret_cast<double*>(P.out) + h;
+#pragma unroll
+  for (int n = 0; n < 64; ++n) {
+    if (n < nlim) outd[2 * o] = fx::to_double(neg ? -acc[n] : acc[n], er + ec[n]);
+    o += step;
+    step += dstep;
+  }
+}
+
+// The producer's loads of one tile: for every drain step of the tile, its K
+// stages (A: plane `pass` of slice i, this CTA's 128 rows; B: this CTA's half
+// of the slice group).  SPLIT: the CTA's two 64-row blocks are not adjacent
+// and A goes as two 64-row boxes.  `it` counts the stages; false if a wait
+// ran out.
+template <bool SPLIT, class PP>
+__device__ __forceinline__ bool produce_tile(const SliceMaps& maps, const Prob& P, const EmuTile& T,
+                                             int rowA0, int rowA1, int rowB, uint32_t rank, int n_slices,
+                                             uint8_t* smem, uint32_t bar0, uint32_t& it, const Abort& ab) {
+  constexpr int kStages = PP::kStages, kStageChunks = PP::kStageChunks;
+  Sched sc;
+  for (bool more = sc.begin(units_of(P, T.split), n_slices); more; more = sc.next()) {
+    const uint32_t b_bytes = sc.two ? kTileB : kTileB / 2;
+    for (int c = sc.s0; c < sc.s1; c += kStageChunks) {
+      const int nv = min(kStageChunks, sc.s1 - c);
+      const int stage = it % kStages;
+      const uint32_t round = it / kStages;
+      if (!mbar_wait(bar0 + 8u * (kStages + stage), (round & 1u) ^ 1u, ab)) return false;  // empty
+      const uint32_t sbase = smem_u32(smem + stage * PP::kStageBytes);
+      const uint32_t fb = bar0 + 8u * stage;  // full
+      // CTA 0's barrier counts the bytes of both CTAs
+      if (rank == 0) mbar_expect_tx(fb, 2u * (uint32_t)nv * (kTileA + b_bytes));
+      const uint32_t cfb = map_to_rank(fb, 0);
+      for (int q = 0; q < nv; ++q) {
+        const int kc = (c + q) * kChunk;
+        if (SPLIT) {
+          tma_load_4d(sbase + q * kTileA, &maps.b1, cfb, kc, rowA0, sc.pass, sc.i);
+          tma_load_4d(sbase + q * kTileA + kTileA / 2, &maps.b1, cfb, kc, rowA1, sc.pass, sc.i);
+        } else {
+          tma_load_4d(sbase + q * kTileA, &maps.a, cfb, kc, rowA0, sc.pass, sc.i);
+        }
+        // B half: slice j + rank, both planes (or plane `rank` of a lone slice j)
+        if (sc.two)
+          tma_load_4d(sbase + PP::kOffB + q * kTileB, &maps.b2, cfb, kc, rowB, 0, sc.j + (int)rank);
+        else
+          tma_load_4d(sbase + PP::kOffB + q * kTileB, &maps.b1, cfb, kc, rowB, (int)rank, sc.j);
+      }
+      ++it;
+    }
+  }
+  return true;
+}
+// CYC: tiles of the cyclic cover (tiles.cuh: a CTA's two row blocks may be
+// apart, blocks above the strip's diagonal are written transposed);
+// otherwise tiles of the aligned cover (256-row blocks: one 128-row load per
+// CTA, lower parts written in place).  Separate instantiations: the aligned
+// one keeps its load loop and epilogue free of the cyclic cover's cases.
+template <class PP, bool CYC>
 __global__ void __launch_bounds__(kThreads, 1)
     herk_emu_kernel(const __grid_constant__ SliceMaps maps, const Prob* __restrict__ probs,
                     const EmuTile* __restrict__ tiles, int n_tiles, const int* __restrict__ rexp,
@@ -296,7 +400,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const Abort ab{abort_word, map_to_rank(smem_u32(abort_word), rank ^ 1u), true};
-
+  if (warp < kDrainWarp0) {
+  // the first warpgroup gives registers up (its role code is dominated by this)
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsCtl));
   if (warp == 0) {
     // ---------------- TMA producer (both CTAs) ----------------
     if (lane == 0) {
@@ -305,7 +411,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int tile = pair; tile < n_tiles && ok; tile += n_pairs) {
         const EmuTile T = tiles[tile];
         const Prob P = probs[T.prob];
-        const int rowA = P.row_base + T.ib * 256 + (int)rank * 128, rowB = P.col_base + T.jb * 64;
+        const int rowB = P.col_base + T.jb * 64;
+        if constexpr (CYC) {
+          // this CTA's two 64-row blocks: one 128-row box when adjacent (the
+          // common case), else two 64-row boxes, each case a loop of its own
+          const int ra0 = rank ? T.rb[2] : T.rb[0], ra1 = rank ? T.rb[3] : T.rb[1];
+          const int rowA0 = P.row_base + ra0 * 64;
+          if (ra1 == ra0 + 1)
+            ok = produce_tile<false, PP>(maps, P, T, rowA0, 0, rowB, rank, n_slices, smem, bar0, it, ab);
+          else
+            ok = produce_tile<true, PP>(maps, P, T, rowA0, P.row_base + ra1 * 64, rowB, rank, n_slices, smem,
+                                        bar0, it, ab);
+          continue;
+        }
+        // aligned cover: this CTA's rows 128 rank .. 128 rank + 127 of the 256-row block
+        const int rowA = P.row_base + T.rb[0] * 64 + (int)rank * 128;
         Sched sc;
         for (bool more = sc.begin(units_of(P, T.split), n_slices); more && ok; more = sc.next()) {
           const uint32_t b_bytes = sc.two ? kTileB : kTileB / 2;
@@ -396,9 +516,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       // CTA 1: its TMEM is written until CTA 0's last MMA completes
       mbar_wait_bounded(drain_bar, 0);
     }
+  }
   } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsDrain));
     // ---------------- drain + epilogue (256 threads per CTA) ----------------
-    const int ew = warp - 2;
+    const int ew = warp - kDrainWarp0;
     const int q = warp & 3;       // TMEM lane quadrant this warp may access
     const int h = ew >> 2;        // 0: Re, 1: Im
     const int m = q * 32 + lane;  // row within this CTA's 128 rows
@@ -464,9 +586,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int n = 0; n < 64; ++n) acc[n] += __ldcg(other + n * 32);
         }
       }
-      // write the lower-triangle part of this CTA's rows of the tile
+      // write this thread's row of the tile: in place below the strip's
+      // diagonal (on and below it in the diagonal block), conjugate-
+      // transposed into the lower triangle above it.  Element n of the row
+      // goes to offset o_n, o_{n+1} = o_n + step_n, step_{n+1} = step_n + dstep.
+      if constexpr (CYC) {
+        write_tile_row(T, P, rank, m, h, acc, rexp, frac);
+        continue;
+      }
+      // aligned cover: this thread's row of the 256-row block, in place, on
+      // and below the diagonal (blocks above it are computed, not written)
       const int64_t ng = P.n_g;
-      const int64_t gr = (int64_t)T.ib * 256 + (int64_t)rank * 128 + m;
+      const int64_t gr = (int64_t)T.rb[0] * 64 + (int64_t)rank * 128 + m;
       if (gr < ng) {
         const int er = rexp[P.row_base + gr];
         double* outd = reinterpret_cast<double*>(P.out);
@@ -529,12 +660,14 @@ cudaError_t herk_emu_init() {
   std::lock_guard<std::mutex> lk(g_state_mutex);
   if (g_state[dev].ready) return cudaSuccess;
   const size_t smem = PipeShallow::kSmemBytes;
-  e = cudaFuncSetAttribute(herk_emu_kernel<PipeShallow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(herk_emu_kernel<PipeDeep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)PipeDeep::kSmemBytes);
-  if (e != cudaSuccess) return e;
+  for (auto k : {herk_emu_kernel<PipeShallow, false>, herk_emu_kernel<PipeShallow, true>}) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  for (auto k : {herk_emu_kernel<PipeDeep, false>, herk_emu_kernel<PipeDeep, true>}) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipeDeep::kSmemBytes);
+    if (e != cudaSuccess) return e;
+  }
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
@@ -550,10 +683,10 @@ cudaError_t herk_emu_init() {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int n = 0, nd = 0;
-  e = cudaOccupancyMaxActiveClusters(&n, herk_emu_kernel<PipeShallow>, &cfg);
+  e = cudaOccupancyMaxActiveClusters(&n, herk_emu_kernel<PipeShallow, false>, &cfg);
   if (e != cudaSuccess) return e;
   cfg.dynamicSmemBytes = PipeDeep::kSmemBytes;
-  e = cudaOccupancyMaxActiveClusters(&nd, herk_emu_kernel<PipeDeep>, &cfg);
+  e = cudaOccupancyMaxActiveClusters(&nd, herk_emu_kernel<PipeDeep, false>, &cfg);
   if (e != cudaSuccess) return e;
   if (n < 1 || nd < 1) return cudaErrorInvalidConfiguration;
   g_state[dev].max_pairs = std::min(n, nd);  // one pair per 2 SMs in both shapes
@@ -569,7 +702,8 @@ int herk_emu_pairs(int busy_sms) {
 
 cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuTile* tiles,
                             int n_tiles, const int* rexp, int n_slices, int frac, int* err,
-                            int busy_sms, const SplitScratch& split, bool deep, cudaStream_t st) {
+                            int busy_sms, const SplitScratch& split, bool deep, bool cyclic,
+                            cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   if (n_slices < 1 || n_slices > kMaxS || frac < 40 || frac > 50) return cudaErrorInvalidValue;
   cudaError_t e = herk_emu_init();
@@ -593,12 +727,9 @@ cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuT
   cfg.stream = st;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (deep)
-    e = cudaLaunchKernelEx(&cfg, herk_emu_kernel<PipeDeep>, maps, probs, tiles, n_tiles, rexp, n_slices,
-                           frac, err, split);
-  else
-    e = cudaLaunchKernelEx(&cfg, herk_emu_kernel<PipeShallow>, maps, probs, tiles, n_tiles, rexp,
-                           n_slices, frac, err, split);
+  auto k = deep ? (cyclic ? herk_emu_kernel<PipeDeep, true> : herk_emu_kernel<PipeDeep, false>)
+                : (cyclic ? herk_emu_kernel<PipeShallow, true> : herk_emu_kernel<PipeShallow, false>);
+  e = cudaLaunchKernelEx(&cfg, k, maps, probs, tiles, n_tiles, rexp, n_slices, frac, err, split);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -44,11 +44,12 @@ def alloc_out(ng, layout, host=False):
 
 def run_hs(p, precision, layout=fl.LAYOUT_LOWER_FULL, operands=fl.OPERANDS_FROM_AB, n_slices=7,
            T=None, h=None, AB=None, use_graph=0, tile_order=0, s_method=fl.S_CONTRACTION,
-           h_method=fl.H_FACTORED, pipeline=0):
+           h_method=fl.H_FACTORED, pipeline=0, tile_cover=0):
     """build_AB + build_HS; returns (handle, [H_k], [S_k]) as device tensors."""
     opt = fl.default_options(precision=precision, layout=layout, operands=operands,
                              n_slices=n_slices, use_graph=use_graph, tile_order=tile_order,
-                             s_method=s_method, h_method=h_method, pipeline=pipeline)
+                             s_method=s_method, h_method=h_method, pipeline=pipeline,
+                             tile_cover=tile_cover)
     if h is None:
         h = fl.from_problem(p, opt)
     else:

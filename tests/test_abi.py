@@ -141,7 +141,7 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
     with pytest.raises(fl.FlapwError):
         fl.hs_create(p.lattice, p.pos_frac, p.atom_type, p.mt_radius, 4, p.k_frac, p.kmax, bad)
     # option values outside their ranges are rejected before any device work
-    for kw in (dict(pipeline=3), dict(h_method=2), dict(s_method=2), dict(tile_order=8),
+    for kw in (dict(pipeline=3), dict(h_method=2), dict(s_method=2), dict(tile_order=7), dict(tile_cover=3),
                dict(operands=fl.OPERANDS_FROM_AB, s_method=fl.S_LEGENDRE)):
         with pytest.raises(fl.FlapwError) as e:
             fl.hs_create(p.lattice, p.pos_frac, p.atom_type, p.mt_radius, 4, p.k_frac, p.kmax,
@@ -158,10 +158,11 @@ def test_structs_match_header_layout(tmp_path):
 #include "flapw.h"
 int main(void) {
   printf("%zu %zu\\n", sizeof(flapw_options), sizeof(flapw_stats));
-  printf("%zu %zu %zu\\n", offsetof(flapw_options, tile_order), offsetof(flapw_options, s_method),
-         offsetof(flapw_options, reserved));
-  printf("%zu %zu %zu %zu\\n", offsetof(flapw_stats, flops_tensor), offsetof(flapw_stats, k_total),
-         offsetof(flapw_stats, graph_replays), offsetof(flapw_stats, ms_s));
+  printf("%zu %zu %zu %zu\\n", offsetof(flapw_options, tile_order), offsetof(flapw_options, s_method),
+         offsetof(flapw_options, tile_cover), offsetof(flapw_options, reserved));
+  printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(flapw_stats, flops_tensor), offsetof(flapw_stats, k_total),
+         offsetof(flapw_stats, graph_replays), offsetof(flapw_stats, tile_cover),
+         offsetof(flapw_stats, pipeline), offsetof(flapw_stats, ms_s));
   return 0;
 }
 """)
@@ -171,7 +172,8 @@ int main(void) {
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
     vals = [int(v) for v in out]
     assert vals[0] == ctypes.sizeof(fl.Options) and vals[1] == ctypes.sizeof(fl.Stats)
-    assert vals[2:5] == [fl.Options.tile_order.offset, fl.Options.s_method.offset,
-                         fl.Options.reserved.offset]
-    assert vals[5:9] == [fl.Stats.flops_tensor.offset, fl.Stats.k_total.offset,
-                         fl.Stats.graph_replays.offset, fl.Stats.ms_s.offset]
+    assert vals[2:6] == [fl.Options.tile_order.offset, fl.Options.s_method.offset,
+                         fl.Options.tile_cover.offset, fl.Options.reserved.offset]
+    assert vals[6:12] == [fl.Stats.flops_tensor.offset, fl.Stats.k_total.offset,
+                          fl.Stats.graph_replays.offset, fl.Stats.tile_cover.offset,
+                          fl.Stats.pipeline.offset, fl.Stats.ms_s.offset]

@@ -53,9 +53,35 @@ def test_copied_elements_cover_the_lower_triangle(bench):
 def test_peaks_and_traffic_table(bench):
     bf16, bf16_sus, hbm, src = bench.peaks()
     assert bf16 > 0 and bf16_sus > 0 and hbm > 0 and src in ("measured", "fallback")
-    for (name, slices, s_method, h_method), v in bench.MEASURED_TRAFFIC.items():
+    for (name, slices, s_method, h_method, cover, order, pipe), v in bench.MEASURED_TRAFFIC.items():
         assert 4 <= slices <= 8 and s_method in ("contraction", "legendre")
-        assert h_method in ("factored", "alg3") and v > 0
+        assert h_method in ("factored", "alg3") and v["bytes"] > 0
+        assert cover in (1, 2) and 0 <= order <= 5 and pipe in (1, 2)
+        assert len(v["kernel_sha"]) == 16
+    # a capture is reported only for the kernel sources it was taken on
+    key = next(iter(bench.MEASURED_TRAFFIC))
+    rec = bench.MEASURED_TRAFFIC[key]
+    if rec["kernel_sha"] == bench.kernel_source_hash():
+        assert bench.measured_traffic(*key) == rec["bytes"]
+    saved = rec["kernel_sha"]
+    rec["kernel_sha"] = "0" * 16
+    try:
+        assert bench.measured_traffic(*key) is None
+    finally:
+        rec["kernel_sha"] = saved
+
+
+def test_columns_from_lower_matches_full_matrix(bench):
+    import numpy as np
+    rng = np.random.default_rng(3)
+    ng = 37
+    X = rng.normal(size=(ng, ng)) + 1j * rng.normal(size=(ng, ng))
+    X = X + X.conj().T
+    cols = np.array([0, 5, 36])
+    full = X.T.reshape(-1)                      # full layout, column-major
+    packed = np.concatenate([X[j:, j] for j in range(ng)])
+    assert np.allclose(bench.columns_from_lower(full, ng, 0, cols), X[:, cols].T)
+    assert np.allclose(bench.columns_from_lower(packed, ng, 1, cols), X[:, cols].T)
 
 
 class _Handle:

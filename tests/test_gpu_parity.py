@@ -222,7 +222,7 @@ def test_hs_config2_sampled_columns(precision, tol, operands):
 
 # --------------------------------------------- options: autotune, graph, host buffers
 
-def test_autotune_keeps_results_and_picks_an_order():
+def test_autotune_keeps_results_and_picks_a_configuration():
     p = inputs.config1()
     opt = fl.default_options(precision=fl.PREC_EMU)
     opt.autotune = 1
@@ -233,24 +233,95 @@ def test_autotune_keeps_results_and_picks_an_order():
     h.build_HS(p.T, p.atom_slot, p.U, A, B, [H], [S])
     h.sync()
     st = h.stats()
-    assert 0 <= st["tile_order"] <= 6
+    assert 0 <= st["tile_order"] <= 5 and st["tile_cover"] in (1, 2) and st["pipeline"] in (1, 2)
     Ho, So = oracle_hs(p)
     assert herm_relerr(lower_to_full(H, ng, 0), Ho) <= TOL_EMU
     assert herm_relerr(lower_to_full(S, ng, 0), So) <= TOL_EMU
+    # the next call runs with the tuned choice, and gives the same results
+    H2, S2 = alloc_out(ng, 0), alloc_out(ng, 0)
+    h.build_HS(p.T, p.atom_slot, p.U, A, B, [H2], [S2])
+    h.sync()
+    st2 = h.stats()
+    assert (st2["tile_order"], st2["tile_cover"], st2["pipeline"]) == \
+        (st["tile_order"], st["tile_cover"], st["pipeline"])
+    assert herm_relerr(lower_to_full(H2, ng, 0), Ho) <= TOL_EMU
 
 
-@pytest.mark.parametrize("order", range(7))
-def test_every_tile_order(order):
-    # the order only schedules the tiles: every one must give the oracle's H and S
-    # (2 k-points, ragged N_G, more row blocks than any band)
+AUTOTUNE_CHILD = r"""
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np, torch
+import paper_1712_07206_gb300 as fl
+from paper_1712_07206_gb300 import inputs
+p = inputs.small(int(sys.argv[2]), n_atoms=2, n_types=1, lmax=3, n_target=(int(sys.argv[3]),))
+opt = fl.default_options(precision=fl.PREC_EMU, operands=fl.OPERANDS_FACTORED)
+opt.autotune = 1
+h = fl.from_problem(p, opt)
+A = torch.zeros(h.ab_offset(1), dtype=torch.complex128, device="cuda")
+B = torch.zeros_like(A)
+h.build_AB(p.radial, A, B)
+ng = h.num_g(0)
+H = torch.zeros(ng * ng, dtype=torch.complex128, device="cuda")
+S = torch.zeros_like(H)
+h.build_HS(p.T, p.atom_slot, p.U, A, B, [H], [S])
+h.sync()
+st = h.stats()
+print(json.dumps([st["tile_cover"], st["tile_order"], st["pipeline"]]))
+"""
+
+
+def test_autotune_cache_file(tmp_path):
+    # FLAPW_AUTOTUNE_CACHE: a fresh process tunes a new shape and appends one
+    # line; another process with the same shape reads the choice back (no new
+    # line); a new shape appends a second line
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, FLAPW_AUTOTUNE_CACHE=str(cache))
+    child = tmp_path / "child.py"
+    child.write_text(AUTOTUNE_CHILD)
+
+    def run(seed, ng):
+        r = subprocess.run([sys.executable, str(child), root, str(seed), str(ng)], env=env,
+                           capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr
+        return json.loads(r.stdout.strip().splitlines()[-1])
+
+    c1 = run(5, 700)
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1
+    key, cover, order, pipe = lines[0].split()
+    assert [int(cover), int(order), int(pipe)] == c1
+    assert run(5, 700) == c1
+    assert len(cache.read_text().splitlines()) == 1
+    run(6, 1500)
+    assert len(cache.read_text().splitlines()) == 2
+
+
+@pytest.mark.parametrize("cover", [1, 2])
+@pytest.mark.parametrize("order", range(6))
+def test_every_tile_order(order, cover):
+    # the order only schedules the tiles of a cover; the cyclic cover writes
+    # the blocks above a strip's diagonal conjugate-transposed, the aligned one
+    # computes 256-row blocks and writes their lower parts: every combination
+    # must give the oracle's H and S (2 k-points, ragged N_G, an even and an
+    # odd number of 64-row blocks, more row blocks than any band)
     p = inputs.small(19, n_atoms=3, n_types=2, lmax=4, n_target=(2300, 700))
-    h, Hs, Ss, _ = run_hs(p, fl.PREC_EMU, operands=fl.OPERANDS_FACTORED, tile_order=order + 1)
-    assert h.stats()["tile_order"] == order
+    opt = fl.default_options(precision=fl.PREC_EMU, operands=fl.OPERANDS_FACTORED, tile_order=order + 1,
+                             tile_cover=cover)
+    h = fl.from_problem(p, opt)
+    h, Hs, Ss, _ = run_hs(p, fl.PREC_EMU, operands=fl.OPERANDS_FACTORED, tile_order=order + 1, h=h,
+                          tile_cover=cover)
+    st = h.stats()
+    assert st["tile_order"] == order and st["tile_cover"] == cover
     for k in range(p.n_k):
         Ho, So = oracle_hs(p, k)
         ng = Ho.shape[0]
-        assert herm_relerr(lower_to_full(Hs[k], ng, 0), Ho) <= TOL_EMU, (order, k)
-        assert herm_relerr(lower_to_full(Ss[k], ng, 0), So) <= TOL_EMU, (order, k)
+        assert herm_relerr(lower_to_full(Hs[k], ng, 0), Ho) <= TOL_EMU, (order, cover, k)
+        assert herm_relerr(lower_to_full(Ss[k], ng, 0), So) <= TOL_EMU, (order, cover, k)
 
 
 @pytest.mark.parametrize("h_method", [fl.H_FACTORED, fl.H_ALG3])
