@@ -119,7 +119,17 @@ typedef struct flapw_options {
                      64 x 64 block is computed once), 2 aligned (256-row blocks
                      aligned to 256; the upper parts of diagonal tiles are computed
                      and not written); results agree to rounding */
-  int reserved[5];
+  int wait_us;    /* bound of each device-side wait of the tensor-core kernels, in
+                     microseconds (0: the default, 4 s).  A wait that runs out stops
+                     the kernel cleanly (no fault) and the next flapw_sync() returns
+                     FLAPW_ERR_TIMEOUT; the results of that call are invalid and the
+                     handle stays usable.  Small values exist to test that path. */
+  int mem_cap_mb; /* cap on the device workspace this handle allocates, in MiB (0: no
+                     cap).  A call whose workspaces would pass it returns
+                     FLAPW_ERR_OOM before enqueueing anything; what the handle holds
+                     stays owned by it (freed by flapw_destroy) and a later call
+                     under a larger cap proceeds. */
+  int reserved[3];
 } flapw_options;
 
 typedef struct flapw_stats {
@@ -248,15 +258,21 @@ int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const i
  *   sigma[K] (host): +1/-1 per row, or NULL for all +1.
  *   H: device, complex128, lower triangle in `layout` (ld = ldh for the full
  *      layout, ldh >= N).  n_slices 4..8 (0 = 7).  stream: the caller's stream.
- * Size limit: about 44 bytes per N x K entry (7 slices) plus small tables
- * must fit in the 64 MiB array, e.g. N = 1024 with K = 1400; larger problems
- * return FLAPW_ERR_UNSUPPORTED before any work is enqueued.
+ * Size limit: K below 131072, and about 44 bytes per N x K entry (7 slices)
+ * plus small tables must fit in the 64 MiB array, e.g. N = 1024 with
+ * K = 1400; larger problems return FLAPW_ERR_UNSUPPORTED before any work is
+ * enqueued.  sigma and the problem's sizes reach the device in kernel
+ * arguments: nothing of the caller's host memory is read after the call
+ * returns.
  * The first call on each device looks the array's device address up
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Calls share the array and it keeps the last
  * call's contents; calls whose work overlaps on the GPU race.  Errors are
- * reported by the return code only (FLAPW_ERR_ARG, FLAPW_ERR_UNSUPPORTED,
- * FLAPW_ERR_CUDA); a bounded device wait that runs out is not reported. */
+ * reported by the return code (FLAPW_ERR_ARG, FLAPW_ERR_UNSUPPORTED,
+ * FLAPW_ERR_CUDA) with a message for flapw_last_error(NULL).  A bounded
+ * device wait that runs out (the GPU stalled for seconds) is not reported:
+ * H is then invalid, and a caller that must know checks H itself (its
+ * diagonal is real, and non-negative when every sigma is +1). */
 int flapw_herk_noalloc(const void* Z, int64_t ldz, int K, int N, const int* sigma, void* H,
                        int64_t ldh, int layout, int n_slices, void* stream);
 

@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
                 ("operands", ctypes.c_int), ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("tile_order", ctypes.c_int), ("s_method", ctypes.c_int), ("h_method", ctypes.c_int),
                 ("pipeline", ctypes.c_int), ("tile_cover", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("wait_us", ctypes.c_int), ("mem_cap_mb", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class Stats(ctypes.Structure):

@@ -24,10 +24,20 @@ namespace {
 thread_local std::string g_last_error;  // errors of calls without a handle, per thread
 constexpr int kNumTileOrders = cover::kNumOrders;  // emulated tile orders (tiles.cuh)
 
+// Device bytes a handle's workspaces hold, against its cap
+// (options.mem_cap_mb, 0 for none).  A handle's calls make theirs the calling
+// thread's current budget (BudgetScope); workspaces allocated then count
+// against it until they are freed.
+struct Budget {
+  size_t cap = 0, used = 0;
+};
+thread_local Budget* g_budget = nullptr;
+
 // Device buffer that grows on demand.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  Budget* budget = nullptr;  // the budget it counts against
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
@@ -36,14 +46,18 @@ struct DevBuf {
     if (p) {
       cudaFree(p);
       (void)cudaGetLastError();
+      if (budget) budget->used -= bytes;
     }
     p = nullptr;
     bytes = 0;
+    budget = nullptr;
   }
   cudaError_t ensure(size_t n) {
     if (n <= bytes && p) return cudaSuccess;
     release();
     if (n == 0) n = 16;
+    Budget* b = g_budget;
+    if (b && b->cap && b->used + n > b->cap) return cudaErrorMemoryAllocation;  // over the cap
     cudaError_t e = cudaMalloc(&p, n);
     if (e != cudaSuccess) {
       p = nullptr;
@@ -51,6 +65,8 @@ struct DevBuf {
       return e;
     }
     bytes = n;
+    budget = b;
+    if (b) b->used += n;
     return cudaSuccess;
   }
   template <class T>
@@ -99,6 +115,7 @@ void set_thread_error(const char* msg) { g_last_error = msg ? msg : ""; }
 struct flapw_ctx {
   std::string err;
   flapw_options opt{};
+  Budget budget;  // declared before the workspaces, which count against it
   bool engine_only = false;
   int device = 0;
   int num_sms = 0;
@@ -138,7 +155,12 @@ struct flapw_ctx {
   int opmap_kp = 0;
   DevBuf d_T, d_work, d_CH, d_fac, d_cnt, d_slot, d_U, d_off, d_probs, d_rowprob, d_Z, d_SL, d_rexp,
       d_emu_tiles, d_f64_tiles, d_combo, d_kmap, d_stageA, d_stageB, d_stageOut;
-  PinBuf pin_in, pin_probs;
+  // pinned inputs of build_HS: two slots, each guarded by an event recorded
+  // after the copies that read it (graph replays use slot 0 only)
+  PinBuf pin_ring[2], pin_probs_ring[2];
+  cudaEvent_t pin_ev[2]{};
+  bool pin_ev_used[2]{};
+  int pin_slot = 0;
   int64_t k_alloc = 0, rows = 0;
   int64_t k_terms = 0;           // most products summed into one output element
   int n_emu_tiles = 0, n_f64_tiles = 0, split_emu = 0, split_f64 = 0, tiles_order = -1;
@@ -189,11 +211,23 @@ struct flapw_ctx {
     if (aux_stream) cudaStreamDestroy(aux_stream);
     if (copy_stream) cudaStreamDestroy(copy_stream);
     if (ev_copy) cudaEventDestroy(ev_copy);
+    for (auto& e : pin_ev)
+      if (e) cudaEventDestroy(e);
     (void)cudaGetLastError();
   }
 };
 
 namespace {
+
+// Makes the handle's budget current for the calling thread during one call.
+struct BudgetScope {
+  Budget* prev;
+  explicit BudgetScope(flapw_ctx* h) : prev(g_budget) {
+    h->budget.cap = (size_t)h->opt.mem_cap_mb << 20;
+    g_budget = &h->budget;
+  }
+  ~BudgetScope() { g_budget = prev; }
+};
 
 int fail(flapw_ctx* h, int code, const std::string& msg) {
   if (h) h->err = msg;
@@ -231,6 +265,8 @@ int check_options(flapw_ctx* h, const flapw_options& o) {
     return fail(h, FLAPW_ERR_ARG, "options.h_method is not a FLAPW_H_* value");
   if (o.pipeline < 0 || o.pipeline > 2) return fail(h, FLAPW_ERR_ARG, "options.pipeline must be in 0..2");
   if (o.tile_cover < 0 || o.tile_cover > 2) return fail(h, FLAPW_ERR_ARG, "options.tile_cover must be in 0..2");
+  if (o.wait_us < 0) return fail(h, FLAPW_ERR_ARG, "options.wait_us must be >= 0");
+  if (o.mem_cap_mb < 0) return fail(h, FLAPW_ERR_ARG, "options.mem_cap_mb must be >= 0");
   return FLAPW_OK;
 }
 
@@ -252,6 +288,7 @@ int device_setup(flapw_ctx* h) {
   CK(h, cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking), "cudaStreamCreate");
   CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
   CK(h, cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming), "cudaEventCreate");
+  for (auto& e : h->pin_ev) CK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
   CK(h, opform_init(), "constant table upload");
   return FLAPW_OK;
 }
@@ -386,6 +423,10 @@ struct Half {
   int emu_t0, emu_nt, f64_t0, f64_nt;
 };
 
+// Bound of the tensor-core kernels' abortable device waits: options.wait_us,
+// or 0 for the kernels' default (4 s).
+unsigned long long wait_ns(const flapw_ctx* h) { return (unsigned long long)h->opt.wait_us * 1000ull; }
+
 // The contraction's pipeline shape: the option, or by size.
 bool use_deep_pipe(const flapw_ctx* h) {
   if (h->opt.autotune && h->pipe_choice) return h->pipe_choice == 2;
@@ -420,7 +461,7 @@ int enqueue_contraction(flapw_ctx* h, const Half& hf, int busy_sms, cudaStream_t
     CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf.emu_t0,
                           hf.emu_nt, h->d_rexp.as<int>(), s, fixed_frac_bits(h->k_terms),
                           h->d_cnt.as<int>() + 2, busy_sms, sp, use_deep_pipe(h),
-                          h->tiles_cover == cover::kCoverCyclic, st),
+                          h->tiles_cover == cover::kCoverCyclic, wait_ns(h), st),
        "emulated contraction launch");
   } else {
     if (ev_sl >= 0) CK(h, cudaEventRecord(h->ev[ev_sl], st), "cudaEventRecord");
@@ -484,8 +525,8 @@ int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int6
     make_tiles(probs, n_first, (int)probs.size(), order, cover_opt, ps, &emu, &f64, &ids_second, pp);
     h->n_emu_tiles = (int)emu.size();
     h->n_f64_tiles = (int)f64.size();
-    if (upload(h, h->d_emu_tiles, emu)) return FLAPW_ERR_CUDA;
-    if (upload(h, h->d_f64_tiles, f64)) return FLAPW_ERR_CUDA;
+    if (int rc_up = upload(h, h->d_emu_tiles, emu)) return rc_up;
+    if (int rc_up = upload(h, h->d_f64_tiles, f64)) return rc_up;
     // the halves run one after the other on one stream: they share the scratch
     h->split_ids = std::max(ids_first, ids_second);
     CK(h, h->d_split.ensure(split_scratch_bytes(std::max(1, h->split_ids))), "split-tile scratch");
@@ -611,7 +652,7 @@ int autotune_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, in
         CK(h, launch_herk_emu(h->tmap, h->d_probs.as<Prob>(), h->d_emu_tiles.as<EmuTile>() + hf->emu_t0,
                               hf->emu_nt, h->d_rexp.as<int>(), s, fixed_frac_bits(h->k_terms),
                               h->d_cnt.as<int>() + 2, 0, sp, use_deep_pipe(h),
-                              h->tiles_cover == cover::kCoverCyclic, st),
+                              h->tiles_cover == cover::kCoverCyclic, wait_ns(h), st),
            "emulated contraction launch");
       }
       CK(h, cudaEventRecord(h->ev[15], st), "cudaEventRecord");
@@ -858,6 +899,7 @@ static int prepare_prep(flapw_ctx* h, cudaStream_t st) {
 int flapw_build_AB(flapw_handle h, const double* radial, void* A, void* B, void* stream) {
   (void)cudaGetLastError();  // a stale error of unrelated code must not fail our launch checks
   if (!h || !radial || !A || !B) return fail(h, FLAPW_ERR_ARG, "NULL argument");
+  BudgetScope budget_scope(h);
   if (h->engine_only) return fail(h, FLAPW_ERR_STATE, "handle has no crystal");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t nrad = (size_t)h->n_types * (h->lmax + 1) * 4;
@@ -906,6 +948,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
                    void* const* S, void* stream) {
   (void)cudaGetLastError();  // a stale error of unrelated code must not fail our launch checks
   if (!h || !T || !atom_slot || !U || !H || !S) return fail(h, FLAPW_ERR_ARG, "NULL argument");
+  BudgetScope budget_scope(h);
   if (h->engine_only) return fail(h, FLAPW_ERR_STATE, "handle has no crystal");
   const bool factored = h->opt.operands == FLAPW_OPERANDS_FACTORED;
   if (!factored && (!A || !B)) return fail(h, FLAPW_ERR_ARG, "A and B are required with FLAPW_OPERANDS_FROM_AB");
@@ -946,7 +989,6 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   }
   const int n_combo = (int)combo_slot.size();
   const size_t cmb_ints = combo_slot.size() * 2 + combo_atoms.size() + combo_start.size();
-  CK(h, h->pin_in.ensure(t_bytes + slot_bytes + u_bytes + cmb_ints * 4 + 256), "cudaMallocHost");
 
   // outputs: problem k = H of k-point k, problem nk + k = S of k-point k
   OutPlan op;
@@ -1014,7 +1056,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       start.push_back((int)ta.size());
     }
     ta.insert(ta.end(), start.begin(), start.end());
-    if (upload(h, h->d_typeatoms, ta)) return FLAPW_ERR_CUDA;
+    if (int rc_up = upload(h, h->d_typeatoms, ta)) return rc_up;
     CK(h, h->d_khat.ensure((size_t)h->g_total * 3 * 8), "workspace");
     Geom geo{h->n_atoms, h->n_types, h->lmax, h->n_L, h->n_k, h->g_total,
              h->d_rec.as<double>(), h->d_pos.as<double>(), h->d_type.as<int>(),
@@ -1052,7 +1094,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
                                                        [](const OpTile& x, const OpTile& y) {
                                                          return x.combo == y.combo && x.rb == y.rb && x.gb == y.gb;
                                                        })) {
-      if (upload(h, h->d_optiles, tl)) return FLAPW_ERR_CUDA;
+      if (int rc_up = upload(h, h->d_optiles, tl)) return rc_up;
       h->optiles = tl;
     }
     if (h->opmap_a_base != h->d_opSLA.p || h->opmap_a_rows != op_rows_a || h->opmap_kp != op_kp ||
@@ -1085,7 +1127,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
         rp[probs[q].row_base + g] = q;
         rp[probs[q].col_base + g] = q;
       }
-    if (upload(h, h->d_rowprob, rp)) return FLAPW_ERR_CUDA;
+    if (int rc_up = upload(h, h->d_rowprob, rp)) return rc_up;
   }
   // H to host memory: the H contraction in two launches split by columns, the
   // first part's columns copied while the second runs (not with the autotuner,
@@ -1119,15 +1161,27 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   hS.row0 = s_row0;
   hS.nrows = h->g_total;
   if (int rc = ensure_slices(h)) return rc;
-  CK(h, h->pin_probs.ensure(sizeof(Prob) * probs.size()), "cudaMallocHost");
   if (factored && !h->prep_valid) {
     if (int rc = prepare_prep(h, user_st)) return rc;
   }
 
-  // pinned inputs: earlier launches may still read them
-  if (h->last_stream) CK(h, cudaStreamSynchronize(h->last_stream), "cudaStreamSynchronize");
-  CK(h, cudaStreamSynchronize(h->aux_stream), "cudaStreamSynchronize");
-  char* pin = static_cast<char*>(h->pin_in.p);
+  // pinned inputs: a slot whose copies (enqueued two calls back) have run,
+  // so that the call returns after enqueueing; a graph replays the copies
+  // from slot 0, so that path waits for the previous call instead
+  int slot = 0;
+  if (h->opt.use_graph) {
+    if (h->last_stream) CK(h, cudaStreamSynchronize(h->last_stream), "cudaStreamSynchronize");
+    CK(h, cudaStreamSynchronize(h->aux_stream), "cudaStreamSynchronize");
+  } else {
+    slot = h->pin_slot;
+    h->pin_slot ^= 1;
+    if (h->pin_ev_used[slot]) CK(h, cudaEventSynchronize(h->pin_ev[slot]), "cudaEventSynchronize");
+  }
+  PinBuf& pin_in = h->pin_ring[slot];
+  PinBuf& pin_probs = h->pin_probs_ring[slot];
+  CK(h, pin_in.ensure(t_bytes + slot_bytes + u_bytes + cmb_ints * 4 + 256), "cudaMallocHost");
+  CK(h, pin_probs.ensure(sizeof(Prob) * probs.size()), "cudaMallocHost");
+  char* pin = static_cast<char*>(pin_in.p);
   std::memcpy(pin, T, t_bytes);
   std::memcpy(pin + t_bytes, atom_slot, slot_bytes);
   std::memcpy(pin + t_bytes + slot_bytes, U, u_bytes);
@@ -1136,7 +1190,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   std::memcpy(pc + n_combo, combo_type.data(), combo_type.size() * 4);
   std::memcpy(pc + 2 * n_combo, combo_atoms.data(), combo_atoms.size() * 4);
   std::memcpy(pc + 2 * n_combo + combo_atoms.size(), combo_start.data(), combo_start.size() * 4);
-  std::memcpy(h->pin_probs.p, probs.data(), sizeof(Prob) * probs.size());
+  std::memcpy(pin_probs.p, probs.data(), sizeof(Prob) * probs.size());
   h->last_n_slots = n_slots;
   h->last_alg3 = alg3;
 
@@ -1150,7 +1204,11 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     CK(h, cudaMemcpyAsync(h->d_slot.p, pin + t_bytes, slot_bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
     CK(h, cudaMemcpyAsync(h->d_slot.as<char>() + slot_bytes, pc, cmb_ints * 4, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
     CK(h, cudaMemcpyAsync(h->d_U.p, pin + t_bytes + slot_bytes, u_bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
-    CK(h, cudaMemcpyAsync(h->d_probs.p, h->pin_probs.p, sizeof(Prob) * probs.size(), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    CK(h, cudaMemcpyAsync(h->d_probs.p, pin_probs.p, sizeof(Prob) * probs.size(), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    if (!h->opt.use_graph) {
+      CK(h, cudaEventRecord(h->pin_ev[slot], st), "cudaEventRecord");
+      h->pin_ev_used[slot] = true;
+    }
     if (stage_ab) {
       CK(h, cudaMemcpyAsync(h->d_stageA.p, A, ab_total * 16, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
       CK(h, cudaMemcpyAsync(h->d_stageB.p, B, ab_total * 16, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
@@ -1299,17 +1357,6 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
       if (int rc = enqueue_contraction(h, hS, n_slots, st, 3, 4)) return rc;
     }
-    // S outputs in host memory: copied back beside the H work, joined at the end
-    bool s_host = false;
-    for (int i = nk; i < 2 * nk; ++i) s_host = s_host || op.host[i] != nullptr;
-    if (s_host) {
-      CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev[4], 0), "cudaStreamWaitEvent");
-      for (int i = nk; i < 2 * nk; ++i)
-        if (op.host[i])
-          CK(h, copy_out(op.host[i], op.dev[i], h->goff[i - nk + 1] - h->goff[i - nk], layout, 0,
-                         h->goff[i - nk + 1] - h->goff[i - nk], h->copy_stream),
-             "cudaMemcpy2DAsync");
-    }
     // join, then H
     CK(h, cudaStreamWaitEvent(st, h->ev[16], 0), "cudaStreamWaitEvent");
     CK(h, cudaEventRecord(h->ev[8], st), "cudaEventRecord");
@@ -1338,7 +1385,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       ga.alg3_nl = alg3 ? h->n_L : 0;
       ga.r_row0 = h->g_total;
       CK(h, launch_opgemm(h->opmap_a, h->opmap_b, ga, h->d_optiles.as<OpTile>(), (int)h->optiles.size(),
-                          cnt + 2, h->num_sms, st),
+                          cnt + 2, h->num_sms, wait_ns(h), st),
          "H operand launch");
       if (alg3) {
         CK(h, launch_opgemm_phase(ga, n_combo, st), "H operand phase launch");
@@ -1358,8 +1405,23 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     const bool h_presliced = tc_ops && !alg3;
     if (!h_presliced) CK(h, cudaEventRecord(h->ev[10], st), "cudaEventRecord");
     if (int rc = enqueue_contraction(h, hH, 0, st, 11, h_split ? 18 : 12, h_presliced)) return rc;
-    // H outputs in host memory: with the split, columns [0, c1) go back while
-    // the second part runs, the rest after it
+    if (h_split)
+      if (int rc = enqueue_contraction(h, hHb, 0, st, -1, 12, true)) return rc;
+    // Host-memory outputs go back on the copy stream: S beside the H work; with
+    // the split H contraction, columns [0, c1) of H while its second part runs,
+    // the rest after it.  Every copy is enqueued after all the compute, so that
+    // a long copy queue (many k-points) cannot hold the host back from
+    // enqueueing the H work; each waits for the contraction that writes it.
+    bool s_host = false;
+    for (int i = nk; i < 2 * nk; ++i) s_host = s_host || op.host[i] != nullptr;
+    if (s_host) {
+      CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev[4], 0), "cudaStreamWaitEvent");
+      for (int i = nk; i < 2 * nk; ++i)
+        if (op.host[i])
+          CK(h, copy_out(op.host[i], op.dev[i], h->goff[i - nk + 1] - h->goff[i - nk], layout, 0,
+                         h->goff[i - nk + 1] - h->goff[i - nk], h->copy_stream),
+             "cudaMemcpy2DAsync");
+    }
     auto h_c1 = [&](int k) -> int64_t {
       const int64_t ng = h->goff[k + 1] - h->goff[k];
       return h_split ? std::min<int64_t>(ng, 64 * (int64_t)h_split_block((int)ng)) : 0;
@@ -1371,7 +1433,6 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
           CK(h, copy_out(op.host[k], op.dev[k], h->goff[k + 1] - h->goff[k], layout, 0, h_c1(k),
                          h->copy_stream),
              "cudaMemcpy2DAsync");
-      if (int rc = enqueue_contraction(h, hHb, 0, st, -1, 12, true)) return rc;
     }
     if (h_host) CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev[12], 0), "cudaStreamWaitEvent");
     for (int k = 0; k < nk; ++k)
@@ -1400,7 +1461,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   std::vector<uintptr_t> key{(uintptr_t)A, (uintptr_t)B, (uintptr_t)n_slots, (uintptr_t)h->opt.precision,
                              (uintptr_t)h->opt.s_method, (uintptr_t)h->opt.h_method,
                              (uintptr_t)layout, (uintptr_t)h->opt.operands, (uintptr_t)slices_of(h),
-                             (uintptr_t)h->d_Z.p, (uintptr_t)h->d_SL.p, (uintptr_t)h->pin_in.p,
+                             (uintptr_t)h->d_Z.p, (uintptr_t)h->d_SL.p, (uintptr_t)h->pin_ring[0].p,
                              (uintptr_t)h->d_T.p, (uintptr_t)h->d_stageOut.p, (uintptr_t)h->d_emu_tiles.p,
                              (uintptr_t)h->d_opA.p, (uintptr_t)h->d_opB.p, (uintptr_t)h->d_opSLA.p,
                              (uintptr_t)h->d_opSLB.p, (uintptr_t)h->d_oprexp.p, (uintptr_t)h->d_optiles.p,
@@ -1438,6 +1499,7 @@ int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const i
                void* H, int64_t ldh, void* stream) {
   (void)cudaGetLastError();  // a stale error of unrelated code must not fail our launch checks
   if (!h || !Z || !H) return fail(h, FLAPW_ERR_ARG, "NULL argument");
+  BudgetScope budget_scope(h);
   if (K < 1 || N < 1 || ldz < K) return fail(h, FLAPW_ERR_ARG, "need K >= 1, N >= 1, ldz >= K");
   if (K >= (1 << 17)) return fail(h, FLAPW_ERR_UNSUPPORTED, "K must be below 131072");
   if (h->opt.layout == FLAPW_LAYOUT_LOWER_FULL && ldh < N) return fail(h, FLAPW_ERR_ARG, "ldh < N");
@@ -1470,9 +1532,9 @@ int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const i
   h->deep_pipe = herk_emu_deep(N);
   h->max_ng = N;
   set_tile_order(h);
-  if (upload(h, h->d_kmap, kmap) || upload(h, h->d_probs, probs)) return FLAPW_ERR_CUDA;
+  if (int rc_up = upload(h, h->d_kmap, kmap) || upload(h, h->d_probs, probs)) return rc_up;
   std::vector<int> rp(N, 0);
-  if (upload(h, h->d_rowprob, rp)) return FLAPW_ERR_CUDA;
+  if (int rc_up = upload(h, h->d_rowprob, rp)) return rc_up;
   Half hf, none;
   h->tiles_rows_key = -1;
   if (int rc = ensure_tiles(h, probs, 1, -2 - (int64_t)N, &hf, &none)) return rc;

@@ -204,8 +204,10 @@ cudaError_t launch_opgemm_build_alg3(const double2* T, int n_slots, int n, int n
                                      double2* A, cudaStream_t st);
 // P for every tile (opgemm.cu), then every atom's operand rows from P (with
 // alg3_nl set: the L and R columns of Alg. 3).
+// wait_ns: bound of its abortable device waits (0: the default 4 s).
 cudaError_t launch_opgemm(const CUtensorMap& map_a, const CUtensorMap& map_b, const OpGemmArgs& g,
-                          const OpTile* tiles, int n_tiles, int* err, int max_ctas, cudaStream_t st);
+                          const OpTile* tiles, int n_tiles, int* err, int max_ctas,
+                          unsigned long long wait_ns, cudaStream_t st);
 cudaError_t launch_opgemm_phase(const OpGemmArgs& g, int n_combo, cudaStream_t st);
 // The same rows sliced directly (the factored, sigma-grouped layout only):
 // writes the contraction's slices SL (rows x k_alloc per plane) and the row
@@ -304,10 +306,12 @@ cudaError_t herk_emu_init();
 // where busy_sms is the number of SMs that concurrent work holds.  deep: the
 // pipeline of 5 one-chunk stages (large N_G) instead of 3 two-chunk stages.
 // cyclic: the tiles are of the cyclic cover (tiles.cuh), else of the aligned one.
+// wait_ns: bound of each abortable device wait (0: the default 4 s); a wait
+// that runs out sets *err to FLAPW_ERR_TIMEOUT and the pair stops.
 cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuTile* tiles,
                             int n_tiles, const int* rexp, int n_slices, int frac, int* err,
                             int busy_sms, const SplitScratch& split, bool deep, bool cyclic,
-                            cudaStream_t st);
+                            unsigned long long wait_ns, cudaStream_t st);
 // The pair count a launch beside busy_sms busy SMs gets (0 before herk_emu_init).
 int herk_emu_pairs(int busy_sms);
 size_t herk_emu_smem_bytes(bool deep);

@@ -349,7 +349,8 @@ template <class PP, bool CYC>
 __global__ void __launch_bounds__(kThreads, 1)
     herk_emu_kernel(const __grid_constant__ SliceMaps maps, const Prob* __restrict__ probs,
                     const EmuTile* __restrict__ tiles, int n_tiles, const int* __restrict__ rexp,
-                    int n_slices, int frac, int* __restrict__ err, SplitScratch split) {
+                    int n_slices, int frac, int* __restrict__ err, SplitScratch split,
+                    unsigned long long wait_ns) {
   constexpr int kStages = PP::kStages;
   constexpr int kStageChunks = PP::kStageChunks;
   constexpr uint32_t kOffB = PP::kOffB;
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   cluster_sync();  // barriers initialised and TMEM allocated in both CTAs
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const Abort ab{abort_word, map_to_rank(smem_u32(abort_word), rank ^ 1u), true};
+  const Abort ab{abort_word, map_to_rank(smem_u32(abort_word), rank ^ 1u), true, wait_ns};
   if (warp < kDrainWarp0) {
   // the first warpgroup gives registers up (its role code is dominated by this)
   asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsCtl));
@@ -618,6 +619,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 
   // neither CTA leaves while the other may still touch its shared memory
+  settle_after_abort(ab);
   tc_fence_before();
   cluster_sync();
   if (warp == 1) {
@@ -703,7 +705,7 @@ int herk_emu_pairs(int busy_sms) {
 cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuTile* tiles,
                             int n_tiles, const int* rexp, int n_slices, int frac, int* err,
                             int busy_sms, const SplitScratch& split, bool deep, bool cyclic,
-                            cudaStream_t st) {
+                            unsigned long long wait_ns, cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   if (n_slices < 1 || n_slices > kMaxS || frac < 40 || frac > 50) return cudaErrorInvalidValue;
   cudaError_t e = herk_emu_init();
@@ -729,7 +731,8 @@ cudaError_t launch_herk_emu(const SliceMaps& maps, const Prob* probs, const EmuT
   cfg.numAttrs = 1;
   auto k = deep ? (cyclic ? herk_emu_kernel<PipeDeep, true> : herk_emu_kernel<PipeDeep, false>)
                 : (cyclic ? herk_emu_kernel<PipeShallow, true> : herk_emu_kernel<PipeShallow, false>);
-  e = cudaLaunchKernelEx(&cfg, k, maps, probs, tiles, n_tiles, rexp, n_slices, frac, err, split);
+  e = cudaLaunchKernelEx(&cfg, k, maps, probs, tiles, n_tiles, rexp, n_slices, frac, err, split,
+                         wait_ns ? wait_ns : kWaitNs);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

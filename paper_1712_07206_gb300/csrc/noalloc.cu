@@ -223,7 +223,7 @@ extern "C" int flapw_herk_noalloc(const void* Z, int64_t ldz, int K, int N, cons
   if (e == cudaSuccess) e = launch_slicer(Zs, k_alloc, prob, rowp, 0, N, 0, N, s, SL, rexp, st);
   if (e == cudaSuccess)
     e = launch_herk_emu(tmap, prob, tiles, n_tiles, rexp, s, fixed_frac_bits(K), err, 0,
-                        SplitScratch{nullptr, nullptr}, herk_emu_deep(N), /*cyclic*/ true, st);
+                        SplitScratch{nullptr, nullptr}, herk_emu_deep(N), /*cyclic*/ true, 0, st);
   if (e != cudaSuccess) return fail(FLAPW_ERR_CUDA, cudaGetErrorString(e));
   return FLAPW_OK;
 }

@@ -117,7 +117,7 @@ struct OpCursor {
 __global__ void __launch_bounds__(kThreads, 1)
     opgemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                   const OpGemmArgs g, const OpTile* __restrict__ tiles, int n_tiles,
-                  int* __restrict__ err) {
+                  int* __restrict__ err, unsigned long long wait_ns) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const Abort ab{abort_word, 0u, false};
+  const Abort ab{abort_word, 0u, false, wait_ns};
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -681,11 +681,13 @@ cudaError_t launch_opgemm_build_alg3(const double2* T, int n_slots, int n, int n
 }
 
 cudaError_t launch_opgemm(const CUtensorMap& map_a, const CUtensorMap& map_b, const OpGemmArgs& g,
-                          const OpTile* tiles, int n_tiles, int* err, int max_ctas, cudaStream_t st) {
+                          const OpTile* tiles, int n_tiles, int* err, int max_ctas,
+                          unsigned long long wait_ns, cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   if (g.kchunks < 1 || g.kchunks > kMaxKChunks) return cudaErrorInvalidValue;
   const int grid = std::max(1, std::min(n_tiles, max_ctas));
-  opgemm_kernel<<<grid, kThreads, opgemm_smem_bytes(), st>>>(map_a, map_b, g, tiles, n_tiles, err);
+  opgemm_kernel<<<grid, kThreads, opgemm_smem_bytes(), st>>>(map_a, map_b, g, tiles, n_tiles, err,
+                                                             wait_ns ? wait_ns : kWaitNs);
   return cudaGetLastError();
 }
 

@@ -10,7 +10,10 @@
 namespace flapw {
 namespace tc {
 
-constexpr unsigned long long kWaitNs = 4000000000ull;  // bound of every wait: 4 s
+// Default bound of the abortable waits (4 s; a kernel argument, settable per
+// handle) and fixed bound of the teardown waits, which wait for work that
+// was already issued.
+constexpr unsigned long long kWaitNs = 4000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -54,6 +57,7 @@ struct Abort {
   volatile int* local;
   uint32_t peer;
   bool has_peer;
+  unsigned long long limit_ns;  // bound of each abortable wait
   __device__ void raise() const {
     *local = 1;
     if (has_peer) asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer), "r"(1) : "memory");
@@ -69,11 +73,22 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const A
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 63) == 0) {
       if (*ab.local) return false;
-      if (global_ns() - t0 > kWaitNs) {
+      if (global_ns() - t0 > ab.limit_ns) {
         ab.raise();
         return false;
       }
     }
+  }
+}
+// After an abort, copies that one CTA of a pair issued may complete on its
+// peer's barrier, which nobody waits for: every thread of an aborted CTA
+// lets 20 us pass (far longer than a tile copy takes) before the pair's
+// closing barrier, so that nothing is still landing in shared memory when
+// the CTAs exit.
+__device__ __forceinline__ void settle_after_abort(const Abort& ab) {
+  if (!*ab.local) return;
+  const unsigned long long t0 = global_ns();
+  while (global_ns() - t0 < 20000ull) {
   }
 }
 // Wait that ignores the abort flags (teardown), still bounded.

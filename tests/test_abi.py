@@ -124,6 +124,14 @@ def test_herk_noalloc_rejects_bad_arguments_before_touching_the_device():
         rc = lib.flapw_herk_noalloc(a["Z"], a["ldz"], a["K"], a["N"], a["sigma"], a["H"], a["ldh"],
                                     a["layout"], a["n_slices"], None)
         assert rc == -1, change
+        # the message names the argument (the calling thread's handle-less error)
+        assert lib.flapw_last_error(None), change
+    # K at or above 2^17 is refused like the other contraction entry points
+    rc = lib.flapw_herk_noalloc(Z, 1 << 17, 1 << 17, 1, None, H, 1, fl.LAYOUT_LOWER_FULL, 0, None)
+    assert rc == -7
+    assert b"131072" in lib.flapw_last_error(None)
+    rc = lib.flapw_herk_noalloc(Z, 8, 8, 4, None, H, 3, fl.LAYOUT_LOWER_FULL, 0, None)
+    assert rc == -1 and b"ldh" in lib.flapw_last_error(None)
 
 
 def test_create_rejects_bad_arguments_before_touching_the_device():
@@ -142,6 +150,7 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
         fl.hs_create(p.lattice, p.pos_frac, p.atom_type, p.mt_radius, 4, p.k_frac, p.kmax, bad)
     # option values outside their ranges are rejected before any device work
     for kw in (dict(pipeline=3), dict(h_method=2), dict(s_method=2), dict(tile_order=7), dict(tile_cover=3),
+               dict(wait_us=-1), dict(mem_cap_mb=-1),
                dict(operands=fl.OPERANDS_FROM_AB, s_method=fl.S_LEGENDRE)):
         with pytest.raises(fl.FlapwError) as e:
             fl.hs_create(p.lattice, p.pos_frac, p.atom_type, p.mt_radius, 4, p.k_frac, p.kmax,

@@ -366,6 +366,39 @@ def test_graph_replay_matches(precision):
         assert herm_relerr(lower_to_full(Ss[k], ng, 0), So) <= tol
 
 
+@pytest.mark.parametrize("precision", [fl.PREC_FP64, fl.PREC_EMU])
+def test_back_to_back_build_hs_with_different_T(precision):
+    # build_HS returns after enqueueing: two calls with different T blocks on
+    # one handle and no synchronisation between them (the second stages its T
+    # in the other pinned slot while the first call's work runs); both must give
+    # their own oracle's H and S
+    import copy
+    p = inputs.small(29, n_atoms=3, n_types=2, lmax=4, n_target=(900, 420))
+    p2 = copy.deepcopy(p)
+    rng = np.random.default_rng(7)
+    n = p.T.shape[1]
+    for t in range(p2.T.shape[0]):
+        X = rng.uniform(-1, 1, (n, n)) + 1j * rng.uniform(-1, 1, (n, n))
+        p2.T[t] = p2.T[t] + 0.05 * (X + X.conj().T)
+    opt = fl.default_options(precision=precision, operands=fl.OPERANDS_FACTORED)
+    h = fl.from_problem(p, opt)
+    _, A, B = run_ab(p, h)
+    out = []
+    for q in (p, p2):
+        Hs = [alloc_out(h.num_g(k), 0) for k in range(q.n_k)]
+        Ss = [alloc_out(h.num_g(k), 0) for k in range(q.n_k)]
+        h.build_HS(q.T, q.atom_slot, q.U, A, B, Hs, Ss)
+        out.append((q, Hs, Ss))
+    h.sync()
+    tol = TOL_EMU if precision == fl.PREC_EMU else TOL_F64
+    for q, Hs, Ss in out:
+        for k in range(q.n_k):
+            Ho, So = oracle_hs(q, k)
+            ng = Ho.shape[0]
+            assert herm_relerr(lower_to_full(Hs[k], ng, 0), Ho) <= tol
+            assert herm_relerr(lower_to_full(Ss[k], ng, 0), So) <= tol
+
+
 def test_host_buffers_through_the_abi():
     torch = torch_cuda()
     p = inputs.config1()
