@@ -129,7 +129,20 @@ typedef struct flapw_options {
                      FLAPW_ERR_OOM before enqueueing anything; what the handle holds
                      stays owned by it (freed by flapw_destroy) and a later call
                      under a larger cap proceeds. */
-  int reserved[3];
+  int part_count; /* split of the job over independent callers, one per GPU and
+                     none communicating (0 or 1: no split).  See flapw_partition:
+                     whole k-points go to the parts when that balances, otherwise
+                     every part takes every part_count-th output tile of each
+                     k-point.  A part computes A, B and the operands of every
+                     k-point (they are cheap) and only its share of the
+                     contraction; H[k], S[k] of k-points of other parts may be
+                     NULL and are not touched.  With tiles split, a part writes its
+                     blocks of each lower triangle: device-memory outputs keep
+                     whatever they held elsewhere, host-memory outputs receive
+                     zeros there, so the parts' zero-initialised buffers sum to H
+                     and S. */
+  int part_index; /* this caller's part, 0 .. part_count-1 */
+  int reserved[1];
 } flapw_options;
 
 typedef struct flapw_stats {
@@ -183,6 +196,17 @@ int flapw_hs_create(const double lattice[9], int n_atoms, const double* pos_frac
                     const int* atom_type, int n_types, const double* mt_radius, int lmax,
                     int n_k, const double* k_frac, const double* kmax,
                     const flapw_options* opt, flapw_handle* out);
+
+/* How a job of n_k k-points with n_g[k] plane waves is split over part_count
+ * independent callers (options.part_count; the k-points and the output tiles
+ * are independent, the paper's multi-device split of Sec. 5 with no exchange
+ * step).  Whole k-points go to the parts, largest N_G^2 first to the least
+ * loaded part (ties to the lower index), when there are at least part_count
+ * of them and no part then exceeds 1.1 x the mean load: owner[k] receives
+ * the part of k-point k.  Otherwise owner[k] = -1 for every k: each part
+ * computes every part_count-th contraction tile of every k-point.  Host
+ * only; every caller computes the same answer.  Errors: FLAPW_ERR_ARG. */
+int flapw_partition(int n_k, const int* n_g, int part_count, int* owner);
 
 /* A handle without a crystal, usable only with flapw_herk. */
 int flapw_engine_create(const flapw_options* opt, flapw_handle* out);

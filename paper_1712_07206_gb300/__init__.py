@@ -17,7 +17,7 @@ import threading
 import numpy as np
 
 __all__ = ["FlapwError", "Options", "Stats", "Handle", "load", "library_path", "build",
-           "default_options", "enumerate_g", "hs_create", "engine_create", "herk_noalloc",
+           "default_options", "enumerate_g", "hs_create", "engine_create", "herk_noalloc", "partition",
            "declared_symbols",
            "PREC_FP64", "PREC_EMU", "LAYOUT_LOWER_FULL", "LAYOUT_LOWER_PACKED",
            "OPERANDS_FROM_AB", "OPERANDS_FACTORED", "S_CONTRACTION", "S_LEGENDRE",
@@ -47,7 +47,8 @@ class Options(ctypes.Structure):
                 ("tile_order", ctypes.c_int), ("s_method", ctypes.c_int), ("h_method", ctypes.c_int),
                 ("pipeline", ctypes.c_int), ("tile_cover", ctypes.c_int),
                 ("wait_us", ctypes.c_int), ("mem_cap_mb", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("part_count", ctypes.c_int), ("part_index", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class Stats(ctypes.Structure):
@@ -99,6 +100,7 @@ def load():
             "flapw_hs_create": (c_int, [dp, c_int, dp, ip, c_int, dp, c_int, c_int, dp, dp,
                                         P(Options), P(h)]),
             "flapw_engine_create": (c_int, [P(Options), P(h)]),
+            "flapw_partition": (c_int, [c_int, ip, c_int, ip]),
             "flapw_set_options": (c_int, [h, P(Options)]),
             "flapw_num_g": (c_int, [h, c_int, ip]),
             "flapw_get_gvectors": (c_int, [h, c_int, ip]),
@@ -290,6 +292,15 @@ def herk_noalloc(Z, ldz, K, N, sigma, H, ldh, layout=LAYOUT_LOWER_FULL, n_slices
     _check(load().flapw_herk_noalloc(_addr(Z), int(ldz), int(K), int(N),
                                      None if sig is None else _ip(sig), _addr(H), int(ldh),
                                      int(layout), int(n_slices), _stream(stream)))
+
+
+def partition(n_g, part_count) -> np.ndarray:
+    """flapw_partition: the part owning each k-point (-1 for all when the
+    k-points are shared by tiles).  Host only."""
+    ng = _i32(n_g)
+    owner = np.zeros(len(ng), dtype=np.int32)
+    _check(load().flapw_partition(len(ng), _ip(ng), int(part_count), _ip(owner)))
+    return owner
 
 
 def engine_create(options: Options | None = None) -> Handle:

@@ -106,6 +106,13 @@ bool is_device_ptr(const void* p) {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Which problems and tiles one part computes: problems with on[p] set, and of
+// each problem's ordered tile list every stride-th tile from index.
+struct PartFilter {
+  const std::vector<char>* on = nullptr;
+  int stride = 1, index = 0;
+};
+
 }  // namespace
 
 namespace flapw {
@@ -169,6 +176,10 @@ struct flapw_ctx {
   std::vector<int> emu_tiles_per_prob;  // whole emulated tiles of each problem
   int tile_cover = 0;            // emulated tile cover in use (tiles.cuh; 0 by N_G)
   int tiles_cover = -1;          // cover of the uploaded lists
+  // this caller's part of a partitioned job (options.part_count/part_index)
+  std::vector<char> part_on;     // problems this part computes
+  PartFilter part_filter;        // and its tile stride
+  std::string part_key, tiles_part;  // the partition the uploaded lists were made for
   bool deep_pipe = false;        // the contraction's deep pipeline (herk_emu_deep of the largest N_G)
   std::string tuned_shape;       // shape the autotuner's choice in use belongs to
   int pipe_choice = 0;           // autotuner's load pipeline (1 shallow, 2 deep; 0 none)
@@ -266,6 +277,8 @@ int check_options(flapw_ctx* h, const flapw_options& o) {
   if (o.pipeline < 0 || o.pipeline > 2) return fail(h, FLAPW_ERR_ARG, "options.pipeline must be in 0..2");
   if (o.tile_cover < 0 || o.tile_cover > 2) return fail(h, FLAPW_ERR_ARG, "options.tile_cover must be in 0..2");
   if (o.wait_us < 0) return fail(h, FLAPW_ERR_ARG, "options.wait_us must be >= 0");
+  if (o.part_count < 0 || o.part_index < 0 || o.part_index >= std::max(1, o.part_count))
+    return fail(h, FLAPW_ERR_ARG, "options.part_index must be in 0..part_count-1");
   if (o.mem_cap_mb < 0) return fail(h, FLAPW_ERR_ARG, "options.mem_cap_mb must be >= 0");
   return FLAPW_OK;
 }
@@ -307,6 +320,32 @@ int upload(flapw_ctx* h, DevBuf& d, const std::vector<T>& v) {
 // bytes) on config-2-like shapes.
 int h_split_block(int ng) { return (int)(0.55 * ((ng + 63) / 64)); }
 
+// A job split over part_count independent callers (one per GPU, no
+// communication; the k-points and the output tiles are independent, Sec. 5's
+// multi-device split of the BLAS-3 calls and Sec. 6's k-point loop): whole
+// k-points when there are at least as many as parts and the largest-first
+// assignment (by N_G^2, to the least loaded part, ties to the lower index)
+// keeps every part within 10 % of the mean load; otherwise every part takes
+// every part_count-th contraction tile of each k-point.  owner[k] is the part
+// of k-point k, or -1 when the k-points are shared by tiles.
+void partition_owner(int n_k, const int64_t* ng, int parts, std::vector<int>* owner) {
+  owner->assign(n_k, parts <= 1 ? 0 : -1);
+  if (parts <= 1 || n_k < parts) return;
+  std::vector<int> idx(n_k);
+  for (int k = 0; k < n_k; ++k) idx[k] = k;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return ng[a] > ng[b]; });
+  std::vector<double> load(parts, 0.0);
+  std::vector<int> own(n_k);
+  double total = 0;
+  for (int k : idx) {
+    const int r = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    own[k] = r;
+    load[r] += (double)ng[k] * (double)ng[k];
+    total += (double)ng[k] * (double)ng[k];
+  }
+  if (*std::max_element(load.begin(), load.end()) <= 1.1 * total / parts) *owner = own;
+}
+
 // Emulated contraction tiles (one per CTA pair: a 64-column strip against four
 // 64-row blocks, the cyclic cover of tiles.cuh) and FP64 tiles (64 x 64) of the
 // lower triangles of problems [p0, p1).  The order of the emulated tiles
@@ -321,10 +360,11 @@ int h_split_block(int ng) { return (int)(0.55 * ((ng + 63) / 64)); }
 // columns below it).  per_prob[p] counts the whole tiles of problem p.
 void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order, int cover_opt, int pairs,
                 std::vector<EmuTile>* emu, std::vector<F64Tile>* f64, int* n_split_ids,
-                std::vector<int>* per_prob, int part = 0) {
+                std::vector<int>* per_prob, const PartFilter& pf, int part = 0) {
   const size_t emu0 = emu->size();
   const int band = cover::order_band(order);
   for (int p = p0; p < p1; ++p) {
+    if (pf.on && !(*pf.on)[p]) continue;
     const int ng = probs[p].n_g;
     const int ncb = (ng + 63) / 64;
     const int j1 = h_split_block(ng);
@@ -342,12 +382,20 @@ void make_tiles(const std::vector<Prob>& probs, int p0, int p1, int order, int c
         const int bx = x.rb[0] / band, by = y.rb[0] / band;
         return bx != by ? bx < by : x.jb < y.jb;
       });
+    if (pf.stride > 1) {
+      size_t w = 0;
+      for (size_t i = 0; i < pt.size(); ++i)
+        if ((int)(i % pf.stride) == pf.index) pt[w++] = pt[i];
+      pt.resize(w);
+    }
     if (per_prob) (*per_prob)[p] += (int)pt.size();
     emu->insert(emu->end(), pt.begin(), pt.end());
     const int nb = (ng + 63) / 64;
+    int i64 = 0;
     for (int ib = 0; ib < nb; ++ib)
       for (int jb = 0; jb <= ib; ++jb)
-        if (part == 0 || (part == 1) == (jb < j1)) f64->push_back(F64Tile{p, ib, jb, 0});
+        if (part == 0 || (part == 1) == (jb < j1))
+          if (i64++ % pf.stride == pf.index) f64->push_back(F64Tile{p, ib, jb, 0});
   }
   // The pairs take the tiles round-robin, so the last rem = n mod pairs tiles
   // form a partly empty last wave.  Each of them becomes f K parts (f pairs
@@ -509,20 +557,23 @@ int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int6
     ps = herk_emu_pairs(busy_second);
   }
   if (h->tiles_rows_key != key || h->tiles_order != order || h->tiles_cover != cover_opt ||
-      h->tiles_pairs != pf * 1024 + ps || h->tiles_split != split_first) {
+      h->tiles_pairs != pf * 1024 + ps || h->tiles_split != split_first || h->tiles_part != h->part_key) {
     std::vector<EmuTile> emu;
     std::vector<F64Tile> f64;
     int ids_first = 0, ids_second = 0, ids_b = 0;
     std::vector<int>* pp = &h->emu_tiles_per_prob;
     pp->assign(probs.size(), 0);
-    make_tiles(probs, 0, n_first, order, cover_opt, pf, &emu, &f64, &ids_first, pp, split_first ? 1 : 0);
+    make_tiles(probs, 0, n_first, order, cover_opt, pf, &emu, &f64, &ids_first, pp, h->part_filter,
+               split_first ? 1 : 0);
     h->split_emu_b = (int)emu.size();
     h->split_f64_b = (int)f64.size();
-    if (split_first) make_tiles(probs, 0, n_first, order, cover_opt, pf, &emu, &f64, &ids_b, pp, 2);
+    if (split_first)
+      make_tiles(probs, 0, n_first, order, cover_opt, pf, &emu, &f64, &ids_b, pp, h->part_filter, 2);
     ids_first = std::max(ids_first, ids_b);
     h->split_emu = (int)emu.size();
     h->split_f64 = (int)f64.size();
-    make_tiles(probs, n_first, (int)probs.size(), order, cover_opt, ps, &emu, &f64, &ids_second, pp);
+    make_tiles(probs, n_first, (int)probs.size(), order, cover_opt, ps, &emu, &f64, &ids_second, pp,
+               h->part_filter);
     h->n_emu_tiles = (int)emu.size();
     h->n_f64_tiles = (int)f64.size();
     if (int rc_up = upload(h, h->d_emu_tiles, emu)) return rc_up;
@@ -533,6 +584,7 @@ int ensure_tiles(flapw_ctx* h, const std::vector<Prob>& probs, int n_first, int6
     h->tiles_rows_key = key;
     h->tiles_order = order;
     h->tiles_cover = cover_opt;
+    h->tiles_part = h->part_key;
     h->tiles_pairs = pf * 1024 + ps;
     h->tiles_split = split_first;
   }
@@ -715,6 +767,16 @@ int flapw_enumerate_g(const double lattice[9], const double k_frac[3], double km
   if (n < 0) return fail(nullptr, FLAPW_ERR_ARG, "singular lattice or kmax <= 0");
   *n_g = n;
   if (n3) std::memcpy(n3, v.data(), sizeof(int) * 3 * (size_t)std::min(n, std::max(max_g, 0)));
+  return FLAPW_OK;
+}
+
+int flapw_partition(int n_k, const int* n_g, int part_count, int* owner) {
+  if (n_k < 0 || (n_k > 0 && (!n_g || !owner)) || part_count < 1)
+    return fail(nullptr, FLAPW_ERR_ARG, "need n_k >= 0, n_g and owner, part_count >= 1");
+  std::vector<int64_t> ng(n_g, n_g + n_k);
+  std::vector<int> own;
+  partition_owner(n_k, ng.data(), part_count, &own);
+  std::copy(own.begin(), own.end(), owner);
   return FLAPW_OK;
 }
 
@@ -957,8 +1019,24 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   if (n_slots < 1) return fail(h, FLAPW_ERR_ARG, "n_slots must be >= 1");
   for (int a = 0; a < h->n_atoms; ++a)
     if (atom_slot[a] < 0 || atom_slot[a] >= n_slots) return fail(h, FLAPW_ERR_ARG, "atom_slot out of range");
+  // this caller's part of a partitioned job: whole k-points, or every P-th tile
+  {
+    const int parts = std::max(1, h->opt.part_count);
+    std::vector<int64_t> ngk(h->n_k);
+    for (int k = 0; k < h->n_k; ++k) ngk[k] = h->goff[k + 1] - h->goff[k];
+    std::vector<int> owner;
+    partition_owner(h->n_k, ngk.data(), parts, &owner);
+    const bool by_tiles = parts > 1 && h->n_k > 0 && owner[0] < 0;
+    h->part_on.assign(2 * h->n_k, 1);
+    for (int k = 0; k < h->n_k; ++k)
+      h->part_on[k] = h->part_on[h->n_k + k] = (parts == 1 || by_tiles || owner[k] == h->opt.part_index);
+    h->part_filter.on = &h->part_on;
+    h->part_filter.stride = by_tiles ? parts : 1;
+    h->part_filter.index = by_tiles ? h->opt.part_index : 0;
+    h->part_key = std::to_string(parts) + "/" + std::to_string(h->opt.part_index);
+  }
   for (int k = 0; k < h->n_k; ++k)
-    if (!H[k] || !S[k]) return fail(h, FLAPW_ERR_ARG, "NULL H[k] or S[k]");
+    if (h->part_on[k] && (!H[k] || !S[k])) return fail(h, FLAPW_ERR_ARG, "NULL H[k] or S[k]");
   cudaStream_t user_st = static_cast<cudaStream_t>(stream);
   const int n = 2 * h->n_L;
   const int nlp = h->lmax + 1;
@@ -1002,6 +1080,10 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       void* ptr = w ? S[k] : H[k];
       const int idx = w * nk + k;
       op.bytes[idx] = out_bytes(layout, ng);
+      if (!h->part_on[idx]) {  // another part's k-point: nothing written or copied
+        op.dev[idx] = nullptr;
+        continue;
+      }
       if (is_device_ptr(ptr)) {
         op.dev[idx] = static_cast<double2*>(ptr);
       } else {
@@ -1215,6 +1297,10 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     }
     int* cnt = h->d_cnt.as<int>();  // [0] 2x2 pivots, [2] error flag, [8..] npos, nneg
     CK(h, cudaMemsetAsync(cnt, 0, sizeof(int) * 8, st), "cudaMemsetAsync");
+    // tiles split over parts: host-memory outputs get zeros where other parts' blocks are
+    if (h->part_filter.stride > 1)
+      for (int i = 0; i < 2 * nk; ++i)
+        if (op.host[i]) CK(h, cudaMemsetAsync(op.dev[i], 0, op.bytes[i], st), "cudaMemsetAsync");
     int* npos = cnt + 8;
     int* nneg = cnt + 8 + n_slots;
     int* pos_off = h->d_off.as<int>();
@@ -1532,6 +1618,8 @@ int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const i
   h->deep_pipe = herk_emu_deep(N);
   h->max_ng = N;
   set_tile_order(h);
+  h->part_filter = PartFilter{};  // the contraction step alone is never split
+  h->part_key.clear();
   if (int rc_up = upload(h, h->d_kmap, kmap) || upload(h, h->d_probs, probs)) return rc_up;
   std::vector<int> rp(N, 0);
   if (int rc_up = upload(h, h->d_rowprob, rp)) return rc_up;

@@ -1,5 +1,8 @@
-"""The benchmark's multi-rank logic on CPU: the max-over-ranks timing
-reduction with two gloo ranks, and the reference arm under torchrun with two
+"""The multi-rank logic on CPU: the max-over-ranks timing reduction with two
+gloo ranks; the library's split of a job over independent parts
+(flapw_partition, host only), which every rank must compute identically and
+which must give every k-point to exactly one part with a bounded load, or
+share all k-points by tiles; and the reference arm under torchrun with two
 ranks (rank 0 alone runs the oracle and prints one line, both exit 0).
 They cover the host paths of N > 1 ranks without any GPU."""
 import json
@@ -42,6 +45,61 @@ def test_max_over_ranks_gloo_two_ranks():
         p.join(120)
         assert p.exitcode == 0
     assert dict(out) == {0: 2.5, 1: 2.5}
+
+
+# plane-wave counts of the synthetic workloads: 1 k-point (config 2), the
+# 32 uneven k-points of config 4, and uneven sets that do not balance
+PARTITION_CASES = [[3990], list(range(2540, 5869, 104)), [5868, 2540, 2600], [4000] * 5,
+                   [6000, 500, 500, 500], list(range(100, 4100, 250))]
+
+
+def _partition_worker(rank, world, port, out):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import paper_1712_07206_gb300 as fl
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    res = []
+    for ng in PARTITION_CASES:
+        own = fl.partition(ng, world)
+        got = [torch.zeros(len(ng), dtype=torch.int32) for _ in range(world)]
+        dist.all_gather(got, torch.from_numpy(own.astype(np.int32)))
+        res.append([g.tolist() for g in got])
+    out[rank] = res
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_partition_gloo_two_ranks():
+    import numpy as np
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_partition_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    for case, ng in enumerate(PARTITION_CASES):
+        a, b = out[0][case], out[1][case]
+        assert a == b and a[0] == a[1]                 # both ranks: one identical split
+        own = np.array(a[0])
+        if own[0] < 0:                                 # shared by tiles: every k-point
+            assert np.all(own == -1)
+            continue
+        assert set(own.tolist()) <= {0, 1} and len(own) >= 2
+        w = np.asarray(ng, float) ** 2
+        load = [w[own == r].sum() for r in (0, 1)]
+        assert max(load) <= 1.1 * w.sum() / 2         # the balance the split promises
+    # one k-point, or loads that cannot be balanced: tiles
+    assert out[0][0][0] == [-1]
+    assert out[0][2][0] == [-1, -1, -1] or max(
+        sum(x * x for x, o in zip([5868, 2540, 2600], out[0][2][0]) if o == r) for r in (0, 1)) <= \
+        1.1 * sum(x * x for x in [5868, 2540, 2600]) / 2
 
 
 def test_reference_arm_under_torchrun_two_ranks():
