@@ -83,6 +83,18 @@ typedef struct flapw_ctx* flapw_handle;
  * contraction flops of FLAPW_H_FACTORED. */
 #define FLAPW_H_FACTORED 0
 #define FLAPW_H_ALG3 1
+/* FLAPW_H_SPHERICAL: H of the spherical part of T (per slot the l-diagonal
+ * blocks t^XY_l delta_{L'L} given to flapw_set_spherical_T) by the addition
+ * theorem, like FLAPW_S_LEGENDRE for S:
+ *   H_sph = (4 pi / Omega) sum_c rho_c sum_l (2l+1) P_l(Khat'.Khat)
+ *           [t^AA a'a + t^BB b'b + t^AB a'b + t^BA b'a]_l
+ * (c the (slot, type) combinations of atoms, rho_c their phase sums), plus
+ * the FLAPW_H_FACTORED contraction of the rest T - T_sph.  The factorisation
+ * drops exact zero pivots, so a rest confined to r rows and columns of each
+ * slot contracts over K = r per atom; a rest that is exactly zero (T is its
+ * spherical part) runs no factorisation, operands or contraction for H.
+ * Needs FLAPW_OPERANDS_FACTORED; the addition-theorem part runs in FP64. */
+#define FLAPW_H_SPHERICAL 2
 
 typedef struct flapw_options {
   int precision; /* FLAPW_PREC_EMU (default) or FLAPW_PREC_FP64 */
@@ -196,6 +208,16 @@ int flapw_hs_create(const double lattice[9], int n_atoms, const double* pos_frac
                     const int* atom_type, int n_types, const double* mt_radius, int lmax,
                     int n_k, const double* k_frac, const double* kmax,
                     const flapw_options* opt, flapw_handle* out);
+
+/* The spherical part of T for options.h_method = FLAPW_H_SPHERICAL.
+ *   t_sph[n_slots*(lmax+1)*4] (host, copied): per slot and l the real
+ *       t^AA_l, the real t^BB_l and Re, Im of t^BA_l (t^AB_l = conj t^BA_l),
+ *       such that the slot's T holds T^XY_{(lm),(lm)} = t^XY_l + (the rest).
+ *   NULL or n_slots < 1 clears it.  build_HS returns FLAPW_ERR_STATE with
+ *   FLAPW_H_SPHERICAL unless n_slots matches its own and lmax the handle's.
+ * H is the same for any t_sph (linearity in T); the split only changes how
+ * much is contracted.  Errors: FLAPW_ERR_ARG for non-finite entries. */
+int flapw_set_spherical_T(flapw_handle h, const double* t_sph, int n_slots);
 
 /* How a job of n_k k-points with n_g[k] plane waves is split over part_count
  * independent callers (options.part_count; the k-points and the output tiles

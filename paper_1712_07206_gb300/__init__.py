@@ -21,7 +21,7 @@ __all__ = ["FlapwError", "Options", "Stats", "Handle", "load", "library_path", "
            "declared_symbols",
            "PREC_FP64", "PREC_EMU", "LAYOUT_LOWER_FULL", "LAYOUT_LOWER_PACKED",
            "OPERANDS_FROM_AB", "OPERANDS_FACTORED", "S_CONTRACTION", "S_LEGENDRE",
-           "H_FACTORED", "H_ALG3"]
+           "H_FACTORED", "H_ALG3", "H_SPHERICAL"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _HEADER = os.path.join(os.path.dirname(_HERE), "include", "flapw.h")
@@ -30,7 +30,7 @@ PREC_FP64, PREC_EMU = 0, 1
 LAYOUT_LOWER_FULL, LAYOUT_LOWER_PACKED = 0, 1
 OPERANDS_FROM_AB, OPERANDS_FACTORED = 0, 1
 S_CONTRACTION, S_LEGENDRE = 0, 1
-H_FACTORED, H_ALG3 = 0, 1
+H_FACTORED, H_ALG3, H_SPHERICAL = 0, 1, 2
 ERR = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_FACTOR",
        -5: "ERR_TIMEOUT", -6: "ERR_STATE", -7: "ERR_UNSUPPORTED"}
 
@@ -101,6 +101,7 @@ def load():
                                         P(Options), P(h)]),
             "flapw_engine_create": (c_int, [P(Options), P(h)]),
             "flapw_partition": (c_int, [c_int, ip, c_int, ip]),
+            "flapw_set_spherical_T": (c_int, [h, dp, c_int]),
             "flapw_set_options": (c_int, [h, P(Options)]),
             "flapw_num_g": (c_int, [h, c_int, ip]),
             "flapw_get_gvectors": (c_int, [h, c_int, ip]),
@@ -242,6 +243,15 @@ class Handle:
         sig = None if sigma is None else _i32(sigma)
         self._call("flapw_herk", _addr(Z), int(ldz), int(K), int(N),
                    None if sig is None else _ip(sig), _addr(H), int(ldh), _stream(stream))
+
+    def set_spherical_T(self, t_sph):
+        """flapw_set_spherical_T: t_sph [n_slots][lmax+1][4] = t^AA, t^BB,
+        Re t^BA, Im t^BA (None clears)."""
+        if t_sph is None:
+            self._call("flapw_set_spherical_T", None, 0)
+            return
+        t = _f64(t_sph)
+        self._call("flapw_set_spherical_T", _dp(t), int(t.shape[0]))
 
     def sync(self):
         self._call("flapw_sync")

@@ -209,6 +209,11 @@ struct flapw_ctx {
   flapw_stats stats{};
   int last_n_slots = 0;
   bool last_alg3 = false;        // the last build_HS formed H by the paper's Alg. 3
+  // spherical part of T (flapw_set_spherical_T): [slot][l][4] = t^AA, t^BB, Re t^BA, Im t^BA
+  std::vector<double> tsph;
+  int tsph_slots = 0, tsph_lmax = -1;
+  DevBuf d_tsph;
+  bool last_h_zero = false;      // the last build_HS's T was its spherical part (no H contraction)
 
   // CUDA graph replay of build_HS
   cudaGraphExec_t gexec = nullptr;
@@ -272,8 +277,10 @@ int check_options(flapw_ctx* h, const flapw_options& o) {
     return fail(h, FLAPW_ERR_ARG, "options.s_method is not a FLAPW_S_* value");
   if (o.s_method == FLAPW_S_LEGENDRE && o.operands != FLAPW_OPERANDS_FACTORED)
     return fail(h, FLAPW_ERR_ARG, "options.s_method FLAPW_S_LEGENDRE needs FLAPW_OPERANDS_FACTORED");
-  if (o.h_method != FLAPW_H_FACTORED && o.h_method != FLAPW_H_ALG3)
+  if (o.h_method != FLAPW_H_FACTORED && o.h_method != FLAPW_H_ALG3 && o.h_method != FLAPW_H_SPHERICAL)
     return fail(h, FLAPW_ERR_ARG, "options.h_method is not a FLAPW_H_* value");
+  if (o.h_method == FLAPW_H_SPHERICAL && o.operands != FLAPW_OPERANDS_FACTORED)
+    return fail(h, FLAPW_ERR_ARG, "options.h_method FLAPW_H_SPHERICAL needs FLAPW_OPERANDS_FACTORED");
   if (o.pipeline < 0 || o.pipeline > 2) return fail(h, FLAPW_ERR_ARG, "options.pipeline must be in 0..2");
   if (o.tile_cover < 0 || o.tile_cover > 2) return fail(h, FLAPW_ERR_ARG, "options.tile_cover must be in 0..2");
   if (o.wait_us < 0) return fail(h, FLAPW_ERR_ARG, "options.wait_us must be >= 0");
@@ -770,6 +777,24 @@ int flapw_enumerate_g(const double lattice[9], const double k_frac[3], double km
   return FLAPW_OK;
 }
 
+int flapw_set_spherical_T(flapw_handle h, const double* t_sph, int n_slots) {
+  if (!h) return fail(h, FLAPW_ERR_ARG, "NULL handle");
+  if (h->engine_only) return fail(h, FLAPW_ERR_STATE, "handle has no crystal");
+  if (!t_sph || n_slots < 1) {
+    h->tsph.clear();
+    h->tsph_slots = 0;
+    h->tsph_lmax = -1;
+    return FLAPW_OK;
+  }
+  const size_t n = (size_t)n_slots * (h->lmax + 1) * 4;
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(t_sph[i])) return fail(h, FLAPW_ERR_ARG, "t_sph entries must be finite");
+  h->tsph.assign(t_sph, t_sph + n);
+  h->tsph_slots = n_slots;
+  h->tsph_lmax = h->lmax;
+  return FLAPW_OK;
+}
+
 int flapw_partition(int n_k, const int* n_g, int part_count, int* owner) {
   if (n_k < 0 || (n_k > 0 && (!n_g || !owner)) || part_count < 1)
     return fail(nullptr, FLAPW_ERR_ARG, "need n_k >= 0, n_g and owner, part_count >= 1");
@@ -1044,6 +1069,13 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   const int64_t K = (int64_t)h->n_atoms * n;
   // H by the paper's Alg. 3: L^H R over 3 N_A N_L rows, no factorisation
   const bool alg3 = h->opt.h_method == FLAPW_H_ALG3;
+  // H from the spherical part of T by the addition theorem plus the contraction
+  // of the rest (which is skipped when the rest is zero)
+  const bool h_sph = h->opt.h_method == FLAPW_H_SPHERICAL;
+  bool h_zero = false;
+  if (h_sph && (h->tsph_slots != n_slots || h->tsph_lmax != h->lmax))
+    return fail(h, FLAPW_ERR_STATE, "FLAPW_H_SPHERICAL needs flapw_set_spherical_T for these n_slots");
+  const size_t tsph_bytes = h_sph ? h->tsph.size() * sizeof(double) : 0;
   const int64_t K_H = alg3 ? (int64_t)h->n_atoms * 3 * h->n_L : K;
   if (K_H >= ((int64_t)1 << 17))
     return fail(h, FLAPW_ERR_UNSUPPORTED, "the H contraction's K (2 N_A N_L, or 3 N_A N_L for Alg. 3) must be below 131072");
@@ -1129,7 +1161,8 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   // S by the addition theorem: Khat of every plane wave and the atoms grouped
   // by type, both fixed by the crystal (computed once)
   const bool s_legendre = h->opt.s_method == FLAPW_S_LEGENDRE;
-  if (s_legendre && !h->khat_valid) {
+  if (h_sph) CK(h, h->d_tsph.ensure(tsph_bytes), "workspace");
+  if ((s_legendre || h_sph) && !h->khat_valid) {
     std::vector<int> ta;
     std::vector<int> start{0};
     for (int t = 0; t < h->n_types; ++t) {
@@ -1235,7 +1268,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     }
   }
   // (the call that tunes times whole halves: no split there)
-  const bool h_split = h_host && !(tune && h->tuned_shape != shape);
+  const bool h_split = h_host && !(tune && h->tuned_shape != shape) && !h_sph;
   Half hH, hHb, hS;
   if (int rc = ensure_tiles(h, probs, nk, h->rows, &hH, &hS, 0, n_slots, h_split, &hHb)) return rc;
   hH.row0 = 0;
@@ -1261,7 +1294,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   }
   PinBuf& pin_in = h->pin_ring[slot];
   PinBuf& pin_probs = h->pin_probs_ring[slot];
-  CK(h, pin_in.ensure(t_bytes + slot_bytes + u_bytes + cmb_ints * 4 + 256), "cudaMallocHost");
+  CK(h, pin_in.ensure(t_bytes + slot_bytes + u_bytes + cmb_ints * 4 + tsph_bytes + 256), "cudaMallocHost");
   CK(h, pin_probs.ensure(sizeof(Prob) * probs.size()), "cudaMallocHost");
   char* pin = static_cast<char*>(pin_in.p);
   std::memcpy(pin, T, t_bytes);
@@ -1272,6 +1305,38 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   std::memcpy(pc + n_combo, combo_type.data(), combo_type.size() * 4);
   std::memcpy(pc + 2 * n_combo, combo_atoms.data(), combo_atoms.size() * 4);
   std::memcpy(pc + 2 * n_combo + combo_atoms.size(), combo_start.data(), combo_start.size() * 4);
+  if (h_sph) {
+    // the rest of T after its spherical part: t^AA_l, t^BB_l and t^BA_l come
+    // off the diagonals of the blocks (t^AB_l = conj t^BA_l off T^AB)
+    std::memcpy(pin + t_bytes + slot_bytes + u_bytes + cmb_ints * 4, h->tsph.data(), tsph_bytes);
+    double* Tr = reinterpret_cast<double*>(pin);
+    const int nl = h->n_L;
+    for (int sl = 0; sl < n_slots; ++sl)
+      for (int l = 0; l <= h->lmax; ++l) {
+        const double* c = &h->tsph[((size_t)sl * (h->lmax + 1) + l) * 4];
+        for (int L = l * l; L < (l + 1) * (l + 1); ++L) {
+          double* blk = Tr + (size_t)sl * n * n * 2;
+          blk[2 * ((size_t)L * n + L)] -= c[0];
+          blk[2 * ((size_t)(nl + L) * n + nl + L)] -= c[1];
+          blk[2 * ((size_t)(nl + L) * n + L)] -= c[2];
+          blk[2 * ((size_t)(nl + L) * n + L) + 1] -= c[3];
+          blk[2 * ((size_t)L * n + nl + L)] -= c[2];
+          blk[2 * ((size_t)L * n + nl + L) + 1] += c[3];
+        }
+      }
+    // a remainder that is exactly zero (on and below the diagonal) needs no contraction
+    h_zero = true;
+    for (int sl = 0; sl < n_slots && h_zero; ++sl)
+      for (int r = 0; r < n && h_zero; ++r)
+        for (int c = 0; c <= r; ++c) {
+          const double* e = Tr + ((size_t)sl * n * n + (size_t)r * n + c) * 2;
+          if (e[0] != 0.0 || e[1] != 0.0) {
+            h_zero = false;
+            break;
+          }
+        }
+  }
+  h->last_h_zero = h_zero;
   std::memcpy(pin_probs.p, probs.data(), sizeof(Prob) * probs.size());
   h->last_n_slots = n_slots;
   h->last_alg3 = alg3;
@@ -1286,6 +1351,10 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     CK(h, cudaMemcpyAsync(h->d_slot.p, pin + t_bytes, slot_bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
     CK(h, cudaMemcpyAsync(h->d_slot.as<char>() + slot_bytes, pc, cmb_ints * 4, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
     CK(h, cudaMemcpyAsync(h->d_U.p, pin + t_bytes + slot_bytes, u_bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    if (h_sph)
+      CK(h, cudaMemcpyAsync(h->d_tsph.p, pin + t_bytes + slot_bytes + u_bytes + cmb_ints * 4, tsph_bytes,
+                            cudaMemcpyHostToDevice, st),
+         "cudaMemcpyAsync");
     CK(h, cudaMemcpyAsync(h->d_probs.p, pin_probs.p, sizeof(Prob) * probs.size(), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
     if (!h->opt.use_graph) {
       CK(h, cudaEventRecord(h->pin_ev[slot], st), "cudaEventRecord");
@@ -1353,7 +1422,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev[13], 0), "cudaStreamWaitEvent");
     int* oprexp_a = h->d_oprexp.as<int>();
     int* oprexp_b = oprexp_a + op_rows_a;
-    if (!alg3) {
+    if (!alg3 && !h_zero) {
       // beside the S contraction one CTA per slot; with S by the addition
       // theorem the factorisation leads the critical path: a cluster per slot
       CK(h, launch_tfactor(h->d_T.as<double2>(), n, n_slots, h->d_work.as<double2>(), h->d_CH.as<double2>(),
@@ -1368,13 +1437,13 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       CK(h, launch_opgemm_build_alg3(h->d_T.as<double2>(), n_slots, n, h->n_L, op_kp, h->d_opA.as<double2>(),
                                      h->aux_stream),
          "operand factor launch");
-    } else if (tc_ops) {
+    } else if (tc_ops && !h_zero) {
       CK(h, launch_opgemm_build(h->d_CH.as<double2>(), perm, n_slots, n, op_kp, nullptr, nullptr, nullptr,
                                 h->n_L, h->lmax, h->n_types, h->g_total, h->d_opA.as<double2>(), nullptr,
                                 h->aux_stream, true),
          "operand factor launch");
     }
-    if (tc_ops) {
+    if (tc_ops && !h_zero) {
       CK(h, launch_slicer_rows(h->d_opA.as<double2>(), op_kp, op_rows_a, kOpSlices, h->d_opSLA.as<__half>(),
                                oprexp_a, h->aux_stream),
          "operand factor slicer launch");
@@ -1446,7 +1515,32 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     // join, then H
     CK(h, cudaStreamWaitEvent(st, h->ev[16], 0), "cudaStreamWaitEvent");
     CK(h, cudaEventRecord(h->ev[8], st), "cudaEventRecord");
-    if (tc_ops) {
+    HLegArgs hl{};
+    if (h_sph) {
+      hl.probs = h->d_probs.as<Prob>();
+      hl.h_row0 = 0;
+      hl.g_total = h->g_total;
+      hl.lmax = h->lmax;
+      hl.khat = h->d_khat.as<double>();
+      hl.al = h->d_al.as<double>();
+      hl.bl = h->d_bl.as<double>();
+      hl.ph = h->d_ph.as<double2>();
+      hl.tsph = h->d_tsph.as<double>();
+      hl.combo_slot = oa.combo_slot;
+      hl.combo_type = oa.combo_type;
+      hl.combo_atoms = oa.combo_atoms;
+      hl.combo_start = oa.combo_start;
+      hl.n_combo = n_combo;
+      hl.scale = 4.0 * M_PI / h->volume;
+    }
+    if (h_zero) {
+      // T is its spherical part: no factorisation, operands or contraction for H
+      CK(h, cudaEventRecord(h->ev[10], st), "cudaEventRecord");
+      CK(h, cudaEventRecord(h->ev[11], st), "cudaEventRecord");
+      CK(h, launch_hlegendre(hl, h->d_f64_tiles.as<F64Tile>() + hH.f64_t0, hH.f64_nt, false, st),
+         "H (addition theorem) launch");
+      CK(h, cudaEventRecord(h->ev[12], st), "cudaEventRecord");
+    } else if (tc_ops) {
       OpGemmArgs ga{};
       ga.n = n;
       ga.kchunks = op_kp / kChunk;
@@ -1488,11 +1582,19 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     } else {
       CK(h, launch_opform_H(oa, factored, st), "H operand launch");
     }
-    const bool h_presliced = tc_ops && !alg3;
-    if (!h_presliced) CK(h, cudaEventRecord(h->ev[10], st), "cudaEventRecord");
-    if (int rc = enqueue_contraction(h, hH, 0, st, 11, h_split ? 18 : 12, h_presliced)) return rc;
-    if (h_split)
-      if (int rc = enqueue_contraction(h, hHb, 0, st, -1, 12, true)) return rc;
+    if (!h_zero) {
+      const bool h_presliced = tc_ops && !alg3;
+      if (!h_presliced) CK(h, cudaEventRecord(h->ev[10], st), "cudaEventRecord");
+      if (int rc = enqueue_contraction(h, hH, 0, st, 11, h_split ? 18 : 12, h_presliced)) return rc;
+      if (h_split)
+        if (int rc = enqueue_contraction(h, hHb, 0, st, -1, 12, true)) return rc;
+      // the spherical part of T by the addition theorem, added to the contraction of the rest
+      if (h_sph) {
+        CK(h, launch_hlegendre(hl, h->d_f64_tiles.as<F64Tile>() + hH.f64_t0, hH.f64_nt, true, st),
+           "H (addition theorem) launch");
+        CK(h, cudaEventRecord(h->ev[12], st), "cudaEventRecord");
+      }
+    }
     // Host-memory outputs go back on the copy stream: S beside the H work; with
     // the split H contraction, columns [0, c1) of H while its second part runs,
     // the rest after it.  Every copy is enqueued after all the compute, so that
@@ -1545,6 +1647,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
 
   // graph replay, keyed on everything the captured sequence bakes in
   std::vector<uintptr_t> key{(uintptr_t)A, (uintptr_t)B, (uintptr_t)n_slots, (uintptr_t)h->opt.precision,
+                             (uintptr_t)h_zero, (uintptr_t)h->d_tsph.p,
                              (uintptr_t)h->opt.s_method, (uintptr_t)h->opt.h_method,
                              (uintptr_t)layout, (uintptr_t)h->opt.operands, (uintptr_t)slices_of(h),
                              (uintptr_t)h->d_Z.p, (uintptr_t)h->d_SL.p, (uintptr_t)h->pin_ring[0].p,
@@ -1731,6 +1834,10 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
       if (h->last_alg3) {  // no factorisation: every H row has sigma = +1
         kpk[1] = (int)s.k_total;
         kpk[2] = 0;
+        c[0] = 0;
+      }
+      if (h->last_h_zero) {  // T was its spherical part: no H contraction
+        kpk[1] = kpk[2] = 0;
         c[0] = 0;
       }
       s.n_pivot2 = c[0];

@@ -276,6 +276,27 @@ struct SLegArgs {
                           // evaluate in double-float; null: in FP64
 };
 size_t slegendre_df_floats2(int n_types, int lmax, int n_atoms, int64_t G);
+// The spherical part of H by the addition theorem (slegendre.cu), on the
+// 64 x 64 lower tiles of the H problems, FP64.
+struct HLegArgs {
+  const Prob* probs;       // problems (row_base - h_row0 = first global plane wave)
+  int64_t h_row0;
+  int64_t g_total;
+  int lmax;
+  const double* khat;      // [G][3]
+  const double* al;        // [t][l][G]
+  const double* bl;
+  const double2* ph;       // [atom][G]
+  const double* tsph;      // [slot][l][4]: t^AA, t^BB, Re t^BA, Im t^BA
+  const int* combo_slot;   // atoms grouped by (slot, type) combination
+  const int* combo_type;
+  const int* combo_atoms;
+  const int* combo_start;  // [n_combo + 1]
+  int n_combo;
+  double scale;            // 4 pi / Omega
+};
+// add: the spherical part is added to the lower triangle already written.
+cudaError_t launch_hlegendre(const HLegArgs& a, const F64Tile* tiles, int n_tiles, bool add, cudaStream_t st);
 cudaError_t launch_khat(const Geom& geo, const GData& gd, double* khat, cudaStream_t st);
 cudaError_t launch_slegendre(const SLegArgs& a, const F64Tile* tiles, int n_tiles, cudaStream_t st);
 

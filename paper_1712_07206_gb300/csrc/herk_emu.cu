@@ -255,10 +255,12 @@ struct Sched {
   }
 };
 
-// This thread's row of a finished tile into the lower triangle: in place
+// This thread's row of a finished tile of the cyclic cover into the lower
+// triangle: output columns gc0 + 32h + n, n < 32, Re in acc[n] and Im in
+// acc[32 + n], written as whole complex elements (16-byte stores): in place
 // below the strip's diagonal (on and below it in the diagonal block),
-// conjugate-transposed above it (element (gr, gc) to (gc, gr); Hermitian
-// result).  Element n goes to offset o_n, o_{n+1} = o_n + step_n,
+// conjugated and transposed above it (element (gr, gc) to (gc, gr); the result
+// is Hermitian).  Element n goes to offset o_n, o_{n+1} = o_n + step_n,
 // step_{n+1} = step_n + dstep (the packed layout's columns shorten by one).
 // Out of line: it runs once per tile, and kept inline it changed how the
 // compiler laid out the MMA and load loops (measured 5-10 % on the contraction).
@@ -268,7 +270,7 @@ __device__ __noinline__ void write_tile_row(const EmuTile& T, const Prob& P, uin
   const int rbk = (blk & 2) ? ((blk & 1) ? T.rb[3] : T.rb[2]) : ((blk & 1) ? T.rb[1] : T.rb[0]);
   const int64_t ng = P.n_g;
   const int64_t gr = (int64_t)rbk * 64 + (m & 63);
-  const int64_t gc0 = (int64_t)T.jb * 64;
+  const int64_t gc0 = (int64_t)T.jb * 64 + 32 * h;
   if (!(((T.wmask >> blk) & 1) && gr < ng)) return;
   const bool packed = P.layout == FLAPW_LAYOUT_LOWER_PACKED;
   const bool trans = rbk < T.jb;
@@ -285,14 +287,16 @@ __device__ __noinline__ void write_tile_row(const EmuTile& T, const Prob& P, uin
     step = P.ld;
   }
   const int64_t lim = trans ? ng - gc0 : min(ng - gc0, gr - gc0 + 1);
-  const int nlim = lim < 64 ? (int)lim : 64;
-  const bool neg = trans && h;
+  const int nlim = lim < 32 ? (int)lim : 32;
   const int er = rexp[P.row_base + gr] - frac;
   const int* ec = rexp + P.col_base + gc0;
-  double* outd = reinterpret_cast<double*>(P.out) + h;
+  double2* out = P.out;
 #pragma unroll
-  for (int n = 0; n < 64; ++n) {
-    if (n < nlim) outd[2 * o] = fx::to_double(neg ? -acc[n] : acc[n], er + ec[n]);
+  for (int n = 0; n < 32; ++n) {
+    if (n < nlim) {
+      const int e = er + ec[n];
+      out[o] = make_double2(fx::to_double(acc[n], e), fx::to_double(trans ? -acc[32 + n] : acc[32 + n], e));
+    }
     o += step;
     step += dstep;
   }
@@ -523,7 +527,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- drain + epilogue (256 threads per CTA) ----------------
     const int ew = warp - kDrainWarp0;
     const int q = warp & 3;       // TMEM lane quadrant this warp may access
-    const int h = ew >> 2;        // 0: Re, 1: Im
+    const int h = ew >> 2;        // aligned: 0 Re, 1 Im; cyclic: output columns 32h .. 32h + 31
     const int m = q * 32 + lane;  // row within this CTA's 128 rows
     uint32_t acc_it = 0;
     bool ok = true;
@@ -545,13 +549,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();  // tcgen05.ld is warp-collective
         // R pass: Re += RR (cols 0..63 of a pair block), Im += RI (64..127);
         // I pass: Re += II (64..127), Im -= IR (0..63).
-        const uint32_t col = (h == 0) ? (sc.pass ? 64u : 0u) : (sc.pass ? 0u : 64u);
-        const bool sub = (h == 1 && sc.pass == 1);
-        for (int pq = 0; pq <= sc.two; ++pq) {
-          const int sh = frac - kSliceBits * (sc.i + sc.j + pq + 2);
-          const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * 256u +
-                              (uint32_t)pq * 128u + col;
-          drain_fixed<64>(tb, acc, 0, sh, sub);
+        if constexpr (CYC) {
+          // warp half h owns output columns 32h .. 32h + 31, Re in acc[0..31]
+          // and Im in acc[32..63] (whole complex elements for the epilogue)
+          const uint32_t rcol = (sc.pass ? 64u : 0u) + 32u * h, icol = (sc.pass ? 0u : 64u) + 32u * h;
+          for (int pq = 0; pq <= sc.two; ++pq) {
+            const int sh = frac - kSliceBits * (sc.i + sc.j + pq + 2);
+            const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * 256u +
+                                (uint32_t)pq * 128u;
+            drain_fixed<32>(tb + rcol, acc, 0, sh, false);
+            drain_fixed<32>(tb + icol, acc, 32, sh, sc.pass == 1);
+          }
+        } else {
+          const uint32_t col = (h == 0) ? (sc.pass ? 64u : 0u) : (sc.pass ? 0u : 64u);
+          const bool sub = (h == 1 && sc.pass == 1);
+          for (int pq = 0; pq <= sc.two; ++pq) {
+            const int sh = frac - kSliceBits * (sc.i + sc.j + pq + 2);
+            const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * 256u +
+                                (uint32_t)pq * 128u + col;
+            drain_fixed<64>(tb, acc, 0, sh, sub);
+          }
         }
         tc_fence_before();
         __syncwarp();

@@ -327,7 +327,155 @@ __global__ void __launch_bounds__(kDfThreads) slegendre_df_kernel(SLegArgs a, co
   }
 }
 
+// The spherical part of H by the addition theorem (FLAPW_H_SPHERICAL): for
+// T^{XY}_{L'L} = t^{XY}_l delta_{L'L} per slot, Eq. (def_hamilton) with the
+// library's matching coefficients collapses like S:
+//   H_{G'G} = (4 pi / Omega) sum_c rho_c(G', G) sum_l (2l+1) P_l(Khat'.Khat)
+//             [t^AA a'a + t^BB b'b + Re t^BA (a'b + b'a) + i Im t^BA (b'a - a'b)]_l
+// with a' = a_l(K'), a = a_l(K) (b likewise) of the combination's type, t of
+// its slot (t^AB = conj t^BA: T is Hermitian), rho_c the phase sum over the
+// atoms of the (slot, type) combination c.  FP64 throughout.  add: the result
+// is added to the lower triangle already in P.out (the contraction of the
+// rest of T), otherwise written.
+__global__ void __launch_bounds__(256) hlegendre_kernel(HLegArgs a, const F64Tile* __restrict__ tiles,
+                                                        int add) {
+  __shared__ double kh[2][kT][3];
+  __shared__ double rad[4][kL1][kT];  // (2l+1) a_l, (2l+1) b_l rows; a_l, b_l columns
+  __shared__ double2 phs[2][kChunkAtoms][kT];
+  __shared__ double coef[kL1][4];     // t^AA, t^BB, Re t^BA, Im t^BA of the slot
+  __shared__ double rec_ab[kL1][2];
+  const F64Tile T = tiles[blockIdx.x];
+  const Prob P = a.probs[T.prob];
+  const int64_t ng = P.n_g;
+  const int64_t g0 = P.row_base - a.h_row0;  // global plane wave of the problem's first row
+  const int r0 = T.ib * kT, c0 = T.jb * kT;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int L1 = a.lmax + 1;
+  const int64_t G = a.g_total;
+  if (tid < kL1) {
+    rec_ab[tid][0] = (double)(2 * tid + 1) / (double)(tid + 1);
+    rec_ab[tid][1] = (double)tid / (double)(tid + 1);
+  }
+  for (int i = tid; i < 2 * kT * 3; i += 256) {
+    const int w = i / (kT * 3), e = i % (kT * 3), g = e / 3, c = e % 3;
+    const int64_t gl = (w == 0 ? r0 : c0) + g;
+    kh[w][g][c] = (gl < ng) ? a.khat[3 * (g0 + gl) + c] : 0.0;
+  }
+  double2 Hs[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) Hs[i][j] = make_double2(0.0, 0.0);
+
+  for (int cb = 0; cb < a.n_combo; ++cb) {
+    const int t = a.combo_type[cb], sl = a.combo_slot[cb];
+    __syncthreads();
+    for (int i = tid; i < 4 * L1 * kT; i += 256) {
+      const int w = i / (L1 * kT), e = i % (L1 * kT), l = e / kT, g = e % kT;
+      const int64_t gl = ((w < 2) ? r0 : c0) + g;
+      double v = 0.0;
+      if (gl < ng) {
+        const int64_t ro = ((int64_t)t * L1 + l) * G + g0 + gl;
+        const double x = (w == 0 || w == 2) ? a.al[ro] : a.bl[ro];
+        v = (w < 2) ? (2 * l + 1) * x : x;
+      }
+      rad[w][l][g] = v;
+    }
+    if (tid < 4 * L1) coef[tid >> 2][tid & 3] = a.tsph[((int64_t)sl * L1 + (tid >> 2)) * 4 + (tid & 3)];
+    double2 rho[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) rho[i][j] = make_double2(0.0, 0.0);
+    const int a0 = a.combo_start[cb], a1 = a.combo_start[cb + 1];
+    for (int ab = a0; ab < a1; ab += kChunkAtoms) {
+      const int na = min(kChunkAtoms, a1 - ab);
+      __syncthreads();
+      for (int i = tid; i < 2 * kChunkAtoms * kT; i += 256) {
+        const int w = i / (kChunkAtoms * kT), e = i % (kChunkAtoms * kT), q = e / kT, g = e % kT;
+        const int64_t gl = (w == 0 ? r0 : c0) + g;
+        double2 v = make_double2(0.0, 0.0);
+        if (q < na && gl < ng) v = a.ph[(int64_t)a.combo_atoms[ab + q] * G + g0 + gl];
+        phs[w][q][g] = v;
+      }
+      __syncthreads();
+      for (int q = 0; q < na; ++q) {
+        double2 pr[4], pc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          pr[i] = phs[0][q][ty * 4 + i];
+          pc[i] = phs[1][q][tx * 4 + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {  // conj(pr) pc
+            rho[i][j].x = fma(pr[i].x, pc[j].x, fma(pr[i].y, pc[j].y, rho[i][j].x));
+            rho[i][j].y = fma(pr[i].x, pc[j].y, fma(-pr[i].y, pc[j].x, rho[i][j].y));
+          }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int ri = ty * 4 + i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int cj = tx * 4 + j;
+        const double x = kh[0][ri][0] * kh[1][cj][0] + kh[0][ri][1] * kh[1][cj][1] + kh[0][ri][2] * kh[1][cj][2];
+        double pm = 1.0, p = x;  // P_{l-1}, P_l from l = 1
+        double Lr = 0.0, Li = 0.0;
+        for (int l = 0; l < L1; ++l) {
+          const double pl = (l == 0) ? 1.0 : p;
+          const double aa = rad[0][l][ri] * rad[2][l][cj], bb = rad[1][l][ri] * rad[3][l][cj];
+          const double ab_ = rad[0][l][ri] * rad[3][l][cj], ba = rad[1][l][ri] * rad[2][l][cj];
+          const double wr = fma(coef[l][0], aa, fma(coef[l][1], bb, coef[l][2] * (ab_ + ba)));
+          const double wi = coef[l][3] * (ba - ab_);
+          Lr = fma(pl, wr, Lr);
+          Li = fma(pl, wi, Li);
+          if (l >= 1) {
+            const double pn = fma(rec_ab[l][0] * x, p, -rec_ab[l][1] * pm);
+            pm = p;
+            p = pn;
+          }
+        }
+        // rho_c x L_c, complex
+        Hs[i][j].x = fma(rho[i][j].x, Lr, fma(-rho[i][j].y, Li, Hs[i][j].x));
+        Hs[i][j].y = fma(rho[i][j].x, Li, fma(rho[i][j].y, Lr, Hs[i][j].y));
+      }
+    }
+  }
+  double* outd = reinterpret_cast<double*>(P.out);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gr = r0 + ty * 4 + i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gc = c0 + tx * 4 + j;
+      if (gr < ng && gc <= gr) {
+        const int64_t o = (P.layout == FLAPW_LAYOUT_LOWER_PACKED) ? gc * ng - gc * (gc - 1) / 2 + (gr - gc)
+                                                                   : gc * P.ld + gr;
+        const double re = a.scale * Hs[i][j].x, im = a.scale * Hs[i][j].y;
+        if (add) {
+          outd[2 * o] += re;
+          outd[2 * o + 1] += im;
+        } else {
+          outd[2 * o] = re;
+          outd[2 * o + 1] = im;
+        }
+      }
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_hlegendre(const HLegArgs& a, const F64Tile* tiles, int n_tiles, bool add, cudaStream_t st) {
+  if (n_tiles == 0) return cudaSuccess;
+  if (a.lmax < 0 || a.lmax > kMaxLmax) return cudaErrorInvalidValue;
+  hlegendre_kernel<<<n_tiles, 256, 0, st>>>(a, tiles, add ? 1 : 0);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_khat(const Geom& geo, const GData& gd, double* khat, cudaStream_t st) {
   if (geo.g_total == 0) return cudaSuccess;

@@ -484,7 +484,7 @@ def _sampled_check(p, Hs, Ss, h, layout, ks, tol, n_cols=6, seed=0):
 def test_config3_sampled(precision, tol):
     p = inputs.config3()
     h, Hs, Ss, _ = run_hs(p, precision, operands=fl.OPERANDS_FACTORED)
-    _sampled_check(p, Hs, Ss, h, fl.LAYOUT_LOWER_FULL, [0], tol)
+    _sampled_check(p, Hs, Ss, h, fl.LAYOUT_LOWER_FULL, [0], tol, n_cols=32)
 
 
 @pytest.mark.parametrize("precision,tol", [(fl.PREC_EMU, TOL_EMU), (fl.PREC_FP64, TOL_F64)])
@@ -493,7 +493,7 @@ def test_config4_batched_32k_sampled(precision, tol):
     h, Hs, Ss, _ = run_hs(p, precision, operands=fl.OPERANDS_FACTORED, use_graph=1)
     ngs = [h.num_g(k) for k in range(p.n_k)]
     assert min(ngs) >= 2500 and max(ngs) <= 6000 and len(set(ngs)) > 20
-    _sampled_check(p, Hs, Ss, h, fl.LAYOUT_LOWER_FULL, [0, 13, 31], tol, n_cols=4)
+    _sampled_check(p, Hs, Ss, h, fl.LAYOUT_LOWER_FULL, list(range(p.n_k)), tol, n_cols=2)
 
 
 def test_config5_packed_sampled():
@@ -503,6 +503,41 @@ def test_config5_packed_sampled():
                           operands=fl.OPERANDS_FACTORED)
     ng = h.num_g(0)
     assert Hs[0].numel() == ng * (ng + 1) // 2
-    _sampled_check(p, Hs, Ss, h, fl.LAYOUT_LOWER_PACKED, [0], TOL_EMU, n_cols=4)
+    _sampled_check(p, Hs, Ss, h, fl.LAYOUT_LOWER_PACKED, [0], TOL_EMU, n_cols=32)
     del Hs, Ss
+    torch.cuda.empty_cache()
+
+
+def test_config5_fp64_tile_subset():
+    # the FP64 path on config 5 would take hours; part 0 of 4096 parts (every
+    # 4096th 64 x 64 tile, the tile split of the job partition) computes 17
+    # blocks of each lower triangle, compared element by element with the
+    # oracle on one column of each of four blocks
+    torch = torch_cuda()
+    p = inputs.config5()
+    parts = 4096
+    opt = fl.default_options(precision=fl.PREC_FP64, layout=fl.LAYOUT_LOWER_PACKED,
+                             operands=fl.OPERANDS_FACTORED, part_count=parts, part_index=0)
+    h = fl.from_problem(p, opt)
+    _, A, B = run_ab(p, h)
+    del A, B
+    ng = h.num_g(0)
+    H, S = alloc_out(ng, fl.LAYOUT_LOWER_PACKED), alloc_out(ng, fl.LAYOUT_LOWER_PACKED)
+    h.build_HS(p.T, p.atom_slot, p.U, None, None, [H], [S])
+    h.sync()
+    nb = (ng + 63) // 64
+    blocks = [(ib, jb) for ib in range(nb) for jb in range(ib + 1)][::parts]   # part 0's tiles
+    assert len(blocks) >= 17
+    pick = [blocks[i] for i in (0, 5, 11, len(blocks) - 1)]
+    n3 = h.gvectors(0)
+    cols = [jb * 64 + 7 for ib, jb in pick]
+    Ho, So = oracle.hs_columns(p, 0, n3, cols)
+    Hg = columns_from_lower(H, ng, fl.LAYOUT_LOWER_PACKED, cols)
+    Sg = columns_from_lower(S, ng, fl.LAYOUT_LOWER_PACKED, cols)
+    for X, R in ((Hg, Ho), (Sg, So)):
+        got = np.concatenate([X[c, ib * 64:min(ng, ib * 64 + 64)] for c, (ib, jb) in enumerate(pick)])
+        ref = np.concatenate([R[c, ib * 64:min(ng, ib * 64 + 64)] for c, (ib, jb) in enumerate(pick)])
+        assert np.linalg.norm(got - ref) <= TOL_F64 * np.linalg.norm(ref)
+    del H, S
+    h.destroy()
     torch.cuda.empty_cache()
