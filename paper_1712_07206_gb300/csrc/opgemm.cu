@@ -460,6 +460,32 @@ __device__ __forceinline__ void put_digits(long long X, __half* dst, int64_t str
   dst[0] = __float2half_rn(fx::small_int_to_float(y));
 }
 
+// put_digits for two adjacent columns: digit i of X0 and of X1 go out as one
+// fp16 pair to dst2[i * stride2] (4-byte stores; dst2 4-byte aligned).
+template <int NS>
+__device__ __forceinline__ void put_digits2(long long X0, long long X1, __half2* dst2, int64_t stride2) {
+  constexpr int kLo = (NS - 1 < 4) ? NS - 1 : 4;
+  int x0 = (int)(X0 & 0xFFFFFFFll), x1 = (int)(X1 & 0xFFFFFFFll);
+  int y0 = (int)(X0 >> 28), y1 = (int)(X1 >> 28);
+#pragma unroll
+  for (int j = 0; j < kLo; ++j) {
+    const int a0 = ((x0 + 64) & 127) - 64, a1 = ((x1 + 64) & 127) - 64;
+    dst2[(NS - 1 - j) * stride2] = __floats2half2_rn(fx::small_int_to_float(a0), fx::small_int_to_float(a1));
+    x0 = (x0 - a0) >> kSliceBits;
+    x1 = (x1 - a1) >> kSliceBits;
+  }
+  y0 = y0 * (1 << (28 - kSliceBits * kLo)) + x0;
+  y1 = y1 * (1 << (28 - kSliceBits * kLo)) + x1;
+#pragma unroll
+  for (int i = NS - 1 - kLo; i >= 1; --i) {
+    const int a0 = ((y0 + 64) & 127) - 64, a1 = ((y1 + 64) & 127) - 64;
+    dst2[i * stride2] = __floats2half2_rn(fx::small_int_to_float(a0), fx::small_int_to_float(a1));
+    y0 = (y0 - a0) >> kSliceBits;
+    y1 = (y1 - a1) >> kSliceBits;
+  }
+  dst2[0] = __floats2half2_rn(fx::small_int_to_float(y0), fx::small_int_to_float(y1));
+}
+
 // Smallest k with |(x, y)| < 2^k (0 for x = y = 0), |x|, |y| < 2^62: the bit
 // length of x^2 + y^2 in 128-bit integer arithmetic, halved upwards.
 __device__ __forceinline__ int mag_bits(long long x, long long y) {
@@ -633,14 +659,22 @@ __global__ void __launch_bounds__(256) sop_slice_kernel(const SopArgs a, __half*
       const int at = a.combo_atoms[ai];
       const double2 f = a.ph[(int64_t)at * a.G + gi];
       const long long qr = fx::fixed_point(f.x, 62), qi = fx::fixed_point(f.y, 62);
-      for (int c = lane; c < n; c += 32) {
-        const long long Wx = wx[c], Wy = wy[c];
-        const long long zr = fx::mul_q62(Wx, qr) - fx::mul_q62(Wy, qi);
-        const long long zi = fx::mul_q62(Wx, qi) + fx::mul_q62(Wy, qr);
-        const int sh = we[c] + kSliceBits * NS - e_row;
+      // two adjacent columns per lane (n = 2 N_L is even, so an atom's columns
+      // start even): each digit of both entries goes out as one fp16 pair
+      for (int c = 2 * lane; c < n; c += 64) {
+        long long X[2][2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const long long Wx = wx[c + q], Wy = wy[c + q];
+          const long long zr = fx::mul_q62(Wx, qr) - fx::mul_q62(Wy, qi);
+          const long long zi = fx::mul_q62(Wx, qi) + fx::mul_q62(Wy, qr);
+          const int sh = we[c + q] + kSliceBits * NS - e_row;
+          X[q][0] = shift_round(zr, sh, lim);
+          X[q][1] = shift_round(zi, sh, lim);
+        }
         const int64_t col = (int64_t)at * n + c;
-        put_digits<NS>(shift_round(zr, sh, lim), srow + col, 2 * plane_stride);
-        put_digits<NS>(shift_round(zi, sh, lim), srow + plane_stride + col, 2 * plane_stride);
+        put_digits2<NS>(X[0][0], X[1][0], reinterpret_cast<__half2*>(srow + col), plane_stride);
+        put_digits2<NS>(X[0][1], X[1][1], reinterpret_cast<__half2*>(srow + plane_stride + col), plane_stride);
       }
     }
   }
