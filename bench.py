@@ -338,9 +338,14 @@ def run_ours(args):
             step_host()
         e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.e2e_steps)
         h2d = p.T.nbytes + p.U.nbytes + p.radial.nbytes + p.atom_slot.nbytes
-        d2h = 2 * sum(copied_elements(ng, layout) for ng, m in zip(ngs, mine) if m) * 16
+        # the library's own count of the bytes its copies to host memory move
+        # (the lower triangles, plus the small triangles above the diagonal
+        # inside the column blocks of the full layout)
+        st_e = h.stats()
+        d2h = st_e["bytes_d2h"]
         e2e = {"value": round(flops / (e_ms * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
-               "ms_per_step": round(e_ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "ms_per_step": round(e_ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "d2h_copies_per_step": int(st_e["copy_ops"])}
     # the whole job's flops over the slowest part's time (each rank computes its part)
     value = flops / (ms * 1e-3) / 1e12
     line = {
@@ -415,17 +420,6 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
-
-
-def copied_elements(ng, layout):
-    """Elements of one output the library copies to host memory: all of the
-    packed layout; of the full layout, column blocks of max(64, ceil(N/32))
-    columns from each block's first diagonal element down."""
-    import paper_1712_07206_gb300 as fl
-    if layout == fl.LAYOUT_LOWER_PACKED:
-        return ng * (ng + 1) // 2
-    w = max(64, (ng + 31) // 32)
-    return sum((ng - j0) * min(w, ng - j0) for j0 in range(0, ng, w))
 
 
 def launches_per_step(args):

@@ -177,7 +177,9 @@ typedef struct flapw_stats {
   int graph_replays;   /* build_HS calls served by CUDA-graph replay */
   int tile_cover;      /* tile cover in use for the largest problem (1 cyclic, 2 aligned) */
   int pipeline;        /* load pipeline in use (1: 3 stages of two chunks, 2: 5 of one) */
-  int reserved[6];
+  int copy_ops;        /* device-to-host copies the last build_HS or herk enqueued */
+  int64_t bytes_d2h;   /* bytes those copies move (host-memory outputs only) */
+  int reserved[4];
   double ms_s;         /* the S half of ms_contract: its contraction, or with
                           FLAPW_S_LEGENDRE the addition-theorem evaluation */
   double ms_ab_assemble; /* the A/B assembly kernel of the last build_AB (part of ms_ab) */
@@ -266,9 +268,13 @@ int flapw_build_AB(flapw_handle h, const double* radial, void* A, void* B, void*
  *       previous flapw_build_AB on this handle for the radial data.
  *   H[n_k], S[n_k]: per k-point output pointers (device or host memory),
  *       complex128, lower triangle in the handle's layout; the full layout
- *       uses ld = N_G(k).  Elements above the diagonal are not written (in
- *       host memory most of them are left untouched: the lower triangle is
- *       copied back in blocks of columns).
+ *       uses ld = N_G(k).  Elements above the diagonal are not written in
+ *       device memory.  Host memory is written in blocks of columns, each
+ *       from its first diagonal element down, so the elements above the
+ *       diagonal inside each block (about 1/nb of the upper triangle for nb
+ *       blocks per matrix) receive unspecified values and the others are
+ *       left untouched; nb is 32 for one host output per call and shrinks to
+ *       keep one call's copies to about 320 (stats.copy_ops, stats.bytes_d2h).
  * Each T block is factorised as T = C diag(sigma) C^H (Bunch-Kaufman
  * pivoted LDL^H, then 2x2 eigen-splitting; Sec. 3, Alg. 1's Cholesky step
  * generalised to indefinite T), so that H = Z^H diag(sigma) Z with

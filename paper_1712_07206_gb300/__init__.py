@@ -60,7 +60,8 @@ class Stats(ctypes.Structure):
                 ("n_pivot2", ctypes.c_int), ("n_slices", ctypes.c_int), ("n_tiles", ctypes.c_int),
                 ("tile_order", ctypes.c_int), ("graph_replays", ctypes.c_int),
                 ("tile_cover", ctypes.c_int), ("pipeline", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6), ("ms_s", ctypes.c_double),
+                ("copy_ops", ctypes.c_int), ("bytes_d2h", ctypes.c_int64),
+                ("reserved", ctypes.c_int * 4), ("ms_s", ctypes.c_double),
                 ("ms_ab_assemble", ctypes.c_double)]
 
     def as_dict(self):

@@ -435,33 +435,46 @@ struct OutPlan {
 };
 
 // Width of the column blocks in which a full-layout output goes to host
-// memory: at most about 32 blocks per matrix, at least 64 columns.
-int64_t copy_block_cols(int64_t ng) { return std::max<int64_t>(64, (ng + 31) / 32); }
+// memory.  Each block is one 2D copy from the block's first diagonal element
+// down, so nb blocks move the lower triangle plus the small triangles above
+// the diagonal inside the blocks: about (1 + 1/nb) N_G^2 / 2 elements.  (The
+// link to pinned host memory runs at ~190 GB/s on this part with 2D copies of
+// such rows and with contiguous ones alike.)  Every copy takes an entry of the
+// device's work queue, which holds about a thousand operations before an
+// enqueueing call blocks until the GPU has drained some: with many host
+// outputs in one call the blocks widen, so that a call enqueues at most about
+// kCopyOps copies and two calls in flight still fit (32 blocks per matrix for
+// one k-point, 5 for 32 k-points).
+constexpr int kCopyOps = 320;
+int64_t copy_block_cols(int64_t ng, int n_host) {
+  const int nb = std::max(2, std::min(32, kCopyOps / std::max(1, n_host)));
+  return std::max<int64_t>(64, (ng + nb - 1) / nb);
+}
 
-// Device-to-host copy of columns [c0, c1) of one output's lower triangle.
-// The packed layout is one contiguous range; the full layout (ld = ng) goes
-// block of columns by block of columns, each from the block's first diagonal
-// element down, so that about half of the N_G^2 elements (the lower triangle
-// and the small triangles above the diagonal inside each block) cross the
-// link.  (The link to pinned host memory runs at ~190 GB/s on this part with
-// one stream or two alike.)
+// Device-to-host copy of columns [c0, c1) of one output's lower triangle: the
+// packed layout as one contiguous range, the full layout (ld = ng) in blocks
+// of w columns (copy_block_cols).  Adds the copies and bytes to *ops, *bytes.
 cudaError_t copy_out(void* dst, const double2* src, int64_t ng, int layout, int64_t c0, int64_t c1,
-                     cudaStream_t st) {
+                     int64_t w, cudaStream_t st, int* ops, int64_t* bytes) {
   if (c1 <= c0) return cudaSuccess;
   char* d = static_cast<char*>(dst);
   const char* s = reinterpret_cast<const char*>(src);
   if (layout == FLAPW_LAYOUT_LOWER_PACKED) {
     const size_t o0 = (size_t)(c0 * ng - c0 * (c0 - 1) / 2) * 16;
     const size_t o1 = (size_t)(c1 * ng - c1 * (c1 - 1) / 2) * 16;
+    *ops += 1;
+    *bytes += (int64_t)(o1 - o0);
     return cudaMemcpyAsync(d + o0, s + o0, o1 - o0, cudaMemcpyDeviceToHost, st);
   }
-  const int64_t w = copy_block_cols(ng);
   for (int64_t j0 = c0; j0 < c1; j0 += w) {
     const size_t off = (size_t)(j0 * ng + j0) * 16;
+    const int64_t cols = std::min(w, c1 - j0);
     const cudaError_t e = cudaMemcpy2DAsync(d + off, (size_t)ng * 16, s + off, (size_t)ng * 16,
-                                            (size_t)(ng - j0) * 16, (size_t)std::min(w, c1 - j0),
+                                            (size_t)(ng - j0) * 16, (size_t)cols,
                                             cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return e;
+    *ops += 1;
+    *bytes += (ng - j0) * cols * 16;
   }
   return cudaSuccess;
 }
@@ -1601,33 +1614,33 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     // a long copy queue (many k-points) cannot hold the host back from
     // enqueueing the H work; each waits for the contraction that writes it.
     bool s_host = false;
+    int n_host = 0, copy_ops = 0;
+    int64_t copy_bytes = 0;
+    for (int i = 0; i < 2 * nk; ++i) n_host += op.host[i] != nullptr;
     for (int i = nk; i < 2 * nk; ++i) s_host = s_host || op.host[i] != nullptr;
+    auto ng_of = [&](int k) -> int64_t { return h->goff[k + 1] - h->goff[k]; };
+    auto copy = [&](int i, int k, int64_t c0, int64_t c1) -> cudaError_t {
+      return copy_out(op.host[i], op.dev[i], ng_of(k), layout, c0, c1, copy_block_cols(ng_of(k), n_host),
+                      h->copy_stream, &copy_ops, &copy_bytes);
+    };
     if (s_host) {
       CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev[4], 0), "cudaStreamWaitEvent");
       for (int i = nk; i < 2 * nk; ++i)
-        if (op.host[i])
-          CK(h, copy_out(op.host[i], op.dev[i], h->goff[i - nk + 1] - h->goff[i - nk], layout, 0,
-                         h->goff[i - nk + 1] - h->goff[i - nk], h->copy_stream),
-             "cudaMemcpy2DAsync");
+        if (op.host[i]) CK(h, copy(i, i - nk, 0, ng_of(i - nk)), "cudaMemcpy2DAsync");
     }
     auto h_c1 = [&](int k) -> int64_t {
-      const int64_t ng = h->goff[k + 1] - h->goff[k];
-      return h_split ? std::min<int64_t>(ng, 64 * (int64_t)h_split_block((int)ng)) : 0;
+      return h_split ? std::min<int64_t>(ng_of(k), 64 * (int64_t)h_split_block((int)ng_of(k))) : 0;
     };
     if (h_split) {
       CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev[18], 0), "cudaStreamWaitEvent");
       for (int k = 0; k < nk; ++k)
-        if (op.host[k])
-          CK(h, copy_out(op.host[k], op.dev[k], h->goff[k + 1] - h->goff[k], layout, 0, h_c1(k),
-                         h->copy_stream),
-             "cudaMemcpy2DAsync");
+        if (op.host[k]) CK(h, copy(k, k, 0, h_c1(k)), "cudaMemcpy2DAsync");
     }
     if (h_host) CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev[12], 0), "cudaStreamWaitEvent");
     for (int k = 0; k < nk; ++k)
-      if (op.host[k])
-        CK(h, copy_out(op.host[k], op.dev[k], h->goff[k + 1] - h->goff[k], layout, h_c1(k),
-                       h->goff[k + 1] - h->goff[k], h->copy_stream),
-           "cudaMemcpy2DAsync");
+      if (op.host[k]) CK(h, copy(k, k, h_c1(k), ng_of(k)), "cudaMemcpy2DAsync");
+    h->stats.copy_ops = copy_ops;
+    h->stats.bytes_d2h = copy_bytes;
     if (s_host || h_host) {
       CK(h, cudaEventRecord(h->ev_copy, h->copy_stream), "cudaEventRecord");
       CK(h, cudaStreamWaitEvent(st, h->ev_copy, 0), "cudaStreamWaitEvent");
@@ -1744,6 +1757,8 @@ int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const i
   CK(h, cudaEventRecord(h->ev[2], st), "cudaEventRecord");
   if (int rc = enqueue_contraction(h, hf, 0, st, 3, 4)) return rc;
   if (!devH) CK(h, cudaMemcpyAsync(H, dH, ob, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+  h->stats.copy_ops = devH ? 0 : 1;
+  h->stats.bytes_d2h = devH ? 0 : (int64_t)ob;
   CK(h, cudaEventRecord(h->ev[5], st), "cudaEventRecord");
   h->ev_recorded = true;
   h->ev_engine = true;

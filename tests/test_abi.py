@@ -169,9 +169,10 @@ int main(void) {
   printf("%zu %zu\\n", sizeof(flapw_options), sizeof(flapw_stats));
   printf("%zu %zu %zu %zu\\n", offsetof(flapw_options, tile_order), offsetof(flapw_options, s_method),
          offsetof(flapw_options, tile_cover), offsetof(flapw_options, reserved));
-  printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(flapw_stats, flops_tensor), offsetof(flapw_stats, k_total),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(flapw_stats, flops_tensor), offsetof(flapw_stats, k_total),
          offsetof(flapw_stats, graph_replays), offsetof(flapw_stats, tile_cover),
-         offsetof(flapw_stats, pipeline), offsetof(flapw_stats, ms_s));
+         offsetof(flapw_stats, pipeline), offsetof(flapw_stats, ms_s), offsetof(flapw_stats, copy_ops),
+         offsetof(flapw_stats, bytes_d2h));
   return 0;
 }
 """)
@@ -183,6 +184,7 @@ int main(void) {
     assert vals[0] == ctypes.sizeof(fl.Options) and vals[1] == ctypes.sizeof(fl.Stats)
     assert vals[2:6] == [fl.Options.tile_order.offset, fl.Options.s_method.offset,
                          fl.Options.tile_cover.offset, fl.Options.reserved.offset]
-    assert vals[6:12] == [fl.Stats.flops_tensor.offset, fl.Stats.k_total.offset,
+    assert vals[6:14] == [fl.Stats.flops_tensor.offset, fl.Stats.k_total.offset,
                           fl.Stats.graph_replays.offset, fl.Stats.tile_cover.offset,
-                          fl.Stats.pipeline.offset, fl.Stats.ms_s.offset]
+                          fl.Stats.pipeline.offset, fl.Stats.ms_s.offset, fl.Stats.copy_ops.offset,
+                          fl.Stats.bytes_d2h.offset]

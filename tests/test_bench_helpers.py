@@ -39,17 +39,6 @@ def test_launches_per_step(bench, operands, s_method, h_method, n):
     assert bench.launches_per_step(Args(operands, s_method, h_method)) == n
 
 
-def test_copied_elements_cover_the_lower_triangle(bench):
-    import paper_1712_07206_gb300 as fl
-    for ng in (1, 63, 64, 65, 300, 2049, 3990):
-        full = bench.copied_elements(ng, fl.LAYOUT_LOWER_FULL)
-        assert ng * (ng + 1) // 2 <= full <= ng * ng
-        w = max(64, (ng + 31) // 32)
-        # the lower triangle plus at most one w x w triangle per block
-        assert full - ng * (ng + 1) // 2 <= ((ng + w - 1) // w) * w * (w - 1) // 2
-        assert bench.copied_elements(ng, fl.LAYOUT_LOWER_PACKED) == ng * (ng + 1) // 2
-
-
 def test_peaks_and_traffic_table(bench):
     bf16, bf16_sus, hbm, src = bench.peaks()
     assert bf16 > 0 and bf16_sus > 0 and hbm > 0 and src in ("measured", "fallback")

@@ -444,6 +444,48 @@ def test_host_outputs_every_lower_element_copied(layout, precision, tol):
         ng = Ho.shape[0]
         assert herm_relerr(lower_to_full(Hs[k], ng, layout), Ho) <= tol, k
         assert herm_relerr(lower_to_full(Ss[k], ng, layout), So) <= tol, k
+    # the library's count of what crossed the link: every lower element, and
+    # with the full layout at most one block-sized triangle per block more
+    st = h.stats()
+    lower = 2 * 16 * sum(h.num_g(k) * (h.num_g(k) + 1) // 2 for k in range(p.n_k))
+    if layout == fl.LAYOUT_LOWER_PACKED:
+        assert st["bytes_d2h"] == lower
+    else:
+        assert lower < st["bytes_d2h"] <= 1.25 * lower
+    assert 2 * p.n_k <= st["copy_ops"] <= 320 + p.n_k
+
+
+def test_many_host_outputs_wider_copy_blocks():
+    # 48 k-points into pinned host memory in one call: the column blocks widen
+    # (5 per matrix instead of 32) so that the call enqueues at most ~320
+    # copies and returns before they run (the device's work queue holds about a
+    # thousand operations); every lower element must still arrive
+    torch = torch_cuda()
+    sizes = tuple(300 + 37 * (i % 11) for i in range(48))
+    p = inputs.small(91, n_atoms=2, n_types=2, lmax=2, n_target=sizes)
+    h = fl.from_problem(p, fl.default_options(precision=fl.PREC_EMU, operands=fl.OPERANDS_FACTORED))
+    _, A, B = run_ab(p, h)
+    Hs, Ss = [], []
+    for k in range(p.n_k):
+        ng = h.num_g(k)
+        Hs.append(torch.full((ng * ng,), float("nan"), dtype=torch.complex128).pin_memory())
+        Ss.append(torch.full((ng * ng,), float("nan"), dtype=torch.complex128).pin_memory())
+    h.build_HS(p.T, p.atom_slot, p.U, A, B, Hs, Ss)
+    h.sync()
+    st = h.stats()
+    assert st["copy_ops"] <= 320 + p.n_k, st["copy_ops"]
+    lower = 2 * 16 * sum(h.num_g(k) * (h.num_g(k) + 1) // 2 for k in range(p.n_k))
+    assert lower < st["bytes_d2h"] <= 1.6 * lower
+    for k in (0, 1, 17, 46, 47):
+        Ho, So = oracle_hs(p, k)
+        ng = Ho.shape[0]
+        assert herm_relerr(lower_to_full(Hs[k], ng, 0), Ho) <= TOL_EMU, k
+        assert herm_relerr(lower_to_full(Ss[k], ng, 0), So) <= TOL_EMU, k
+    for k in range(p.n_k):
+        ng = h.num_g(k)
+        L = np.tril(np.ones((ng, ng), dtype=bool))
+        for X in (Hs[k], Ss[k]):
+            assert not np.isnan(X.numpy().reshape(ng, ng).T[L]).any(), k
 
 
 def test_bad_calls_return_codes_not_faults():
