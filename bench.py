@@ -29,6 +29,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# options.h_method values of include/flapw.h
+H_METHODS = {"factored": 0, "alg3": 1, "spherical": 2}
+
 METRIC = "H+S build TFLOP/s & ms/k-point, emulated vs FP64 path, at ≤1e-12 rel err"
 
 
@@ -62,8 +65,10 @@ def max_over_ranks(x: float) -> float:
 # the kernel sources it was taken on (kernel_source_hash).  A capture of other
 # sources, or of another shape or configuration, reports null.
 MEASURED_TRAFFIC = {
+    ("c2_ortho_16at_l8_ng4000", 7, "contraction", "factored", 1, 5, 1):
+        {"bytes": 2.1885e9, "kernel_sha": "f3d8a413f4bb6e62"},
     ("c2_ortho_16at_l8_ng4000", 7, "contraction", "factored", 1, 0, 1):
-        {"bytes": 2.2001e9, "kernel_sha": "5eec19f62de98072"},
+        {"bytes": 2.1866e9, "kernel_sha": "f3d8a413f4bb6e62"},
 }
 
 KERNEL_SOURCES = ("herk_emu.cu", "tc_common.cuh", "tiles.cuh", "fixed64.cuh")
@@ -209,6 +214,12 @@ def run_ours(args):
         torch.cuda.set_device(0)
     fl.build()
     p = workload(args.config)
+    t_sph = None
+    if args.h_method == "spherical":
+        # the workload with T replaced by its spherical part (per slot and l the
+        # means over m of the l-diagonal entries): H then comes from the
+        # addition theorem alone, with no H contraction
+        p.T, t_sph = spherical_part(p.T, p.lmax)
     operands = fl.OPERANDS_FACTORED if args.operands == "factored" else fl.OPERANDS_FROM_AB
     layout = fl.LAYOUT_LOWER_PACKED if p.layout == "packed" else fl.LAYOUT_LOWER_FULL
     # N > 1 ranks: each rank computes its part of the job (whole k-points, or
@@ -218,8 +229,10 @@ def run_ours(args):
                              autotune=1 if args.autotune else 0, use_graph=1 if args.graph else 0,
                              part_count=ws, part_index=rank,
                              s_method=fl.S_LEGENDRE if args.s_method == "legendre" else fl.S_CONTRACTION,
-                             h_method=fl.H_ALG3 if args.h_method == "alg3" else fl.H_FACTORED)
+                             h_method=H_METHODS[args.h_method])
     h = fl.from_problem(p, opt)
+    if t_sph is not None:
+        h.set_spherical_T(t_sph)
     ngs = [h.num_g(k) for k in range(p.n_k)]
     flops = hs_flops(p, ngs)
     dev = torch.device("cuda")
@@ -252,8 +265,12 @@ def run_ours(args):
             if collect_kernel:
                 h.sync()
                 st_ = h.stats()
-                # the tensor-core contraction alone (with Legendre S only the H half)
-                kms.append(st_["ms_contract"] - (st_["ms_s"] if args.s_method == "legendre" else 0.0))
+                # the tensor-core contraction alone (with Legendre S only the H half,
+                # with H by the addition theorem only the S half)
+                if args.h_method == "spherical":
+                    kms.append(st_["ms_s"])
+                else:
+                    kms.append(st_["ms_contract"] - (st_["ms_s"] if args.s_method == "legendre" else 0.0))
                 abms.append(st_["ms_ab_assemble"])
         torch.cuda.synchronize()
         return [a.elapsed_time(b) for a, b in ev], (kms, abms)
@@ -284,10 +301,14 @@ def run_ours(args):
     # slice-pair products of the timed launches: H (K = k_total) and, unless S
     # comes from the addition theorem, S (K = 2 N_A N_L)
     k_s = 0 if args.s_method == "legendre" else 2 * p.n_atoms * p.n_L
-    alg_tensor = n_pairs * 4.0 * (st["k_total"] + k_s) * float(np.sum(np.asarray(ngs, float) ** 2))
+    k_h = 0 if args.h_method == "spherical" else st["k_total"]
+    alg_tensor = n_pairs * 4.0 * (k_h + k_s) * float(np.sum(np.asarray(ngs, float) ** 2))
     achieved_alg = alg_tensor / (k_ms * 1e-3) / 1e12
     stage = {k: round(st[k], 4) for k in ("ms_ab", "ms_factor", "ms_operands", "ms_slice", "ms_contract",
                                           "ms_hs_total")}
+    # the measured FP64 peak (DGEMM), the bound of the FP64 path and of the A/B assembly
+    fp64_peak = fp64_peak_tflops()
+    ab_instr = 8.0 * p.n_atoms * p.n_L * sum(ngs)
     # the plain FP64 path on the same workload (fewer steps: ~0.3 s each)
     f64_ms = None
     H64 = S64 = None
@@ -313,7 +334,6 @@ def run_ours(args):
                 f_kms.append(h.stats()["ms_contract"])
         f64_ms = float(np.mean(f_ms))
         f64_kms = float(np.mean(f_kms))
-        fp64_peak = fp64_peak_tflops()
         h.set_options(opt)
     # end-to-end through the C ABI: the step's inputs (radial data, T, U, slots)
     # from host memory and its results H and S into pinned host buffers, copies
@@ -333,10 +353,18 @@ def run_ours(args):
 
         step_host()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        e_steps, e_enq, e_lib = [], [], []
         for _ in range(args.e2e_steps):
-            step_host()
-        e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.e2e_steps)
+            t1 = time.perf_counter()
+            h.build_AB(p.radial, A, B, stream)
+            h.build_HS(p.T, p.atom_slot, p.U, A, B, Hh, Sh, stream)
+            t2 = time.perf_counter()
+            h.sync()
+            t3 = time.perf_counter()
+            e_steps.append((t3 - t1) * 1e3)
+            e_enq.append((t2 - t1) * 1e3)
+            e_lib.append(h.stats()["ms_hs_total"])
+        e_ms = max_over_ranks(float(np.mean(e_steps)))
         h2d = p.T.nbytes + p.U.nbytes + p.radial.nbytes + p.atom_slot.nbytes
         # the library's own count of the bytes its copies to host memory move
         # (the lower triangles, plus the small triangles above the diagonal
@@ -345,7 +373,11 @@ def run_ours(args):
         d2h = st_e["bytes_d2h"]
         e2e = {"value": round(flops / (e_ms * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
                "ms_per_step": round(e_ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "d2h_copies_per_step": int(st_e["copy_ops"])}
+               "d2h_copies_per_step": int(st_e["copy_ops"]),
+               "steps_ms": [round(x, 3) for x in e_steps],
+               # per step: host time until build_HS returned, and the library's
+               # own device time of build_HS (its events, copies included)
+               "enqueue_ms": [round(x, 3) for x in e_enq], "hs_device_ms": [round(x, 3) for x in e_lib]}
     # the whole job's flops over the slowest part's time (each rank computes its part)
     value = flops / (ms * 1e-3) / 1e12
     line = {
@@ -394,7 +426,9 @@ def run_ours(args):
                                       st["tile_cover"], st["tile_order"], st["pipeline"]),
                      "kernel_source_hash": kernel_source_hash(),
                      "kernel": "herk_emu_kernel (" + ("H launch; S by the addition theorem"
-                                                      if args.s_method == "legendre" else "S and H launches")
+                                                      if args.s_method == "legendre" else
+                                                      "S launch; H by the addition theorem"
+                                                      if args.h_method == "spherical" else "S and H launches")
                                + ("; H as Alg. 3's L^H R" if args.h_method == "alg3" else "") + ")",
                      "kernel_ms": round(k_ms, 4),
                      "peak_source": f"{src} bf16 {peak_kind} x 1.0 (fp16 = bf16 nominal rate)"},
@@ -404,7 +438,16 @@ def run_ours(args):
                         "kernel_ms": round(float(np.mean(abms)), 4),
                         "achieved": round(32 * p.n_atoms * p.n_L * sum(ngs) / (float(np.mean(abms)) * 1e-3) / 1e9, 1),
                         "peak": hbm, "unit": "GB/s",
-                        "frac": round(32 * p.n_atoms * p.n_L * sum(ngs) / (float(np.mean(abms)) * 1e-3) / 1e9 / hbm, 4)},
+                        "frac": round(32 * p.n_atoms * p.n_L * sum(ngs) / (float(np.mean(abms)) * 1e-3) / 1e9 / hbm, 4),
+                        # what bounds it: 8 FP64 instructions per (atom, L, G) (the
+                        # complex phase x Y product, 2 DMUL + 2 DFMA, then 4 DMUL by
+                        # a_l and b_l) against the FP64 issue rate of the measured DGEMM
+                        # (one DFMA per 2 flops)
+                        "fp64_issue": {"instr_per_elem": 8,
+                                       "achieved_ginstr_s": round(ab_instr / (float(np.mean(abms)) * 1e-3) / 1e9, 1),
+                                       "peak_ginstr_s": round(fp64_peak * 1e3 / 2, 1),
+                                       "frac": round(ab_instr / (float(np.mean(abms)) * 1e-3) / 1e9
+                                                     / (fp64_peak * 1e3 / 2), 4)}},
         "e2e": e2e,
         "gpu_launches": launches_per_step(args) * args.steps,
         "clocks": clk,
@@ -422,6 +465,28 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
+def spherical_part(T, lmax):
+    """The l-diagonal part of T per slot: t[slot][l] = (t^AA_l, t^BB_l, Re t^BA_l,
+    Im t^BA_l), the means over m of the diagonal entries of each block, and the
+    matrix it makes (T^XY_{(lm),(lm)} = t^XY_l, zero elsewhere)."""
+    ns, n = T.shape[0], T.shape[1]
+    nl = n // 2
+    t = np.zeros((ns, lmax + 1, 4))
+    Ts = np.zeros_like(T)
+    for s_ in range(ns):
+        for l in range(lmax + 1):
+            L = np.arange(l * l, (l + 1) * (l + 1))
+            taa = float(np.mean(T[s_, L, L].real))
+            tbb = float(np.mean(T[s_, nl + L, nl + L].real))
+            tba = complex(np.mean(T[s_, nl + L, L]))
+            t[s_, l] = (taa, tbb, tba.real, tba.imag)
+            Ts[s_, L, L] = taa
+            Ts[s_, nl + L, nl + L] = tbb
+            Ts[s_, nl + L, L] = tba
+            Ts[s_, L, nl + L] = np.conj(tba)
+    return Ts, t
+
+
 def launches_per_step(args):
     """Kernels one timed step launches: ab_prep and ab_assemble; the S half
     (opform_S, slicer, contraction; or the addition theorem's split and
@@ -435,6 +500,10 @@ def launches_per_step(args):
         from A/B, the FP64 product and copy kernels and the slicer."""
     n = 2
     n += 2 if args.s_method == "legendre" else 3
+    if args.h_method == "spherical":
+        # T is its spherical part: the W factor formed and sliced, and the
+        # addition-theorem kernel; no factorisation, H operands or H contraction
+        return n + 3
     n += 1
     if args.h_method == "alg3":
         n += 8 if args.operands == "factored" else 3
@@ -585,9 +654,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--refined-cols", type=int, default=1024,
                     help="columns of the host-BLAS Alg. 3 comparator")
-    ap.add_argument("--h-method", choices=["factored", "alg3"], default="factored",
-                    help="H as one Hermitian rank-K update after factorising T (default) or by the "
-                         "paper's Alg. 3 sequence (zher2k + zherkx as one L^H R contraction)")
+    ap.add_argument("--h-method", choices=list(H_METHODS), default="factored",
+                    help="H as one Hermitian rank-K update after factorising T (default), by the "
+                         "paper's Alg. 3 sequence (zher2k + zherkx as one L^H R contraction), or "
+                         "(spherical) by the addition theorem on the workload with T replaced by "
+                         "its spherical part")
     ap.add_argument("--s-method", choices=["contraction", "legendre"], default="contraction",
                     help="S by the slice contraction (default) or by the addition theorem")
     ap.add_argument("--graph", action="store_true",

@@ -153,6 +153,7 @@ struct flapw_ctx {
   DevBuf d_opA, d_opB, d_opSLA, d_opSLB, d_oprexp, d_optiles, d_opP;
   DevBuf d_khat, d_typeatoms;    // S by the addition theorem: Khat per G, atoms by type
   DevBuf d_sdf;                  // its double-float inputs (emulated precision)
+  DevBuf d_hdf;                  // those of H's spherical part by the addition theorem
   bool khat_valid = false;       // both depend on the crystal only
   std::vector<OpTile> optiles;
   CUtensorMap opmap_a{}, opmap_b{};
@@ -1198,6 +1199,9 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   if (s_legendre && h->opt.precision == FLAPW_PREC_EMU)
     CK(h, h->d_sdf.ensure(slegendre_df_floats2(h->n_types, h->lmax, h->n_atoms, h->g_total) * 8),
        "workspace");
+  if (h_sph && h->opt.precision == FLAPW_PREC_EMU)
+    CK(h, h->d_hdf.ensure(slegendre_df_floats2(h->n_types, h->lmax, h->n_atoms, h->g_total) * 8),
+       "workspace");
   // emulated path with factored operands: the H operands come from the
   // tensor-core product of conj(C^H) and W (opgemm.cu)
   // (for Alg. 3 the product of M = [[T^BA, T^BB/2], [T^AA, 0]] and W)
@@ -1545,6 +1549,9 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       hl.combo_start = oa.combo_start;
       hl.n_combo = n_combo;
       hl.scale = 4.0 * M_PI / h->volume;
+      hl.n_atoms = h->n_atoms;
+      hl.n_types = h->n_types;
+      hl.dfw = (h->opt.precision == FLAPW_PREC_EMU) ? h->d_hdf.as<float2>() : nullptr;
     }
     if (h_zero) {
       // T is its spherical part: no factorisation, operands or contraction for H
@@ -1667,7 +1674,8 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
                              (uintptr_t)h->d_T.p, (uintptr_t)h->d_stageOut.p, (uintptr_t)h->d_emu_tiles.p,
                              (uintptr_t)h->d_opA.p, (uintptr_t)h->d_opB.p, (uintptr_t)h->d_opSLA.p,
                              (uintptr_t)h->d_opSLB.p, (uintptr_t)h->d_oprexp.p, (uintptr_t)h->d_optiles.p,
-                             (uintptr_t)h->d_opP.p, (uintptr_t)h->d_split.p};
+                             (uintptr_t)h->d_opP.p, (uintptr_t)h->d_split.p, (uintptr_t)h->d_sdf.p,
+                             (uintptr_t)h->d_hdf.p};
   for (int k = 0; k < nk; ++k) {
     key.push_back((uintptr_t)H[k]);
     key.push_back((uintptr_t)S[k]);
@@ -1713,8 +1721,8 @@ int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const i
     if (sg != 1 && sg != -1) return fail(h, FLAPW_ERR_ARG, "sigma entries must be +1 or -1");
     (sg > 0 ? pos : neg).push_back(k);
   }
-  const int64_t kp_pad = round_up((int64_t)pos.size(), kChunk);
-  const int64_t k_alloc = std::max<int64_t>(kp_pad + round_up((int64_t)neg.size(), kChunk), kChunk);
+  const int64_t kp_pad = neg_base((int)pos.size());
+  const int64_t k_alloc = std::max<int64_t>((int64_t)k_chunks((int)pos.size(), (int)neg.size()) * kChunk, kChunk);
   std::vector<int> kmap(k_alloc, -1);
   for (size_t i = 0; i < pos.size(); ++i) kmap[i] = pos[i];
   for (size_t i = 0; i < neg.size(); ++i) kmap[kp_pad + i] = neg[i];
@@ -1859,11 +1867,12 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
       s.n_pos = kpk[1];
       s.n_neg = kpk[2];
       // tensor flops executed: per tile, slice pair and 16-wide K step of
-      // the 64-wide chunks (each sign block padded to whole chunks), an R and
-      // an I pass of M = 256, N = 128, K = 16 MMAs
+      // the 64-wide chunks (the sigma = -1 block from the next multiple of 16
+      // after the sigma = +1 one, the end padded to a whole chunk), an R and an
+      // I pass of M = 256, N = 128, K = 16 MMAs
       const int S_ = slices_of(h);
       const double pairs = S_ * (S_ + 1) / 2.0;
-      const double ksH = 4.0 * (std::ceil(kpk[1] / 64.0) + std::ceil(kpk[2] / 64.0));
+      const double ksH = 4.0 * k_chunks(kpk[1], kpk[2]);
       const double ksS = (h->opt.s_method == FLAPW_S_LEGENDRE)
                              ? 0.0
                              : 4.0 * std::ceil((double)h->n_atoms * 2 * h->n_L / 64.0);

@@ -16,6 +16,13 @@ namespace flapw {
 constexpr int kMaxLmax = 12;
 constexpr int kMaxNL = (kMaxLmax + 1) * (kMaxLmax + 1);
 constexpr int kChunk = 64;        // columns of K per pipeline step (one 128-byte fp16 row)
+// The sigma = -1 rows of an operand start at the first multiple of kSignAlign
+// at or after the sigma = +1 rows (one tcgen05 MMA K step of fp16), so that the
+// two groups together fill whole K chunks up to the last one.
+constexpr int kSignAlign = 16;
+__host__ __device__ inline int neg_base(int kp) { return (kp + kSignAlign - 1) / kSignAlign * kSignAlign; }
+// K chunks of an operand with kp rows of sigma = +1 and kn of sigma = -1.
+__host__ __device__ inline int k_chunks(int kp, int kn) { return (neg_base(kp) + kn + kChunk - 1) / kChunk; }
 constexpr int kSliceBits = 7;     // magnitude bits per emulation slice
 constexpr int kUnitChunks = 64;   // K chunks per unit: the longest exact FP32 accumulation
                                   // (4096 terms, digit products <= 2^12)
@@ -28,7 +35,7 @@ struct Prob {
   int row_base;   // first row of L in the operand / slice arrays
   int n_g;        // N_G of the problem
   int kp;         // operand rows (K index) with sigma = +1; columns [0, kp)
-  int kn;         // rows with sigma = -1; columns [ceil(kp/64)*64, ... + kn)
+  int kn;         // rows with sigma = -1; columns [neg_base(kp), ... + kn)
   int layout;     // FLAPW_LAYOUT_*
   int col_base;   // first row of R (= row_base for L = R)
   int64_t ld;     // leading dimension of the full layout
@@ -277,7 +284,7 @@ struct SLegArgs {
 };
 size_t slegendre_df_floats2(int n_types, int lmax, int n_atoms, int64_t G);
 // The spherical part of H by the addition theorem (slegendre.cu), on the
-// 64 x 64 lower tiles of the H problems, FP64.
+// 64 x 64 lower tiles of the H problems, in FP64 or double-float.
 struct HLegArgs {
   const Prob* probs;       // problems (row_base - h_row0 = first global plane wave)
   int64_t h_row0;
@@ -294,6 +301,9 @@ struct HLegArgs {
   const int* combo_start;  // [n_combo + 1]
   int n_combo;
   double scale;            // 4 pi / Omega
+  int n_atoms, n_types;
+  float2* dfw;             // double-float workspace (slegendre_df_floats2 pairs):
+                           // evaluate in double-float; null: in FP64
 };
 // add: the spherical part is added to the lower triangle already written.
 cudaError_t launch_hlegendre(const HLegArgs& a, const F64Tile* tiles, int n_tiles, bool add, cudaStream_t st);

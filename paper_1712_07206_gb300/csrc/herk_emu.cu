@@ -43,9 +43,10 @@
 // of one pass overlaps the MMAs of the next.  Against one CTA per tile (M=128)
 // the pair halves the B bytes each SM loads per MMA flop, and 128-wide stages
 // halve the producer/MMA hand-offs per flop; both bound the tensor pipe's
-// occupancy.  Rows with sigma = -1 sit in the K chunks from Kp_pad on; their
-// MMAs set the descriptor's negate-B bit, so H = Z^H diag(sigma) Z accumulates
-// both signs in the same sums and has the schedule of S.
+// occupancy.  Rows with sigma = -1 sit in the K columns from neg_base(kp), the
+// next multiple of the 16-wide MMA K step; the MMAs of those steps set the
+// descriptor's negate-B bit, so H = Z^H diag(sigma) Z accumulates both signs in
+// the same sums and has the schedule of S.
 //
 // Warp roles (both CTAs): warp 0 TMA producer, warp 1 TMEM allocator (and in
 // CTA 0 the MMA issuer), warps 2-3 idle, warps 4..11 drain/epilogue (warp w
@@ -158,12 +159,13 @@ __device__ __forceinline__ void umma_commit_both(uint32_t bar) {
 // (i.e. 1-based levels i + j + 2 <= s + 1), i = 0..t.  Every role walks the
 // same order.
 
-// K units: the chunks [0, kpc) of the sigma = +1 rows and [kpc, kpc + knc)
-// of the sigma = -1 rows (their MMAs negate B, so both signs accumulate in
-// one sum, bounded by the magnitudes alone), cut into the fewest equal units
-// of at most kUnitChunks.
+// K units: the chunks [0, k_chunks(kp, kn)) holding the sigma = +1 rows from
+// column 0 and the sigma = -1 rows from column neg_base(kp), a multiple of the
+// 16-wide MMA K step (the MMAs of the steps from there on negate B, so both
+// signs accumulate in one sum, bounded by the magnitudes alone), cut into the
+// fewest equal units of at most kUnitChunks.
 struct Units {
-  int kpc, knc;  // positive / negative chunk counts
+  int kns;       // first 16-wide K step of the sigma = -1 rows
   int cb, ce;    // the chunk window of this tile part: [cb, ce)
   __device__ int total() const { return ce - cb; }
   __device__ int count() const { return (total() + kUnitChunks - 1) / kUnitChunks; }
@@ -185,9 +187,8 @@ __device__ __forceinline__ int pair_span(int i, int j) {
 // the last wave split over several pairs; EmuTile::split).
 __device__ __forceinline__ Units units_of(const Prob& P, int split) {
   Units u;
-  u.kpc = (P.kp + kChunk - 1) / kChunk;
-  u.knc = (P.kn + kChunk - 1) / kChunk;
-  const int parts = split_parts(split), part = split_part(split), t = u.kpc + u.knc;
+  u.kns = neg_base(P.kp) / kSignAlign;
+  const int parts = split_parts(split), part = split_part(split), t = k_chunks(P.kp, P.kn);
   u.cb = (int)((long long)part * t / parts);
   u.ce = (int)((long long)(part + 1) * t / parts);
   return u;
@@ -500,10 +501,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t sbase = smem_u32(smem + stage * kStageBytes);
             for (int q = 0; q < nv; ++q) {
               const uint64_t da = sdesc(sbase + q * kTileA), db = sdesc(sbase + kOffB + q * kTileB);
-              const uint32_t id = (c + q >= sc.U.kpc) ? (idesc | kNegateB) : idesc;  // sigma = -1
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t id = (4 * (c + q) + kk >= sc.U.kns) ? (idesc | kNegateB) : idesc;  // sigma = -1
                 umma_pair(d, da + 2 * kk, db + 2 * kk, id, (c > sc.s0 || q > 0 || kk > 0) ? 1u : 0u);
+              }
             }
             umma_commit_both(empty_bar(stage));
             ++it;

@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(256) herk_f64_kernel(const double2* __restrict
   const Prob P = probs[t.prob];
   const int row0 = t.ib * kTM, col0 = t.jb * kTN;
   const int kp = P.kp, kn = P.kn;
-  const int kp_pad = (kp + kChunk - 1) / kChunk * kChunk;
+  const int kp_pad = neg_base(kp);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp & 1, wn = warp >> 1;  // 2 x 4 warps: 32 rows x 16 cols each
   double cre[4][2][2], cim[4][2][2];

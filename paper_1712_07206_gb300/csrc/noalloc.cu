@@ -158,8 +158,8 @@ extern "C" int flapw_herk_noalloc(const void* Z, int64_t ldz, int K, int N, cons
       sb.w[k >> 5] |= 1u << (k & 31);
     }
   }
-  const int64_t kp_pad = (kp + kChunk - 1) / kChunk * kChunk;
-  int64_t k_alloc = kp_pad + (kn + kChunk - 1) / kChunk * kChunk;
+  const int64_t kp_pad = neg_base(kp);
+  int64_t k_alloc = (int64_t)k_chunks(kp, kn) * kChunk;
   if (k_alloc < kChunk) k_alloc = kChunk;
   const int ncb = (N + 63) / 64;
   const int n_tiles = count_tiles(ncb);

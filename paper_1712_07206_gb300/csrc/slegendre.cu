@@ -174,33 +174,44 @@ __global__ void __launch_bounds__(256) slegendre_kernel(SLegArgs a, const F64Til
   }
 }
 
-// Double-float copies of the kernel's inputs: rows (2l+1) a_l and (2l+1) U^2
-// b_l, columns a_l and b_l ([4][t][l][G]), phases ([atom][G] as Re, Im
-// pairs) and Khat ([G][3]).  One thread per plane wave.
-__global__ void __launch_bounds__(128) slegendre_split_kernel(SLegArgs a) {
-  const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t G = a.g_total;
-  if (gi >= G) return;
-  const int L1 = a.lmax + 1;
-  const int64_t nr = (int64_t)a.n_types * L1 * G;
-  float2* rad = a.dfw;
+// Double-float copies of the Legendre kernels' inputs for plane wave gi:
+// rows (2l+1) a_l and (2l+1) U^2 b_l (U = null: (2l+1) b_l, for H), columns
+// a_l and b_l ([4][t][l][G]), phases ([atom][G] as Re, Im pairs) and Khat
+// ([G][3]).
+__device__ void split_inputs(int64_t gi, int64_t G, int L1, int n_types, int n_atoms, const double* U,
+                             const double* al_, const double* bl_, const double2* ph_, const double* khat,
+                             float2* rad) {
+  const int64_t nr = (int64_t)n_types * L1 * G;
   float2* ph = rad + 4 * nr;
-  float2* kh = ph + 2 * (int64_t)a.n_atoms * G;
-  for (int t = 0; t < a.n_types; ++t)
+  float2* kh = ph + 2 * (int64_t)n_atoms * G;
+  for (int t = 0; t < n_types; ++t)
     for (int l = 0; l < L1; ++l) {
       const int64_t ro = ((int64_t)t * L1 + l) * G + gi;
-      const double u = a.U[t * L1 + l], al = a.al[ro], bl = a.bl[ro];
+      const double u = U ? U[t * L1 + l] : 1.0, al = al_[ro], bl = bl_[ro];
       rad[ro] = dfl::split((2 * l + 1) * al);
       rad[nr + ro] = dfl::split((2 * l + 1) * u * u * bl);
       rad[2 * nr + ro] = dfl::split(al);
       rad[3 * nr + ro] = dfl::split(bl);
     }
-  for (int at = 0; at < a.n_atoms; ++at) {
-    const double2 v = a.ph[(int64_t)at * G + gi];
+  for (int at = 0; at < n_atoms; ++at) {
+    const double2 v = ph_[(int64_t)at * G + gi];
     ph[2 * ((int64_t)at * G + gi)] = dfl::split(v.x);
     ph[2 * ((int64_t)at * G + gi) + 1] = dfl::split(v.y);
   }
-  for (int c = 0; c < 3; ++c) kh[3 * gi + c] = dfl::split(a.khat[3 * gi + c]);
+  for (int c = 0; c < 3; ++c) kh[3 * gi + c] = dfl::split(khat[3 * gi + c]);
+}
+
+// One thread per plane wave.
+__global__ void __launch_bounds__(128) slegendre_split_kernel(SLegArgs a) {
+  const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= a.g_total) return;
+  split_inputs(gi, a.g_total, a.lmax + 1, a.n_types, a.n_atoms, a.U, a.al, a.bl, a.ph, a.khat, a.dfw);
+}
+
+__global__ void __launch_bounds__(128) hlegendre_split_kernel(HLegArgs a) {
+  const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= a.g_total) return;
+  split_inputs(gi, a.g_total, a.lmax + 1, a.n_types, a.n_atoms, nullptr, a.al, a.bl, a.ph, a.khat, a.dfw);
 }
 
 // slegendre_kernel in double-float: 512 threads of 2 x 4 elements (the double-float
@@ -334,7 +345,8 @@ __global__ void __launch_bounds__(kDfThreads) slegendre_df_kernel(SLegArgs a, co
 //             [t^AA a'a + t^BB b'b + Re t^BA (a'b + b'a) + i Im t^BA (b'a - a'b)]_l
 // with a' = a_l(K'), a = a_l(K) (b likewise) of the combination's type, t of
 // its slot (t^AB = conj t^BA: T is Hermitian), rho_c the phase sum over the
-// atoms of the (slot, type) combination c.  FP64 throughout.  add: the result
+// atoms of the (slot, type) combination c.  FP64 on the FP64 path, double-float
+// (hlegendre_df_kernel) on the emulated path.  add: the result
 // is added to the lower triangle already in P.out (the contraction of the
 // rest of T), otherwise written.
 __global__ void __launch_bounds__(256) hlegendre_kernel(HLegArgs a, const F64Tile* __restrict__ tiles,
@@ -468,12 +480,160 @@ __global__ void __launch_bounds__(256) hlegendre_kernel(HLegArgs a, const F64Til
   }
 }
 
+// hlegendre_kernel in double-float (the emulated path): the layout of
+// slegendre_df_kernel, 512 threads of 2 x 4 elements, with the complex
+// Legendre weight of the (slot, type) combinations.
+__global__ void __launch_bounds__(kDfThreads) hlegendre_df_kernel(HLegArgs a, const F64Tile* __restrict__ tiles,
+                                                                  int add) {
+  using dfl::df;
+  __shared__ float2 kh[2][kT][3];
+  __shared__ float2 rad[4][kL1][kT];
+  __shared__ float4 phs[2][kChunkAtoms][kT];
+  __shared__ float2 coef[kL1][4];
+  __shared__ float2 rec_ab[kL1][2];
+  const F64Tile T = tiles[blockIdx.x];
+  const Prob P = a.probs[T.prob];
+  const int64_t ng = P.n_g;
+  const int64_t g0 = P.row_base - a.h_row0;
+  const int r0 = T.ib * kT, c0 = T.jb * kT;
+  const int tid = threadIdx.x, ty = tid / (kT / kDfCols), tx = tid % (kT / kDfCols);
+  const int L1 = a.lmax + 1;
+  const int64_t G = a.g_total;
+  const int64_t nr = (int64_t)a.n_types * L1 * G;
+  const float2* radg = a.dfw;
+  const float4* phg = reinterpret_cast<const float4*>(a.dfw + 4 * nr);
+  const float2* khg = a.dfw + 4 * nr + 2 * (int64_t)a.n_atoms * G;
+  const float2 zero2 = make_float2(0.f, 0.f);
+  if (tid < kL1) {
+    rec_ab[tid][0] = dfl::split((double)(2 * tid + 1) / (double)(tid + 1));
+    rec_ab[tid][1] = dfl::split((double)tid / (double)(tid + 1));
+  }
+  for (int i = tid; i < 2 * kT * 3; i += kDfThreads) {
+    const int w = i / (kT * 3), e = i % (kT * 3), g = e / 3, c = e % 3;
+    const int64_t gl = (w == 0 ? r0 : c0) + g;
+    kh[w][g][c] = (gl < ng) ? khg[3 * (g0 + gl) + c] : zero2;
+  }
+  df Hr[kDfRows][kDfCols], Hi[kDfRows][kDfCols];
+#pragma unroll
+  for (int i = 0; i < kDfRows; ++i)
+#pragma unroll
+    for (int j = 0; j < kDfCols; ++j) Hr[i][j] = Hi[i][j] = df{0.f, 0.f};
+
+  for (int cb = 0; cb < a.n_combo; ++cb) {
+    const int t = a.combo_type[cb], sl = a.combo_slot[cb];
+    __syncthreads();
+    for (int i = tid; i < 4 * L1 * kT; i += kDfThreads) {
+      const int w = i / (L1 * kT), e = i % (L1 * kT), l = e / kT, g = e % kT;
+      const int64_t gl = ((w < 2) ? r0 : c0) + g;
+      rad[w][l][g] = (gl < ng) ? radg[w * nr + ((int64_t)t * L1 + l) * G + g0 + gl] : zero2;
+    }
+    if (tid < 4 * L1) coef[tid >> 2][tid & 3] = dfl::split(a.tsph[((int64_t)sl * L1 + (tid >> 2)) * 4 + (tid & 3)]);
+    df rr[kDfRows][kDfCols], ri[kDfRows][kDfCols];  // rho_c
+#pragma unroll
+    for (int i = 0; i < kDfRows; ++i)
+#pragma unroll
+      for (int j = 0; j < kDfCols; ++j) rr[i][j] = ri[i][j] = df{0.f, 0.f};
+    const int a0 = a.combo_start[cb], a1 = a.combo_start[cb + 1];
+    for (int ab = a0; ab < a1; ab += kChunkAtoms) {
+      const int na = min(kChunkAtoms, a1 - ab);
+      __syncthreads();
+      for (int i = tid; i < 2 * kChunkAtoms * kT; i += kDfThreads) {
+        const int w = i / (kChunkAtoms * kT), e = i % (kChunkAtoms * kT), q = e / kT, g = e % kT;
+        const int64_t gl = (w == 0 ? r0 : c0) + g;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < na && gl < ng) v = phg[(int64_t)a.combo_atoms[ab + q] * G + g0 + gl];
+        phs[w][q][g] = v;
+      }
+      __syncthreads();
+      for (int q = 0; q < na; ++q) {
+        float4 pr[kDfRows], pc[kDfCols];
+#pragma unroll
+        for (int i = 0; i < kDfRows; ++i) pr[i] = phs[0][q][ty * kDfRows + i];
+#pragma unroll
+        for (int j = 0; j < kDfCols; ++j) pc[j] = phs[1][q][tx * kDfCols + j];
+#pragma unroll
+        for (int i = 0; i < kDfRows; ++i) {
+          const df ar{pr[i].x, pr[i].y}, ai{pr[i].z, pr[i].w};
+#pragma unroll
+          for (int j = 0; j < kDfCols; ++j) {  // conj(pr) pc
+            const df br{pc[j].x, pc[j].y}, bi{pc[j].z, pc[j].w};
+            rr[i][j] = dfl::fma(ar, br, dfl::fma(ai, bi, rr[i][j]));
+            ri[i][j] = dfl::fma(ar, bi, dfl::fma(dfl::neg(ai), br, ri[i][j]));
+          }
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kDfRows; ++i) {
+      const int rw = ty * kDfRows + i;
+#pragma unroll
+      for (int j = 0; j < kDfCols; ++j) {
+        const int cl = tx * kDfCols + j;
+        const df x = dfl::fma(dfl::make(kh[0][rw][0]), dfl::make(kh[1][cl][0]),
+                              dfl::fma(dfl::make(kh[0][rw][1]), dfl::make(kh[1][cl][1]),
+                                       dfl::mul(dfl::make(kh[0][rw][2]), dfl::make(kh[1][cl][2]))));
+        df pm{1.f, 0.f}, p{1.f, 0.f};  // P_{l-1}, P_l
+        df Lr{0.f, 0.f}, Li{0.f, 0.f};
+        for (int l = 0; l < L1; ++l) {
+          if (l == 1) p = x;
+          const df ra = dfl::make(rad[0][l][rw]), rb = dfl::make(rad[1][l][rw]);
+          const df ca = dfl::make(rad[2][l][cl]), cb_ = dfl::make(rad[3][l][cl]);
+          const df ab_ = dfl::mul(ra, cb_), ba = dfl::mul(rb, ca);
+          // t^AA a'a + t^BB b'b + Re t^BA (a'b + b'a), and Im t^BA (b'a - a'b)
+          const df wr = dfl::fma(dfl::make(coef[l][0]), dfl::mul(ra, ca),
+                                 dfl::fma(dfl::make(coef[l][1]), dfl::mul(rb, cb_),
+                                          dfl::mul(dfl::make(coef[l][2]), dfl::add(ab_, ba))));
+          const df wi = dfl::mul(dfl::make(coef[l][3]), dfl::add(ba, dfl::neg(ab_)));
+          Lr = dfl::fma(p, wr, Lr);
+          Li = dfl::fma(p, wi, Li);
+          if (l >= 1) {
+            const df pn = dfl::fma(dfl::mul(dfl::make(rec_ab[l][0]), x), p,
+                                   dfl::neg(dfl::mul(dfl::make(rec_ab[l][1]), pm)));
+            pm = p;
+            p = pn;
+          }
+        }
+        // rho_c x L_c, complex
+        Hr[i][j] = dfl::fma(rr[i][j], Lr, dfl::fma(dfl::neg(ri[i][j]), Li, Hr[i][j]));
+        Hi[i][j] = dfl::fma(rr[i][j], Li, dfl::fma(ri[i][j], Lr, Hi[i][j]));
+      }
+    }
+  }
+  double* outd = reinterpret_cast<double*>(P.out);
+#pragma unroll
+  for (int i = 0; i < kDfRows; ++i) {
+    const int64_t gr = r0 + ty * kDfRows + i;
+#pragma unroll
+    for (int j = 0; j < kDfCols; ++j) {
+      const int64_t gc = c0 + tx * kDfCols + j;
+      if (gr < ng && gc <= gr) {
+        const int64_t o = (P.layout == FLAPW_LAYOUT_LOWER_PACKED) ? gc * ng - gc * (gc - 1) / 2 + (gr - gc)
+                                                                   : gc * P.ld + gr;
+        const double re = a.scale * dfl::to_double(Hr[i][j]), im = a.scale * dfl::to_double(Hi[i][j]);
+        if (add) {
+          outd[2 * o] += re;
+          outd[2 * o + 1] += im;
+        } else {
+          outd[2 * o] = re;
+          outd[2 * o + 1] = im;
+        }
+      }
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_hlegendre(const HLegArgs& a, const F64Tile* tiles, int n_tiles, bool add, cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   if (a.lmax < 0 || a.lmax > kMaxLmax) return cudaErrorInvalidValue;
-  hlegendre_kernel<<<n_tiles, 256, 0, st>>>(a, tiles, add ? 1 : 0);
+  if (a.dfw) {
+    hlegendre_split_kernel<<<(unsigned)((a.g_total + 127) / 128), 128, 0, st>>>(a);
+    hlegendre_df_kernel<<<n_tiles, kDfThreads, 0, st>>>(a, tiles, add ? 1 : 0);
+  } else {
+    hlegendre_kernel<<<n_tiles, 256, 0, st>>>(a, tiles, add ? 1 : 0);
+  }
   return cudaGetLastError();
 }
 

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256, 4) slicer_kernel(const double2* __restric
     kp = P.kp;
     kn = P.kn;
   }
-  const int64_t kp_pad = (kp + kChunk - 1) / kChunk * kChunk;
+  const int64_t kp_pad = neg_base((int)kp);
   const double2* zr = Z + row * k_alloc;
   auto valid = [&](int64_t c) { return c < kp || (c >= kp_pad && c < kp_pad + kn); };
   unsigned long long m = 0;

@@ -774,8 +774,7 @@ __global__ void layout_kernel(const int* npos, const int* nneg, const int* atom_
     p += npos[atom_slot[a]];
     q += nneg[atom_slot[a]];
   }
-  const int kp_pad = (p + kChunk - 1) / kChunk * kChunk;
-  kpk[0] = kp_pad;
+  kpk[0] = neg_base(p);
   kpk[1] = p;
   kpk[2] = q;
   for (int k = 0; k < n_k; ++k) {  // problems [0, n_k) are the H problems

@@ -1,6 +1,5 @@
-"""Host-side helpers of bench.py (no GPU): launch counts per mode, the bytes
-the library copies to host memory, the measured-peak file and the traffic
-table."""
+"""Host-side helpers of bench.py (no GPU): launch counts per mode, the
+spherical part of T, the measured-peak file and the traffic table."""
 import importlib.util
 import os
 import sys
@@ -34,6 +33,7 @@ class Args:
     ("from_ab", "contraction", "factored", 10),
     ("factored", "contraction", "alg3", 14),
     ("from_ab", "contraction", "alg3", 9),
+    ("factored", "contraction", "spherical", 8),
 ])
 def test_launches_per_step(bench, operands, s_method, h_method, n):
     assert bench.launches_per_step(Args(operands, s_method, h_method)) == n
@@ -127,3 +127,25 @@ def test_cpu_baseline_calibrates_and_measures_parity(bench, layout_name):
     assert int(out["sample"].split()[0]) <= 20
     assert out["parity_rel_err"]["H"] > 1e-6 and out["parity_rel_err"]["S"] < 1e-15
     assert "parity_rel_err_fp64_path" not in out
+
+
+def test_spherical_part_is_a_projection(bench):
+    import numpy as np
+    import paper_1712_07206_gb300 as fl
+    assert bench.H_METHODS == {"factored": fl.H_FACTORED, "alg3": fl.H_ALG3, "spherical": fl.H_SPHERICAL}
+    from paper_1712_07206_gb300 import inputs
+    p = inputs.small(5, n_atoms=2, n_types=2, lmax=3)
+    Ts, t = bench.spherical_part(p.T, p.lmax)
+    nl = p.n_L
+    assert t.shape == (p.T.shape[0], p.lmax + 1, 4)
+    assert np.allclose(Ts, np.conj(np.transpose(Ts, (0, 2, 1))))
+    # l-diagonal: nonzero only where both indices have the same L
+    idx = np.arange(2 * nl) % nl
+    assert np.all(Ts[:, idx[:, None] != idx[None, :]] == 0)
+    # a second projection changes nothing
+    Ts2, t2 = bench.spherical_part(Ts, p.lmax)
+    assert np.allclose(Ts2, Ts, rtol=0, atol=1e-15) and np.allclose(t2, t, rtol=0, atol=1e-15)
+    # the l = 1 entries are the mean over m of T's diagonal entries
+    L = np.arange(1, 4)
+    assert np.isclose(t[0, 1, 0], np.mean(p.T[0, L, L].real))
+    assert np.isclose(t[1, 1, 2] + 1j * t[1, 1, 3], np.mean(p.T[1, nl + L, L]))

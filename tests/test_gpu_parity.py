@@ -38,6 +38,13 @@ def test_ab_matches_oracle(seed, lmax, nt):
         Ag, Bg = ab_block(p, h, A, k), ab_block(p, h, B, k)
         assert np.abs(Ag - Ao).max() <= 1e-13 * np.abs(Ao).max()
         assert np.abs(Bg - Bo).max() <= 1e-13 * np.abs(Bo).max()
+        # every (atom, L) row against its own size too, so that the small rows
+        # of high l (j_l(KR) ~ (KR)^l / (2l+1)!!) are checked in relative terms
+        for X, Xo in ((Ag, Ao), (Bg, Bo)):
+            num = np.linalg.norm(X - Xo, axis=2)
+            den = np.linalg.norm(Xo, axis=2)
+            assert (den > 0).all()
+            assert (num / den).max() <= 1e-12, (num / den).max()
 
 
 def test_ab_config2_sampled():

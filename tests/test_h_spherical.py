@@ -12,7 +12,7 @@ import pytest
 import paper_1712_07206_gb300 as fl
 from paper_1712_07206_gb300 import inputs
 
-from helpers import TOL_EMU, TOL_F64, alloc_out, herm_relerr, lower_to_full, oracle_hs, run_ab
+from helpers import TOL_EMU, TOL_F64, alloc_out, columns_from_lower, herm_relerr, lower_to_full, oracle_hs, run_ab
 
 pytestmark = pytest.mark.gpu
 
@@ -92,3 +92,43 @@ def test_spherical_split_needs_t_sph():
     with pytest.raises(fl.FlapwError) as e:
         h.build_HS(p.T, p.atom_slot, p.U, A, B, [alloc_out(ng, 0)], [alloc_out(ng, 0)])
     assert e.value.code == -6
+
+
+@pytest.mark.parametrize("precision,tol", [(fl.PREC_EMU, TOL_EMU), (fl.PREC_FP64, TOL_F64)])
+def test_config2_with_spherical_T_has_no_H_contraction(precision, tol):
+    # config 2 with T replaced by its spherical part (per slot and l the mean
+    # over m of each block's diagonal): H comes from the addition theorem alone
+    # (double-float on the emulated path, FP64 on the other), S from the
+    # contraction; sampled full columns against the oracle of the same T
+    import oracle
+    p = inputs.config2()
+    nl, L1 = p.n_L, p.lmax + 1
+    t = np.zeros((p.T.shape[0], L1, 4))
+    Ts = np.zeros_like(p.T)
+    for s in range(p.T.shape[0]):
+        for l in range(L1):
+            L = np.arange(l * l, (l + 1) * (l + 1))
+            tba = np.mean(p.T[s, nl + L, L])
+            t[s, l] = (np.mean(p.T[s, L, L].real), np.mean(p.T[s, nl + L, nl + L].real), tba.real, tba.imag)
+            Ts[s, L, L] = t[s, l, 0]
+            Ts[s, nl + L, nl + L] = t[s, l, 1]
+            Ts[s, nl + L, L] = tba
+            Ts[s, L, nl + L] = np.conj(tba)
+    p.T = Ts
+    opt = fl.default_options(precision=precision, operands=fl.OPERANDS_FACTORED, h_method=fl.H_SPHERICAL)
+    h = fl.from_problem(p, opt)
+    _, A, B = run_ab(p, h)
+    h.set_spherical_T(t)
+    ng = h.num_g(0)
+    H, S = alloc_out(ng, 0), alloc_out(ng, 0)
+    h.build_HS(p.T, p.atom_slot, p.U, A, B, [H], [S])
+    h.sync()
+    st = h.stats()
+    assert st["n_pos"] + st["n_neg"] == 0
+    n3 = h.gvectors(0)
+    cols = [0, 1, 63, 64, 1777, 2048, ng - 2, ng - 1]
+    Ho, So = oracle.hs_columns(p, 0, n3, cols)
+    eh = np.linalg.norm(columns_from_lower(H, ng, 0, cols) - Ho) / np.linalg.norm(Ho)
+    es = np.linalg.norm(columns_from_lower(S, ng, 0, cols) - So) / np.linalg.norm(So)
+    assert eh <= tol and es <= tol, (eh, es)
+    h.destroy()
