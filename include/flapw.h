@@ -299,6 +299,27 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
 int flapw_herk(flapw_handle h, const void* Z, int64_t ldz, int K, int N, const int* sigma,
                void* H, int64_t ldh, void* stream);
 
+/* The generalised eigenproblem of Sec. 2 for one k-point, H c = lambda S c,
+ * on matrices this library built (Hermitian H, Hermitian positive definite S).
+ *   H, S: device, complex128, column-major, lower triangle read (the
+ *       flapw_build_HS full layout: ldh = lds = N_G(k)); overwritten: H by the
+ *       eigenvectors as columns, S-orthonormal (C^H S C = I), when vectors != 0
+ *       (otherwise destroyed), S by its Cholesky factor L (S = L L^H, lower).
+ *   w[n] (host or device): the eigenvalues, ascending.
+ * The solve is cuSOLVER's zhegvd (Cholesky of S, reduction to standard form,
+ * Hermitian eigensolver, back-transformation; FP64), loaded when this is
+ * first called; its workspace belongs to the handle.  It runs on `stream`
+ * and returns when it has finished there.  The muffin-tin S alone is
+ * positive definite only where 2 N_A N_L >= N_G (a physical problem adds the
+ * interstitial part, which is not built here).
+ * Errors: FLAPW_ERR_FACTOR if S is not positive definite (the message names
+ * the failing leading minor) or the eigensolver does not converge;
+ * FLAPW_ERR_UNSUPPORTED if cuSOLVER cannot be loaded; FLAPW_ERR_ARG for n < 1,
+ * ldh or lds < n, or H, S outside device memory; FLAPW_ERR_OOM if the
+ * workspace does not fit. */
+int flapw_eigh(flapw_handle h, int n, void* H, int64_t ldh, void* S, int64_t lds, double* w,
+               int vectors, void* stream);
+
 /* The contraction step alone (as flapw_herk, emulated precision) for callers
  * that must not allocate device memory: code that runs under a fixed device
  * memory budget or inside a framework whose caching allocator owns the GPU,

@@ -114,6 +114,8 @@ def load():
                                    ctypes.c_int64, c_void_p]),
             "flapw_herk_noalloc": (c_int, [c_void_p, ctypes.c_int64, c_int, c_int, ip, c_void_p,
                                            ctypes.c_int64, c_int, c_int, c_void_p]),
+            "flapw_eigh": (c_int, [h, c_int, c_void_p, ctypes.c_int64, c_void_p, ctypes.c_int64, dp,
+                                   c_int, c_void_p]),
             "flapw_sync": (c_int, [h]),
             "flapw_get_stats": (c_int, [h, P(Stats)]),
             "flapw_get_factor": (c_int, [h, c_int, dp, ip, ip]),
@@ -244,6 +246,14 @@ class Handle:
         sig = None if sigma is None else _i32(sigma)
         self._call("flapw_herk", _addr(Z), int(ldz), int(K), int(N),
                    None if sig is None else _ip(sig), _addr(H), int(ldh), _stream(stream))
+
+    def eigh(self, n, H, ldh, S, lds, vectors=True, stream=None):
+        """flapw_eigh: H c = lambda S c in place on device matrices (H becomes
+        the eigenvectors, S its Cholesky factor); returns the eigenvalues."""
+        w = np.zeros(int(n), dtype=np.float64)
+        self._call("flapw_eigh", int(n), _addr(H), int(ldh), _addr(S), int(lds), _dp(w),
+                   1 if vectors else 0, _stream(stream))
+        return w
 
     def set_spherical_T(self, t_sph):
         """flapw_set_spherical_T: t_sph [n_slots][lmax+1][4] = t^AA, t^BB,

@@ -14,6 +14,9 @@
 #include <string>
 #include <vector>
 
+#include <cusolverDn.h>
+#include <dlfcn.h>
+
 #include "flapw_internal.h"
 #include "tiles.cuh"
 
@@ -220,7 +223,55 @@ struct flapw_ctx {
   cudaGraphExec_t gexec = nullptr;
   std::vector<uintptr_t> gkey;
 
-  ~flapw_ctx() {
+  // generalised eigensolve (flapw_eigh): the solver's handle and workspaces
+  void* solver = nullptr;
+  DevBuf d_eig_work, d_eig_w;
+
+  ~flapw_ctx();
+};
+
+namespace {
+
+// cuSOLVER, opened on the first flapw_eigh: the library loads and runs the
+// H/S build without it.
+struct Solver {
+  bool ok = false;
+  std::string why;
+  decltype(&cusolverDnCreate) create = nullptr;
+  decltype(&cusolverDnDestroy) destroy = nullptr;
+  decltype(&cusolverDnSetStream) set_stream = nullptr;
+  decltype(&cusolverDnZhegvd_bufferSize) zhegvd_buffer = nullptr;
+  decltype(&cusolverDnZhegvd) zhegvd = nullptr;
+};
+
+Solver& solver_lib() {
+  static Solver s;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* lib = nullptr;
+    for (const char* name : {"libcusolver.so.12", "libcusolver.so", "/usr/local/cuda/lib64/libcusolver.so.12"})
+      if ((lib = dlopen(name, RTLD_NOW | RTLD_LOCAL))) break;
+    if (!lib) {
+      const char* e = dlerror();
+      s.why = std::string("cuSOLVER could not be loaded: ") + (e ? e : "not found");
+      return;
+    }
+    s.create = reinterpret_cast<decltype(s.create)>(dlsym(lib, "cusolverDnCreate"));
+    s.destroy = reinterpret_cast<decltype(s.destroy)>(dlsym(lib, "cusolverDnDestroy"));
+    s.set_stream = reinterpret_cast<decltype(s.set_stream)>(dlsym(lib, "cusolverDnSetStream"));
+    s.zhegvd_buffer = reinterpret_cast<decltype(s.zhegvd_buffer)>(dlsym(lib, "cusolverDnZhegvd_bufferSize"));
+    s.zhegvd = reinterpret_cast<decltype(s.zhegvd)>(dlsym(lib, "cusolverDnZhegvd"));
+    s.ok = s.create && s.destroy && s.set_stream && s.zhegvd_buffer && s.zhegvd;
+    if (!s.ok) s.why = "cuSOLVER lacks the zhegvd entry points";
+  });
+  return s;
+}
+
+}  // namespace
+
+flapw_ctx::~flapw_ctx() {
+  if (solver) solver_lib().destroy(static_cast<cusolverDnHandle_t>(solver));
+  {
     if (gexec) cudaGraphExecDestroy(gexec);
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
@@ -232,7 +283,7 @@ struct flapw_ctx {
       if (e) cudaEventDestroy(e);
     (void)cudaGetLastError();
   }
-};
+}
 
 namespace {
 
@@ -1917,6 +1968,55 @@ int flapw_get_factor(flapw_handle h, int slot, double* CH, int* n_pos, int* n_ne
       CH[o + 1] = M[(size_t)r * n + i].y;
     }
   }
+  return FLAPW_OK;
+}
+
+int flapw_eigh(flapw_handle h, int n, void* H, int64_t ldh, void* S, int64_t lds, double* w, int vectors,
+               void* stream) {
+  (void)cudaGetLastError();
+  if (!h || !H || !S || !w) return fail(h, FLAPW_ERR_ARG, "NULL argument");
+  if (n < 1 || ldh < n || lds < n) return fail(h, FLAPW_ERR_ARG, "need n >= 1, ldh >= n, lds >= n");
+  if (!is_device_ptr(H) || !is_device_ptr(S)) return fail(h, FLAPW_ERR_ARG, "H and S must be device memory");
+  if (ldh > INT32_MAX || lds > INT32_MAX) return fail(h, FLAPW_ERR_UNSUPPORTED, "ldh and lds must fit in int");
+  BudgetScope budget_scope(h);
+  Solver& sv = solver_lib();
+  if (!sv.ok) return fail(h, FLAPW_ERR_UNSUPPORTED, sv.why.c_str());
+  if (!h->solver) {
+    cusolverDnHandle_t sh = nullptr;
+    if (sv.create(&sh) != CUSOLVER_STATUS_SUCCESS) return fail(h, FLAPW_ERR_CUDA, "cusolverDnCreate failed");
+    h->solver = sh;
+  }
+  cusolverDnHandle_t sh = static_cast<cusolverDnHandle_t>(h->solver);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (sv.set_stream(sh, st) != CUSOLVER_STATUS_SUCCESS) return fail(h, FLAPW_ERR_CUDA, "cusolverDnSetStream failed");
+  const cusolverEigMode_t jobz = vectors ? CUSOLVER_EIG_MODE_VECTOR : CUSOLVER_EIG_MODE_NOVECTOR;
+  cuDoubleComplex* A = static_cast<cuDoubleComplex*>(H);
+  cuDoubleComplex* B = static_cast<cuDoubleComplex*>(S);
+  CK(h, h->d_eig_w.ensure((size_t)n * 8 + 16), "eigensolver workspace");
+  double* dw = h->d_eig_w.as<double>();
+  int* dinfo = reinterpret_cast<int*>(dw + n);
+  int lwork = 0;
+  if (sv.zhegvd_buffer(sh, CUSOLVER_EIG_TYPE_1, jobz, CUBLAS_FILL_MODE_LOWER, n, A, (int)ldh, B, (int)lds, dw,
+                       &lwork) != CUSOLVER_STATUS_SUCCESS)
+    return fail(h, FLAPW_ERR_CUDA, "cusolverDnZhegvd_bufferSize failed");
+  CK(h, h->d_eig_work.ensure((size_t)std::max(lwork, 1) * sizeof(cuDoubleComplex)), "eigensolver workspace");
+  if (sv.zhegvd(sh, CUSOLVER_EIG_TYPE_1, jobz, CUBLAS_FILL_MODE_LOWER, n, A, (int)ldh, B, (int)lds, dw,
+                h->d_eig_work.as<cuDoubleComplex>(), lwork, dinfo) != CUSOLVER_STATUS_SUCCESS)
+    return fail(h, FLAPW_ERR_CUDA, "cusolverDnZhegvd failed");
+  int info = 0;
+  CK(h, cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+  CK(h, cudaMemcpyAsync(w, dw, (size_t)n * 8, is_device_ptr(w) ? cudaMemcpyDeviceToDevice : cudaMemcpyDefault, st),
+     "cudaMemcpyAsync");
+  CK(h, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  if (info > n) {
+    char msg[160];
+    std::snprintf(msg, sizeof(msg),
+                  "S is not positive definite (its leading minor of order %d): the muffin-tin S alone is "
+                  "singular when 2 N_A N_L < N_G", info - n);
+    return fail(h, FLAPW_ERR_FACTOR, msg);
+  }
+  if (info > 0) return fail(h, FLAPW_ERR_FACTOR, "the Hermitian eigensolver did not converge");
+  if (info < 0) return fail(h, FLAPW_ERR_ARG, "the eigensolver rejected an argument");
   return FLAPW_OK;
 }
 

@@ -64,6 +64,15 @@ def test_enumerate_g_errors():
     assert b"NULL" in lib.flapw_last_error(None)
 
 
+def test_eigh_checks_its_arguments_first():
+    # no handle, no matrices: refused on the host before any CUDA call
+    lib = fl.load()
+    w = np.zeros(4)
+    dp = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.flapw_eigh(None, 4, None, 4, None, 4, dp, 1, None) == -1
+    assert b"NULL" in lib.flapw_last_error(None)
+
+
 def test_enumerate_g_writes_at_most_max_g():
     """The count is always the full one; only the first max_g triples are written."""
     lib = fl.load()
