@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # options.h_method values of include/flapw.h
-H_METHODS = {"factored": 0, "alg3": 1, "spherical": 2}
+H_METHODS = {"factored": 0, "alg3": 1, "spherical": 2, "alg1": 3}
 
 METRIC = "H+S build TFLOP/s & ms/k-point, emulated vs FP64 path, at ≤1e-12 rel err"
 
@@ -429,7 +429,8 @@ def run_ours(args):
                                                       if args.s_method == "legendre" else
                                                       "S launch; H by the addition theorem"
                                                       if args.h_method == "spherical" else "S and H launches")
-                               + ("; H as Alg. 3's L^H R" if args.h_method == "alg3" else "") + ")",
+                               + ("; H as Alg. 3's L^H R" if args.h_method == "alg3" else
+                                  "; H as Alg. 1's L^H R" if args.h_method == "alg1" else "") + ")",
                      "kernel_ms": round(k_ms, 4),
                      "peak_source": f"{src} bf16 {peak_kind} x 1.0 (fp16 = bf16 nominal rate)"},
         # the A/B assembly (HBM store-bound): 32 bytes stored per (atom, L, G)
@@ -539,9 +540,11 @@ def launches_per_step(args):
         (4 kernels), their tensor-core product, and one kernel that applies
         the atom phases and slices the rows;
       A/B operands: tfactor, layout, opform_H and the slicer;
-      Alg. 3: no tfactor and layout; factored, the same four factor kernels,
-        the product, the phase kernel, the copy of A and B and the slicer;
-        from A/B, the FP64 product and copy kernels and the slicer."""
+      Alg. 3 and Alg. 1: no tfactor and layout but the kernel that forms the
+        operand matrix (with Alg. 1 the Cholesky factors of T^AA); factored,
+        the same four factor kernels, the product, the phase kernel, the copy
+        of A and B and the slicer; from A/B, the FP64 product and copy kernels
+        and the slicer."""
     n = 2
     n += 2 if args.s_method == "legendre" else 3
     if args.h_method == "spherical":
@@ -549,8 +552,8 @@ def launches_per_step(args):
         # addition-theorem kernel; no factorisation, H operands or H contraction
         return n + 3
     n += 1
-    if args.h_method == "alg3":
-        n += 8 if args.operands == "factored" else 3
+    if args.h_method in ("alg3", "alg1"):
+        n += 9 if args.operands == "factored" else 4
     else:
         n += 8 if args.operands == "factored" else 4
     return n

@@ -95,6 +95,15 @@ typedef struct flapw_ctx* flapw_handle;
  * spherical part) runs no factorisation, operands or contraction for H.
  * Needs FLAPW_OPERANDS_FACTORED; the addition-theorem part runs in FP64. */
 #define FLAPW_H_SPHERICAL 2
+/* FLAPW_H_ALG1: the paper's Alg. 1 (Sec. 3) on the engine of FLAPW_H_ALG3.  Per
+ * slot it tries the Cholesky factorisation T^AA = C C^H (FP64 on the device);
+ * where it succeeds the H_AA part is the Hermitian update (C^H A)^H (C^H A)
+ * (the paper's ztrmm + zherk), where it fails A^H (T^AA A) (zhemm + zgemm).
+ * In the stacked contraction L^H R of FLAPW_H_ALG3 (K = 3 N_A N_L) this only
+ * changes the third block of L_a and R_a: both C^H A_a, or A_a and T^AA A_a.
+ * stats.n_chol counts the slots that factorised.  The result is the same H;
+ * the executed contraction work is that of FLAPW_H_ALG3. */
+#define FLAPW_H_ALG1 3
 
 typedef struct flapw_options {
   int precision; /* FLAPW_PREC_EMU (default) or FLAPW_PREC_FP64 */
@@ -179,7 +188,8 @@ typedef struct flapw_stats {
   int pipeline;        /* load pipeline in use (1: 3 stages of two chunks, 2: 5 of one) */
   int copy_ops;        /* device-to-host copies the last build_HS or herk enqueued */
   int64_t bytes_d2h;   /* bytes those copies move (host-memory outputs only) */
-  int reserved[4];
+  int n_chol;          /* FLAPW_H_ALG1: slots whose T^AA Cholesky factorisation succeeded */
+  int reserved[3];
   double ms_s;         /* the S half of ms_contract: its contraction, or with
                           FLAPW_S_LEGENDRE the addition-theorem evaluation */
   double ms_ab_assemble; /* the A/B assembly kernel of the last build_AB (part of ms_ab) */

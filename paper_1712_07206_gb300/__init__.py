@@ -21,7 +21,7 @@ __all__ = ["FlapwError", "Options", "Stats", "Handle", "load", "library_path", "
            "declared_symbols",
            "PREC_FP64", "PREC_EMU", "LAYOUT_LOWER_FULL", "LAYOUT_LOWER_PACKED",
            "OPERANDS_FROM_AB", "OPERANDS_FACTORED", "S_CONTRACTION", "S_LEGENDRE",
-           "H_FACTORED", "H_ALG3", "H_SPHERICAL"]
+           "H_FACTORED", "H_ALG3", "H_SPHERICAL", "H_ALG1"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _HEADER = os.path.join(os.path.dirname(_HERE), "include", "flapw.h")
@@ -30,7 +30,7 @@ PREC_FP64, PREC_EMU = 0, 1
 LAYOUT_LOWER_FULL, LAYOUT_LOWER_PACKED = 0, 1
 OPERANDS_FROM_AB, OPERANDS_FACTORED = 0, 1
 S_CONTRACTION, S_LEGENDRE = 0, 1
-H_FACTORED, H_ALG3, H_SPHERICAL = 0, 1, 2
+H_FACTORED, H_ALG3, H_SPHERICAL, H_ALG1 = 0, 1, 2, 3
 ERR = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_FACTOR",
        -5: "ERR_TIMEOUT", -6: "ERR_STATE", -7: "ERR_UNSUPPORTED"}
 
@@ -61,7 +61,8 @@ class Stats(ctypes.Structure):
                 ("tile_order", ctypes.c_int), ("graph_replays", ctypes.c_int),
                 ("tile_cover", ctypes.c_int), ("pipeline", ctypes.c_int),
                 ("copy_ops", ctypes.c_int), ("bytes_d2h", ctypes.c_int64),
-                ("reserved", ctypes.c_int * 4), ("ms_s", ctypes.c_double),
+                ("n_chol", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3), ("ms_s", ctypes.c_double),
                 ("ms_ab_assemble", ctypes.c_double)]
 
     def as_dict(self):

@@ -6,6 +6,12 @@
 // of L_a = [X_a; B_a; A_a] and R_a = [B_a; X_a; Y_a] (3 N_L rows per atom):
 // row r of M [A_a; B_a] is column N_L + r of R_a and, for r < N_L, column r
 // of L_a.
+//
+// The paper's Alg. 1 differs only in the H_AA part: where the Cholesky
+// factorisation T^AA = C C^H succeeds it forms Z_a = C^H A_a and adds
+// Z_a^H Z_a (zherk), elsewhere A_a^H (T^AA A_a) (zgemm).  In the stacked form
+// the Y rows of M become C^H (upper triangular) for such a slot, and the third
+// block of L_a is then Y_a as well: L_a = [X_a; B_a; Y_a], R_a = [B_a; X_a; Y_a].
 #pragma once
 
 #include <cstdint>

@@ -217,6 +217,8 @@ struct flapw_ctx {
   std::vector<double> tsph;
   int tsph_slots = 0, tsph_lmax = -1;
   DevBuf d_tsph;
+  DevBuf d_hpd;                  // Alg. 1: [slot] the Cholesky factorisation of T^AA succeeded
+  bool last_alg1 = false;        // the last build_HS formed H by the paper's Alg. 1
   bool last_h_zero = false;      // the last build_HS's T was its spherical part (no H contraction)
 
   // CUDA graph replay of build_HS
@@ -329,7 +331,8 @@ int check_options(flapw_ctx* h, const flapw_options& o) {
     return fail(h, FLAPW_ERR_ARG, "options.s_method is not a FLAPW_S_* value");
   if (o.s_method == FLAPW_S_LEGENDRE && o.operands != FLAPW_OPERANDS_FACTORED)
     return fail(h, FLAPW_ERR_ARG, "options.s_method FLAPW_S_LEGENDRE needs FLAPW_OPERANDS_FACTORED");
-  if (o.h_method != FLAPW_H_FACTORED && o.h_method != FLAPW_H_ALG3 && o.h_method != FLAPW_H_SPHERICAL)
+  if (o.h_method != FLAPW_H_FACTORED && o.h_method != FLAPW_H_ALG3 && o.h_method != FLAPW_H_SPHERICAL &&
+      o.h_method != FLAPW_H_ALG1)
     return fail(h, FLAPW_ERR_ARG, "options.h_method is not a FLAPW_H_* value");
   if (o.h_method == FLAPW_H_SPHERICAL && o.operands != FLAPW_OPERANDS_FACTORED)
     return fail(h, FLAPW_ERR_ARG, "options.h_method FLAPW_H_SPHERICAL needs FLAPW_OPERANDS_FACTORED");
@@ -1133,7 +1136,10 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   const int nk = h->n_k;
   const int64_t K = (int64_t)h->n_atoms * n;
   // H by the paper's Alg. 3: L^H R over 3 N_A N_L rows, no factorisation
-  const bool alg3 = h->opt.h_method == FLAPW_H_ALG3;
+  // Alg. 1 is Alg. 3's stacked contraction with C^H in place of T^AA where the
+  // Cholesky factorisation of T^AA succeeds (alg3.cuh)
+  const bool alg1 = h->opt.h_method == FLAPW_H_ALG1;
+  const bool alg3 = h->opt.h_method == FLAPW_H_ALG3 || alg1;
   // H from the spherical part of T by the addition theorem plus the contraction
   // of the rest (which is skipped when the rest is zero)
   const bool h_sph = h->opt.h_method == FLAPW_H_SPHERICAL;
@@ -1223,6 +1229,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   CK(h, h->d_T.ensure(t_bytes), "workspace");
   CK(h, h->d_work.ensure(t_bytes), "workspace");
   CK(h, h->d_CH.ensure(t_bytes), "workspace");
+  CK(h, h->d_hpd.ensure(sizeof(int) * (size_t)std::max(n_slots, 1)), "workspace");
   // S by the addition theorem: Khat of every plane wave and the atoms grouped
   // by type, both fixed by the crystal (computed once)
   const bool s_legendre = h->opt.s_method == FLAPW_S_LEGENDRE;
@@ -1408,6 +1415,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
   std::memcpy(pin_probs.p, probs.data(), sizeof(Prob) * probs.size());
   h->last_n_slots = n_slots;
   h->last_alg3 = alg3;
+  h->last_alg1 = alg1;
 
   // ---- the enqueued sequence (graph-capturable) ----
   // S needs no factorisation: its operands, slices and contraction run on the
@@ -1472,6 +1480,8 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     oa.s_row0 = s_row0;
     oa.r_row0 = h->g_total;
     oa.T = h->d_T.as<double2>();
+    oa.M = h->d_CH.as<double2>();
+    oa.hpd = alg1 ? h->d_hpd.as<int>() : nullptr;
     oa.A = dA;
     oa.B = dB;
     oa.Yc = h->d_Yc.as<double2>();
@@ -1500,9 +1510,15 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
                           h->d_probs.as<Prob>(), (int)K, h->aux_stream),
          "layout launch");
     }
+    if (alg3) {
+      // the operand matrix of Alg. 3, or of Alg. 1 with the Cholesky factors of T^AA
+      CK(h, launch_alg_m(h->d_T.as<double2>(), n, h->n_L, n_slots, alg1, h->d_CH.as<double2>(),
+                         h->d_work.as<double2>(), h->d_hpd.as<int>(), h->aux_stream),
+         "operand matrix launch");
+    }
     CK(h, cudaEventRecord(h->ev[1], h->aux_stream), "cudaEventRecord");
     if (tc_ops && alg3) {
-      CK(h, launch_opgemm_build_alg3(h->d_T.as<double2>(), n_slots, n, h->n_L, op_kp, h->d_opA.as<double2>(),
+      CK(h, launch_opgemm_build_alg3(h->d_CH.as<double2>(), n_slots, n, h->n_L, op_kp, h->d_opA.as<double2>(),
                                      h->aux_stream),
          "operand factor launch");
     } else if (tc_ops && !h_zero) {
@@ -1634,6 +1650,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
       ga.k_alloc = h->k_alloc;
       ga.h_row0 = 0;
       ga.alg3_nl = alg3 ? h->n_L : 0;
+      ga.hpd = alg1 ? h->d_hpd.as<int>() : nullptr;
       ga.r_row0 = h->g_total;
       CK(h, launch_opgemm(h->opmap_a, h->opmap_b, ga, h->d_optiles.as<OpTile>(), (int)h->optiles.size(),
                           cnt + 2, h->num_sms, wait_ns(h), st),
@@ -1909,6 +1926,11 @@ int flapw_get_stats(flapw_handle h, flapw_stats* st) {
         kpk[1] = (int)s.k_total;
         kpk[2] = 0;
         c[0] = 0;
+      }
+      if (h->last_alg1 && h->last_n_slots > 0) {
+        std::vector<int> hpd(h->last_n_slots, 0);
+        if (cudaMemcpy(hpd.data(), h->d_hpd.p, sizeof(int) * hpd.size(), cudaMemcpyDeviceToHost) == cudaSuccess)
+          for (int v : hpd) s.n_chol += v;
       }
       if (h->last_h_zero) {  // T was its spherical part: no H contraction
         kpk[1] = kpk[2] = 0;

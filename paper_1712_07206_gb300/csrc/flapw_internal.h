@@ -149,6 +149,8 @@ struct OpformArgs {
   int64_t s_row0;       // operand row of the first S plane wave
   int64_t r_row0;       // the paper's Alg. 3: operand row of the first right-hand H row
   const double2* T;     // the paper's Alg. 3: [slot][n][n] row-major T blocks (lower read)
+  const double2* M;     // Alg. 3 / Alg. 1: [slot][n][n] row-major operand matrices (alg_m)
+  const int* hpd;       // Alg. 1: [slot] Cholesky of T^AA succeeded; null for Alg. 3
   // from A/B
   const double2* A;
   const double2* B;
@@ -197,6 +199,8 @@ struct OpGemmArgs {
   int64_t h_row0;
   int alg3_nl;         // 0: factored C^H rows; N_L: the paper's Alg. 3 rows (alg3.cuh)
   int64_t r_row0;      // Alg. 3: operand row of the first R row
+  const int* hpd;      // Alg. 1: [slot] 1 where T^AA = C C^H (the Y rows are C^H A and go to
+                       // both L and R); null for Alg. 3
 };
 cudaError_t opgemm_init();
 size_t opgemm_smem_bytes();
@@ -207,7 +211,13 @@ cudaError_t launch_opgemm_build(const double2* CH, const int* perm, int n_slots,
                                 int lmax, int n_types, int64_t G, double2* A, double2* B,
                                 cudaStream_t st, bool build_a);
 // The paper's Alg. 3: A[slot n + r][c] = conj(M_s(r, c)) (alg3.cuh) from the T blocks.
-cudaError_t launch_opgemm_build_alg3(const double2* T, int n_slots, int n, int n_L, int kp,
+// The operand matrix of the paper's Alg. 3 or Alg. 1 per slot (alg3.cuh),
+// [slot][n][n] row-major, from T's lower triangle; with alg1 the Y rows are
+// C^H where T^AA = C C^H (Cholesky) succeeds (hpd[slot] = 1), else T^AA.
+// work: [slot][n][n] scratch.  One CTA per slot.
+cudaError_t launch_alg_m(const double2* T, int n, int n_L, int n_slots, bool alg1, double2* M, double2* work,
+                         int* hpd, cudaStream_t st);
+cudaError_t launch_opgemm_build_alg3(const double2* M, int n_slots, int n, int n_L, int kp,
                                      double2* A, cudaStream_t st);
 // P for every tile (opgemm.cu), then every atom's operand rows from P (with
 // alg3_nl set: the L and R columns of Alg. 3).

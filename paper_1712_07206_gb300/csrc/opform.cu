@@ -188,7 +188,8 @@ __global__ void __launch_bounds__(256) opform_s_kernel(OpformArgs p, int64_t G) 
 }
 
 // X and Y rows of Alg. 3: row r of M [A_a; B_a] goes to column N_L + r of R_a
-// and, for r < N_L (an X row), to column r of L_a.
+// and, for r < N_L (an X row), to column r of L_a; with Alg. 1's C^H rows a
+// Y row goes to column N_L + r of L_a too.
 // grid: (g-tiles, ceil(n/32), atoms or combos); 256 threads.
 template <bool kFactored>
 __global__ void __launch_bounds__(256) opform_alg3_kernel(OpformArgs p, int64_t G) {
@@ -208,7 +209,8 @@ __global__ void __launch_bounds__(256) opform_alg3_kernel(OpformArgs p, int64_t 
     type = p.atom_type[a_single];
   }
   const int n = p.n, nL = p.n_L;
-  const double2* T = p.T + (int64_t)slot * n * n;
+  const double2* Ms = p.M + (int64_t)slot * n * n;
+  const bool y_in_l = p.hpd && p.hpd[slot];  // Alg. 1 with C^H: Y rows in L as well
   const int tid = threadIdx.x, rl = tid & 31, gq = tid >> 5;
   double2 acc[8];
 #pragma unroll
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(256) opform_alg3_kernel(OpformArgs p, int64_t 
     for (int idx = tid; idx < kCT * kRT; idx += 256) {
       const int rr = idx / kCT, cc = idx % kCT;
       const int r = r0 + rr, c = c0 + cc;
-      ms[cc][rr] = (r < n && c < n) ? alg3::m_elem(T, n, nL, r, c) : make_double2(0.0, 0.0);
+      ms[cc][rr] = (r < n && c < n) ? Ms[(int64_t)r * n + c] : make_double2(0.0, 0.0);
     }
     for (int idx = tid; idx < kCT * kGT; idx += 256) {
       const int cc = idx / kGT, gg = idx % kGT;
@@ -258,9 +260,81 @@ __global__ void __launch_bounds__(256) opform_alg3_kernel(OpformArgs p, int64_t 
         }
         p.Z[(rrow0 + g) * p.k_alloc + base + nL + r] = z;
         if (r < nL) p.Z[(lrow0 + g) * p.k_alloc + base + r] = z;
+        else if (y_in_l) p.Z[(lrow0 + g) * p.k_alloc + base + nL + r] = z;
       }
     }
   }
+}
+
+// The Alg. 3 / Alg. 1 operand matrix M of one slot (alg3.cuh) into Mo
+// ([n][n] row-major).  With alg1, T^AA = C C^H by the left-looking Cholesky
+// factorisation (column j: the pivot T^AA_jj - sum_k |C_jk|^2, then
+// C_ij = (T^AA_ij - sum_k C_ik conj(C_jk)) / C_jj below it), in FP64, into the
+// scratch W; a pivot that is not positive (or not finite) fails the slot as
+// the paper's zpotrf would, and its Y rows stay T^AA.  One CTA per slot.
+__global__ void __launch_bounds__(256) alg_m_kernel(const double2* __restrict__ T, int n, int nL, int alg1,
+                                                    double2* __restrict__ M, double2* __restrict__ W,
+                                                    int* __restrict__ hpd) {
+  __shared__ double red[256];
+  __shared__ int failed;
+  const int slot = blockIdx.x, tid = threadIdx.x;
+  const double2* Ts = T + (int64_t)slot * n * n;
+  double2* Ms = M + (int64_t)slot * n * n;
+  double2* Ws = W + (int64_t)slot * n * n;  // C (lower), row-major nL x nL
+  for (int i = tid; i < nL * n; i += 256) Ms[i] = alg3::m_elem(Ts, n, nL, i / n, i % n);  // X rows
+  if (tid == 0) failed = alg1 ? 0 : 1;
+  __syncthreads();
+  for (int j = 0; j < nL && !failed; ++j) {
+    double part = 0.0;
+    for (int k = tid; k < j; k += 256) {
+      const double2 c = Ws[(int64_t)j * nL + k];
+      part += c.x * c.x + c.y * c.y;
+    }
+    red[tid] = part;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (tid < s) red[tid] += red[tid + s];
+      __syncthreads();
+    }
+    const double d = alg3::t_elem(Ts, n, j, j).x - red[0];
+    __syncthreads();
+    if (!(d > 0.0) || !isfinite(d)) {
+      if (tid == 0) failed = 1;
+      __syncthreads();
+      break;
+    }
+    const double cjj = sqrt(d);
+    if (tid == 0) Ws[(int64_t)j * nL + j] = make_double2(cjj, 0.0);
+    for (int i = j + 1 + tid; i < nL; i += 256) {
+      double2 s = alg3::t_elem(Ts, n, i, j);
+      for (int k = 0; k < j; ++k) {
+        const double2 a = Ws[(int64_t)i * nL + k], b = Ws[(int64_t)j * nL + k];
+        s.x -= a.x * b.x + a.y * b.y;  // a conj(b)
+        s.y -= a.y * b.x - a.x * b.y;
+      }
+      Ws[(int64_t)i * nL + j] = make_double2(s.x / cjj, s.y / cjj);
+    }
+    __syncthreads();
+  }
+  // Y rows: C^H (row i, column c >= i: conj(C_ci)) where the factorisation
+  // succeeded, else T^AA; zero on the B half
+  const bool chol = !failed;
+  for (int e = tid; e < nL * n; e += 256) {
+    const int i = e / n, c = e % n;
+    double2 v = make_double2(0.0, 0.0);
+    if (c < nL) {
+      if (chol) {
+        if (c >= i) {
+          const double2 w = Ws[(int64_t)c * nL + i];
+          v = make_double2(w.x, -w.y);
+        }
+      } else {
+        v = alg3::m_elem(Ts, n, nL, nL + i, c);
+      }
+    }
+    Ms[(int64_t)(nL + i) * n + c] = v;
+  }
+  if (tid == 0) hpd[slot] = chol ? 1 : 0;
 }
 
 // A_a and B_a into the Alg. 3 operands: L_a = [X; B; A] takes W row c at
@@ -294,13 +368,14 @@ __global__ void __launch_bounds__(256) opform_alg3_copy_kernel(OpformArgs p, int
   __syncthreads();
   const int64_t lrow0 = p.h_row0 + p.goff[k], rrow0 = p.r_row0 + p.goff[k];
   const int64_t base = (int64_t)a * 3 * nL;
+  const bool y_in_l = p.hpd && p.hpd[p.atom_slot[a]];  // Alg. 1 with C^H: L's third block is Y
   for (int idx = threadIdx.x; idx < kRT * kGT; idx += 256) {
     const int gg = idx / kRT, cc = idx % kRT;
     const int c = c0 + cc, g = g0 + gg;
     if (c < n && g < ng) {
       const double2 v = tile[cc][gg];
       if (c < nL) {
-        p.Z[(lrow0 + g) * p.k_alloc + base + 2 * nL + c] = v;
+        if (!y_in_l) p.Z[(lrow0 + g) * p.k_alloc + base + 2 * nL + c] = v;
       } else {
         p.Z[(lrow0 + g) * p.k_alloc + base + c] = v;
         p.Z[(rrow0 + g) * p.k_alloc + base + (c - nL)] = v;
@@ -359,6 +434,13 @@ cudaError_t launch_opform_alg3(const OpformArgs& a, bool factored, bool product,
   dim3 grid_copy(a.n_gtiles, (a.n + kRT - 1) / kRT, a.n_atoms);
   if (factored) opform_alg3_copy_kernel<true><<<grid_copy, 256, 0, st>>>(a, G);
   else opform_alg3_copy_kernel<false><<<grid_copy, 256, 0, st>>>(a, G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_alg_m(const double2* T, int n, int n_L, int n_slots, bool alg1, double2* M, double2* work,
+                         int* hpd, cudaStream_t st) {
+  if (n_slots == 0) return cudaSuccess;
+  alg_m_kernel<<<n_slots, 256, 0, st>>>(T, n, n_L, alg1 ? 1 : 0, M, work, hpd);
   return cudaGetLastError();
 }
 

@@ -323,18 +323,18 @@ __global__ void __launch_bounds__(128) opgemm_build_a_kernel(const double2* __re
   }
 }
 
-// A(slot n + r, c) = conj(M_s(r, c)) for Alg. 3; columns n..kp-1 zero.
-// grid: n_slots * n rows.
-__global__ void __launch_bounds__(128) opgemm_build_a_alg3_kernel(const double2* __restrict__ T,
-                                                                  int n, int nL, int kp,
+// A(slot n + r, c) = conj(M_s(r, c)) for Alg. 3 or Alg. 1 (M from
+// alg_m_kernel); columns n..kp-1 zero.  grid: n_slots * n rows.
+__global__ void __launch_bounds__(128) opgemm_build_a_alg3_kernel(const double2* __restrict__ M,
+                                                                  int n, int kp,
                                                                   double2* __restrict__ A) {
   const int row = blockIdx.x, slot = row / n, r = row % n;
-  const double2* Ts = T + (int64_t)slot * n * n;
+  const double2* Ms = M + ((int64_t)slot * n + r) * n;
   double2* dst = A + (int64_t)row * kp;
   for (int c = threadIdx.x; c < kp; c += blockDim.x) {
     double2 v = make_double2(0.0, 0.0);
     if (c < n) {
-      const double2 m = alg3::m_elem(Ts, n, nL, r, c);
+      const double2 m = Ms[c];
       v = make_double2(m.x, -m.y);
     }
     dst[c] = v;
@@ -396,6 +396,7 @@ __global__ void __launch_bounds__(128) opgemm_phase_kernel(const OpGemmArgs g) {
   double2* zrow_r = g.Z + (g.r_row0 + gi) * g.k_alloc;
   const longlong2* prow = g.P + ((int64_t)combo * g.G + gi) * g.n;
   const int nL = g.alg3_nl;
+  const bool y_in_l = g.hpd && g.hpd[slot];
   for (int r = threadIdx.x; r < g.n; r += blockDim.x) {
     const int rr = nL ? r : g.outrow[slot * g.n + r];  // sigma-grouped position
     if (rr < 0) continue;                               // zero pivot: the row carries nothing
@@ -412,6 +413,7 @@ __global__ void __launch_bounds__(128) opgemm_phase_kernel(const OpGemmArgs g) {
         const int64_t base = (int64_t)a * 3 * nL;
         zrow_r[base + nL + r] = z;
         if (r < nL) zrow[base + r] = z;
+        else if (y_in_l) zrow[base + nL + r] = z;  // Alg. 1 with C^H: Y in L too
       } else {
         zrow[(rr < np) ? g.pos_off[a] + rr : g.kpk[0] + g.neg_off[a] + (rr - np)] = z;
       }
@@ -708,9 +710,10 @@ cudaError_t launch_opgemm_build(const double2* CH, const int* perm, int n_slots,
   return cudaGetLastError();
 }
 
-cudaError_t launch_opgemm_build_alg3(const double2* T, int n_slots, int n, int n_L, int kp,
+cudaError_t launch_opgemm_build_alg3(const double2* M, int n_slots, int n, int n_L, int kp,
                                      double2* A, cudaStream_t st) {
-  if (n_slots * n > 0) opgemm_build_a_alg3_kernel<<<n_slots * n, 128, 0, st>>>(T, n, n_L, kp, A);
+  (void)n_L;
+  if (n_slots * n > 0) opgemm_build_a_alg3_kernel<<<n_slots * n, 128, 0, st>>>(M, n, kp, A);
   return cudaGetLastError();
 }
 

@@ -158,7 +158,7 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
     with pytest.raises(fl.FlapwError):
         fl.hs_create(p.lattice, p.pos_frac, p.atom_type, p.mt_radius, 4, p.k_frac, p.kmax, bad)
     # option values outside their ranges are rejected before any device work
-    for kw in (dict(pipeline=3), dict(h_method=3), dict(h_method=2), dict(s_method=2), dict(tile_order=7), dict(tile_cover=3),
+    for kw in (dict(pipeline=3), dict(h_method=4), dict(h_method=2), dict(s_method=2), dict(tile_order=7), dict(tile_cover=3),
                dict(wait_us=-1), dict(mem_cap_mb=-1),
                dict(operands=fl.OPERANDS_FROM_AB, s_method=fl.S_LEGENDRE)):
         with pytest.raises(fl.FlapwError) as e:

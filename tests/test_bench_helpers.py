@@ -31,8 +31,9 @@ class Args:
     ("factored", "contraction", "factored", 14),
     ("factored", "legendre", "factored", 13),
     ("from_ab", "contraction", "factored", 10),
-    ("factored", "contraction", "alg3", 14),
-    ("from_ab", "contraction", "alg3", 9),
+    ("factored", "contraction", "alg3", 15),
+    ("from_ab", "contraction", "alg3", 10),
+    ("factored", "contraction", "alg1", 15),
     ("factored", "contraction", "spherical", 8),
 ])
 def test_launches_per_step(bench, operands, s_method, h_method, n):
@@ -132,7 +133,8 @@ def test_cpu_baseline_calibrates_and_measures_parity(bench, layout_name):
 def test_spherical_part_is_a_projection(bench):
     import numpy as np
     import paper_1712_07206_gb300 as fl
-    assert bench.H_METHODS == {"factored": fl.H_FACTORED, "alg3": fl.H_ALG3, "spherical": fl.H_SPHERICAL}
+    assert bench.H_METHODS == {"factored": fl.H_FACTORED, "alg3": fl.H_ALG3, "spherical": fl.H_SPHERICAL,
+                               "alg1": fl.H_ALG1}
     from paper_1712_07206_gb300 import inputs
     p = inputs.small(5, n_atoms=2, n_types=2, lmax=3)
     Ts, t = bench.spherical_part(p.T, p.lmax)
