@@ -142,6 +142,29 @@ def _finish(name, rng, lattice, pos_frac, atom_type, radii, lmax, k_frac, n_targ
                    layout=layout, n_target=tuple(n_target))
 
 
+def with_kpoints(p: Problem, copies: int, seed: int = 3000) -> Problem:
+    """The workload over `copies` sets of its k-points, the job of `copies`
+    independent callers: the first set is p's own, the others seeded k-points
+    of the same crystal (uniform in the cube of reciprocal coordinates
+    [-1/2, 1/2)^3), each with the K_max of the k-point whose place it takes, so
+    that N_G stays close.  The name stays the workload's."""
+    if copies <= 1:
+        return p
+    rng = np.random.Generator(np.random.PCG64(seed))
+    extra = rng.uniform(-0.5, 0.5, size=((copies - 1) * p.n_k, 3))
+    return dataclasses.replace(p, k_frac=np.ascontiguousarray(np.vstack([p.k_frac, extra])),
+                               kmax=np.tile(np.asarray(p.kmax, dtype=np.float64), copies),
+                               n_target=tuple(p.n_target) * copies)
+
+
+def subset_kpoints(p: Problem, ks) -> Problem:
+    """The same crystal and data with only the k-points ks (in that order)."""
+    ks = list(ks)
+    return dataclasses.replace(p, k_frac=np.ascontiguousarray(p.k_frac[ks]),
+                               kmax=np.asarray(p.kmax, dtype=np.float64)[ks],
+                               n_target=tuple(p.n_target[k] for k in ks) if p.n_target else ())
+
+
 def config1(hpd=False) -> Problem:
     """2 atoms, one type, simple-cubic a=6 bohr, l_max=4, ~300 plane waves."""
     rng = np.random.Generator(np.random.PCG64(1001))

@@ -2,9 +2,10 @@
 gloo ranks; the library's split of a job over independent parts
 (flapw_partition, host only), which every rank must compute identically and
 which must give every k-point to exactly one part with a bounded load, or
-share all k-points by tiles; and the reference arm under torchrun with two
-ranks (rank 0 alone runs the oracle and prints one line, both exit 0).
-They cover the host paths of N > 1 ranks without any GPU."""
+share all k-points by tiles; the bench's weak-scaling job (N sets of the
+workload's k-points, whole k-points per rank); and the reference arm under
+torchrun with two ranks (rank 0 alone runs the oracle and prints one line,
+both exit 0).  They cover the host paths of N > 1 ranks without any GPU."""
 import json
 import os
 import socket
@@ -114,3 +115,58 @@ def test_reference_arm_under_torchrun_two_ranks():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["value"] > 0
+
+
+def _job_worker(rank, world, port, out):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1712_07206_gb300 import inputs
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    res = {}
+    for cfg in (2, 4):
+        mine, job, ng_job, owner = bench.job_split(inputs.CONFIGS[cfg](), world, rank)
+        got = [torch.zeros(len(owner), dtype=torch.int32) for _ in range(world)]
+        dist.all_gather(got, torch.from_numpy(owner.astype(np.int32)))
+        res[cfg] = {"owners": [g.tolist() for g in got], "ng": ng_job, "n_k": mine.n_k,
+                    "k_frac": mine.k_frac.tolist(), "job_k": job.k_frac.tolist(),
+                    "same_T": bool(np.array_equal(mine.T, job.T))}
+    out[rank] = res
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_bench_weak_scaling_job_gloo_two_ranks():
+    # the bench's job for N ranks: N sets of the workload's k-points, every
+    # k-point on exactly one rank, the same split on every rank, loads within
+    # the partition's bound, and each rank's problem holds exactly its k-points
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    from paper_1712_07206_gb300 import inputs
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_job_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    for cfg, n_k in ((2, 1), (4, 32)):
+        a, b = out[0][cfg], out[1][cfg]
+        assert a["owners"][0] == a["owners"][1] == b["owners"][0]
+        own = np.array(a["owners"][0])
+        assert len(own) == 2 * n_k and set(own.tolist()) == {0, 1}
+        assert a["job_k"] == b["job_k"] and a["ng"] == b["ng"]
+        w = np.asarray(a["ng"], float) ** 2
+        assert max(w[own == 0].sum(), w[own == 1].sum()) <= 1.1 * w.sum() / 2
+        for r, d in ((0, a), (1, b)):
+            ks = np.flatnonzero(own == r)
+            assert d["n_k"] == len(ks) and d["same_T"]
+            assert np.allclose(d["k_frac"], np.asarray(a["job_k"])[ks])
+        # the first set is the workload's own k-points
+        assert np.allclose(np.asarray(a["job_k"])[:n_k], inputs.CONFIGS[cfg]().k_frac)
