@@ -426,24 +426,38 @@ def test_host_buffers_through_the_abi():
     assert herm_relerr(lower_to_full(S, ng, 0), So) <= TOL_EMU
 
 
+def _nan_outputs(torch, h, p, layout, memory):
+    Hs, Ss = [], []
+    for k in range(p.n_k):
+        ng = h.num_g(k)
+        n = ng * (ng + 1) // 2 if layout == fl.LAYOUT_LOWER_PACKED else ng * ng
+        for lst in (Hs, Ss):
+            if memory == "pinned":
+                lst.append(torch.full((n,), float("nan"), dtype=torch.complex128).pin_memory())
+            else:
+                lst.append(np.full(n, np.nan, dtype=np.complex128))
+    return Hs, Ss
+
+
+def _host(x):
+    return x.numpy() if hasattr(x, "numpy") else x
+
+
+@pytest.mark.parametrize("memory", ["pinned", "pageable"])
 @pytest.mark.parametrize("layout", [fl.LAYOUT_LOWER_FULL, fl.LAYOUT_LOWER_PACKED])
 @pytest.mark.parametrize("precision,tol", [(fl.PREC_EMU, TOL_EMU), (fl.PREC_FP64, TOL_F64)])
-def test_host_outputs_every_lower_element_copied(layout, precision, tol):
-    # pinned host outputs filled with NaN: the block-wise copy of the lower
-    # triangle must reach every lower element of every k-point (ragged N_G,
-    # one N_G above 64 x 32 so that the column blocks are wider than 64), with
-    # H contracted in two launches split by column (both precisions)
+def test_host_outputs_every_lower_element_copied(layout, precision, tol, memory):
+    # host outputs (pinned or pageable) filled with NaN must receive every
+    # lower element of every k-point (ragged N_G, one N_G above 64 x 32 so that
+    # the column blocks are wider than 64), both precisions: staged on the
+    # device and copied back in column blocks, H contracted in two launches
+    # split by column
     torch = torch_cuda()
     p = inputs.small(88, n_atoms=3, n_types=2, lmax=3, n_target=(2100, 150, 65))
     h = fl.from_problem(p, fl.default_options(precision=precision, layout=layout,
                                               operands=fl.OPERANDS_FACTORED))
     _, A, B = run_ab(p, h)
-    Hs, Ss = [], []
-    for k in range(p.n_k):
-        ng = h.num_g(k)
-        n = ng * (ng + 1) // 2 if layout == fl.LAYOUT_LOWER_PACKED else ng * ng
-        Hs.append(torch.full((n,), float("nan"), dtype=torch.complex128).pin_memory())
-        Ss.append(torch.full((n,), float("nan"), dtype=torch.complex128).pin_memory())
+    Hs, Ss = _nan_outputs(torch, h, p, layout, memory)
     h.build_HS(p.T, p.atom_slot, p.U, A, B, Hs, Ss)
     h.sync()
     for k in range(p.n_k):
@@ -451,8 +465,9 @@ def test_host_outputs_every_lower_element_copied(layout, precision, tol):
         ng = Ho.shape[0]
         assert herm_relerr(lower_to_full(Hs[k], ng, layout), Ho) <= tol, k
         assert herm_relerr(lower_to_full(Ss[k], ng, layout), So) <= tol, k
-    # the library's count of what crossed the link: every lower element, and
-    # with the full layout at most one block-sized triangle per block more
+    # the library's count of what reached host memory: every lower element,
+    # and with block copies of the full layout at most one block-sized
+    # triangle per block more
     st = h.stats()
     lower = 2 * 16 * sum(h.num_g(k) * (h.num_g(k) + 1) // 2 for k in range(p.n_k))
     if layout == fl.LAYOUT_LOWER_PACKED:
@@ -462,26 +477,24 @@ def test_host_outputs_every_lower_element_copied(layout, precision, tol):
     assert 2 * p.n_k <= st["copy_ops"] <= 320 + p.n_k
 
 
-def test_many_host_outputs_wider_copy_blocks():
-    # 48 k-points into pinned host memory in one call: the column blocks widen
-    # (5 per matrix instead of 32) so that the call enqueues at most ~320
-    # copies and returns before they run (the device's work queue holds about a
-    # thousand operations); every lower element must still arrive
+@pytest.mark.parametrize("memory", ["pinned", "pageable"])
+def test_many_host_outputs(memory):
+    # 48 k-points into host memory (pinned or pageable) in one call: the
+    # column blocks widen (5 per matrix instead of 32) so that the call
+    # enqueues at most ~320 copies and returns before they run (the device's
+    # work queue holds about a thousand operations); every lower element must
+    # still arrive
     torch = torch_cuda()
     sizes = tuple(300 + 37 * (i % 11) for i in range(48))
     p = inputs.small(91, n_atoms=2, n_types=2, lmax=2, n_target=sizes)
     h = fl.from_problem(p, fl.default_options(precision=fl.PREC_EMU, operands=fl.OPERANDS_FACTORED))
     _, A, B = run_ab(p, h)
-    Hs, Ss = [], []
-    for k in range(p.n_k):
-        ng = h.num_g(k)
-        Hs.append(torch.full((ng * ng,), float("nan"), dtype=torch.complex128).pin_memory())
-        Ss.append(torch.full((ng * ng,), float("nan"), dtype=torch.complex128).pin_memory())
+    Hs, Ss = _nan_outputs(torch, h, p, fl.LAYOUT_LOWER_FULL, memory)
     h.build_HS(p.T, p.atom_slot, p.U, A, B, Hs, Ss)
     h.sync()
     st = h.stats()
-    assert st["copy_ops"] <= 320 + p.n_k, st["copy_ops"]
     lower = 2 * 16 * sum(h.num_g(k) * (h.num_g(k) + 1) // 2 for k in range(p.n_k))
+    assert st["copy_ops"] <= 320 + p.n_k, st["copy_ops"]
     assert lower < st["bytes_d2h"] <= 1.6 * lower
     for k in (0, 1, 17, 46, 47):
         Ho, So = oracle_hs(p, k)
@@ -492,7 +505,7 @@ def test_many_host_outputs_wider_copy_blocks():
         ng = h.num_g(k)
         L = np.tril(np.ones((ng, ng), dtype=bool))
         for X in (Hs[k], Ss[k]):
-            assert not np.isnan(X.numpy().reshape(ng, ng).T[L]).any(), k
+            assert not np.isnan(_host(X).reshape(ng, ng).T[L]).any(), k
 
 
 def test_bad_calls_return_codes_not_faults():
