@@ -523,10 +523,24 @@ def eigh_leg(h, H, S, ng, layout, args):
     # reduction to standard form (4 n^3), tridiagonalisation (16/3 n^3),
     # back-transformations of the eigenvectors (8 n^3 + 4 n^3)
     nominal = 22.7 * float(ng) ** 3
+    # the CPU beside it: scipy's generalised Hermitian solver (LAPACK zhegvd) on
+    # the leading n_s x n_s blocks of the same H and S on the host cores (a
+    # leading block of a positive definite S is positive definite), scaled
+    # to n by the n^3 cost
+    import scipy.linalg as sl
+    n_s = min(ng, 2048)
+    Hc = Hf[:n_s, :n_s].cpu().numpy()
+    Sc = Sf[:n_s, :n_s].cpu().numpy()
+    t0 = time.perf_counter()
+    sl.eigh(Hc, Sc)
+    t_cpu = time.perf_counter() - t0
     return {"n": ng, "ms": round(ms, 1), "solver": "cuSOLVER zhegvd, FP64 (flapw_eigh)",
             "lambda_min": float(w[0]), "lambda_max": float(w[-1]),
             "residual_16_vectors": res, "s_orthonormality_16_vectors": orth,
-            "nominal_tflops": round(nominal / (ms * 1e-3) / 1e12, 3)}
+            "nominal_tflops": round(nominal / (ms * 1e-3) / 1e12, 3),
+            "cpu": {"solver": "scipy.linalg.eigh (LAPACK zhegvd)", "n_sample": n_s,
+                    "s": round(t_cpu, 2), "cores": os.cpu_count(),
+                    "scaled_to_n_s": round(t_cpu * (ng / n_s) ** 3, 1)}}
 
 
 def spherical_part(T, lmax):
