@@ -225,8 +225,15 @@ def run_ours(args):
     ws, rank, local = dist_env()
     if ws > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        # one GPU per rank (more ranks than GPUs share them round-robin, which
+        # only the host-side gloo backend allows: no rank's kernels wait on
+        # another's)
+        dev_i = local % torch.cuda.device_count()
+        torch.cuda.set_device(dev_i)
+        if args.dist_backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", dev_i))
+        else:
+            dist.init_process_group("gloo")
     else:
         torch.cuda.set_device(0)
     fl.build()
@@ -741,6 +748,8 @@ def main():
                          "its spherical part")
     ap.add_argument("--s-method", choices=["contraction", "legendre"], default="contraction",
                     help="S by the slice contraction (default) or by the addition theorem")
+    ap.add_argument("--dist-backend", choices=["nccl", "gloo"], default="nccl",
+                    help="process group of N > 1 ranks (the timing reduction and barriers only)")
     ap.add_argument("--eigh", action="store_true",
                     help="also solve H c = lambda S c for k-point 0 (flapw_eigh; S must be positive "
                          "definite: 2 N_A N_L >= N_G, e.g. config 3)")
