@@ -1343,7 +1343,7 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     }
   }
   // (the call that tunes times whole halves: no split there)
-  const bool h_split = h_host && !(tune && h->tuned_shape != shape) && !h_sph;
+  const bool h_split = h_host && !(tune && h->tuned_shape != shape);
   Half hH, hHb, hS;
   if (int rc = ensure_tiles(h, probs, nk, h->rows, &hH, &hS, 0, n_slots, h_split, &hHb)) return rc;
   hH.row0 = 0;
@@ -1622,10 +1622,16 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     }
     if (h_zero) {
       // T is its spherical part: no factorisation, operands or contraction for H
+      // (with H in host memory in two launches split by column, as the contraction)
       CK(h, cudaEventRecord(h->ev[10], st), "cudaEventRecord");
       CK(h, cudaEventRecord(h->ev[11], st), "cudaEventRecord");
       CK(h, launch_hlegendre(hl, h->d_f64_tiles.as<F64Tile>() + hH.f64_t0, hH.f64_nt, false, st),
          "H (addition theorem) launch");
+      if (h_split) {
+        CK(h, cudaEventRecord(h->ev[18], st), "cudaEventRecord");
+        CK(h, launch_hlegendre(hl, h->d_f64_tiles.as<F64Tile>() + hHb.f64_t0, hHb.f64_nt, false, st, hH.f64_nt > 0),
+           "H (addition theorem) launch");
+      }
       CK(h, cudaEventRecord(h->ev[12], st), "cudaEventRecord");
     } else if (tc_ops) {
       OpGemmArgs ga{};
@@ -1673,14 +1679,22 @@ int flapw_build_HS(flapw_handle h, const double* T, int n_slots, const int* atom
     if (!h_zero) {
       const bool h_presliced = tc_ops && !alg3;
       if (!h_presliced) CK(h, cudaEventRecord(h->ev[10], st), "cudaEventRecord");
-      if (int rc = enqueue_contraction(h, hH, 0, st, 11, h_split ? 18 : 12, h_presliced)) return rc;
-      if (h_split)
-        if (int rc = enqueue_contraction(h, hHb, 0, st, -1, 12, true)) return rc;
-      // the spherical part of T by the addition theorem, added to the contraction of the rest
+      // with FLAPW_H_SPHERICAL the spherical part of T by the addition theorem is
+      // added to each part's columns after the contraction of the rest
+      const int ev_first = h_split ? 18 : 12;
+      if (int rc = enqueue_contraction(h, hH, 0, st, 11, ev_first, h_presliced)) return rc;
       if (h_sph) {
         CK(h, launch_hlegendre(hl, h->d_f64_tiles.as<F64Tile>() + hH.f64_t0, hH.f64_nt, true, st),
            "H (addition theorem) launch");
-        CK(h, cudaEventRecord(h->ev[12], st), "cudaEventRecord");
+        CK(h, cudaEventRecord(h->ev[ev_first], st), "cudaEventRecord");
+      }
+      if (h_split) {
+        if (int rc = enqueue_contraction(h, hHb, 0, st, -1, 12, true)) return rc;
+        if (h_sph) {
+          CK(h, launch_hlegendre(hl, h->d_f64_tiles.as<F64Tile>() + hHb.f64_t0, hHb.f64_nt, true, st, hH.f64_nt > 0),
+             "H (addition theorem) launch");
+          CK(h, cudaEventRecord(h->ev[12], st), "cudaEventRecord");
+        }
       }
     }
     // Host-memory outputs go back on the copy stream: S beside the H work; with

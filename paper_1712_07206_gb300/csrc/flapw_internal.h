@@ -316,7 +316,10 @@ struct HLegArgs {
                            // evaluate in double-float; null: in FP64
 };
 // add: the spherical part is added to the lower triangle already written.
-cudaError_t launch_hlegendre(const HLegArgs& a, const F64Tile* tiles, int n_tiles, bool add, cudaStream_t st);
+// inputs_ready: a previous launch of this build_HS already split the inputs
+// into double-float (a second part of the tiles).
+cudaError_t launch_hlegendre(const HLegArgs& a, const F64Tile* tiles, int n_tiles, bool add, cudaStream_t st,
+                             bool inputs_ready = false);
 cudaError_t launch_khat(const Geom& geo, const GData& gd, double* khat, cudaStream_t st);
 cudaError_t launch_slegendre(const SLegArgs& a, const F64Tile* tiles, int n_tiles, cudaStream_t st);
 

@@ -625,11 +625,12 @@ __global__ void __launch_bounds__(kDfThreads) hlegendre_df_kernel(HLegArgs a, co
 
 }  // namespace
 
-cudaError_t launch_hlegendre(const HLegArgs& a, const F64Tile* tiles, int n_tiles, bool add, cudaStream_t st) {
+cudaError_t launch_hlegendre(const HLegArgs& a, const F64Tile* tiles, int n_tiles, bool add, cudaStream_t st,
+                             bool inputs_ready) {
   if (n_tiles == 0) return cudaSuccess;
   if (a.lmax < 0 || a.lmax > kMaxLmax) return cudaErrorInvalidValue;
   if (a.dfw) {
-    hlegendre_split_kernel<<<(unsigned)((a.g_total + 127) / 128), 128, 0, st>>>(a);
+    if (!inputs_ready) hlegendre_split_kernel<<<(unsigned)((a.g_total + 127) / 128), 128, 0, st>>>(a);
     hlegendre_df_kernel<<<n_tiles, kDfThreads, 0, st>>>(a, tiles, add ? 1 : 0);
   } else {
     hlegendre_kernel<<<n_tiles, 256, 0, st>>>(a, tiles, add ? 1 : 0);

@@ -132,3 +132,30 @@ def test_config2_with_spherical_T_has_no_H_contraction(precision, tol):
     es = np.linalg.norm(columns_from_lower(S, ng, 0, cols) - So) / np.linalg.norm(So)
     assert eh <= tol and es <= tol, (eh, es)
     h.destroy()
+
+
+@pytest.mark.parametrize("precision,tol", [(fl.PREC_EMU, TOL_EMU), (fl.PREC_FP64, TOL_F64)])
+@pytest.mark.parametrize("r", [0, 5])
+def test_spherical_split_host_outputs(precision, tol, r):
+    # H and S into pinned host memory: the H work (the contraction of the rest
+    # and the addition theorem, or the addition theorem alone) runs in two
+    # launches split by column so that the first part's columns go back while
+    # the second runs; the second k-point has fewer than 64 plane waves, so
+    # its first part is empty
+    p = inputs.small(47, n_atoms=3, n_types=2, lmax=4, n_target=(700, 40))
+    p.T, t_sph = _spherical_plus_rest(p, r, seed=11 + r)
+    opt = fl.default_options(precision=precision, operands=fl.OPERANDS_FACTORED, h_method=fl.H_SPHERICAL)
+    h = fl.from_problem(p, opt)
+    _, A, B = run_ab(p, h)
+    h.set_spherical_T(t_sph)
+    Hs = [alloc_out(h.num_g(k), 0, True) for k in range(p.n_k)]
+    Ss = [alloc_out(h.num_g(k), 0, True) for k in range(p.n_k)]
+    h.build_HS(p.T, p.atom_slot, p.U, A, B, Hs, Ss)
+    h.sync()
+    assert h.num_g(1) < 64
+    for k in range(p.n_k):
+        Ho, So = oracle_hs(p, k)
+        ng = Ho.shape[0]
+        assert herm_relerr(lower_to_full(Hs[k], ng, 0), Ho) <= tol, k
+        assert herm_relerr(lower_to_full(Ss[k], ng, 0), So) <= tol, k
+    h.destroy()
