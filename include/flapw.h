@@ -48,7 +48,8 @@ typedef struct flapw_ctx* flapw_handle;
 #define FLAPW_ERR_ARG (-1)         /* invalid argument: the message names it */
 #define FLAPW_ERR_CUDA (-2)        /* a CUDA runtime or driver call failed */
 #define FLAPW_ERR_OOM (-3)         /* device memory could not be allocated */
-#define FLAPW_ERR_FACTOR (-4)      /* a T block has a zero 2x2 pivot and cannot be factorised */
+#define FLAPW_ERR_FACTOR (-4)      /* a factorisation failed: a T block with a zero 2x2 pivot, or
+                                      (flapw_eigh) an S that is not positive definite */
 #define FLAPW_ERR_TIMEOUT (-5)     /* a bounded device-side wait ran out; results are invalid */
 #define FLAPW_ERR_STATE (-6)       /* call out of order (e.g. a handle made for flapw_herk only) */
 #define FLAPW_ERR_UNSUPPORTED (-7) /* size outside what the kernels support */
@@ -93,7 +94,8 @@ typedef struct flapw_ctx* flapw_handle;
  * drops exact zero pivots, so a rest confined to r rows and columns of each
  * slot contracts over K = r per atom; a rest that is exactly zero (T is its
  * spherical part) runs no factorisation, operands or contraction for H.
- * Needs FLAPW_OPERANDS_FACTORED; the addition-theorem part runs in FP64. */
+ * Needs FLAPW_OPERANDS_FACTORED; the addition-theorem part runs in FP64 on
+ * the FP64 path and in double-float FP32 pairs on the emulated path. */
 #define FLAPW_H_SPHERICAL 2
 /* FLAPW_H_ALG1: the paper's Alg. 1 (Sec. 3) on the engine of FLAPW_H_ALG3.  Per
  * slot it tries the Cholesky factorisation T^AA = C C^H (FP64 on the device);
@@ -128,7 +130,8 @@ typedef struct flapw_options {
                      FLAPW_S_LEGENDRE: S by the addition theorem (requires
                      FLAPW_OPERANDS_FACTORED; in FP64 on the FP64 path, in
                      double-float FP32 pairs on the emulated path) */
-  int h_method;   /* FLAPW_H_FACTORED (default) or FLAPW_H_ALG3 */
+  int h_method;   /* FLAPW_H_FACTORED (default), FLAPW_H_ALG3, FLAPW_H_SPHERICAL or
+                     FLAPW_H_ALG1 */
   int pipeline;   /* emulated contraction's load pipeline: 0 by size (5 stages of one
                      64-wide K chunk above N_G 8192, else 3 stages of two), 1 the
                      3-stage shape, 2 the 5-stage shape; results are identical */
@@ -176,7 +179,7 @@ typedef struct flapw_stats {
   double flops_herk;   /* 16 N_A N_L sum_k N_G(k)^2: H and S in the Hermitian rank-K count */
   double flops_tensor; /* tensor-core flops executed by the contraction */
   int64_t k_total;     /* inner dimension of the H contraction: K = 2 N_A N_L
-                          (3 N_A N_L with FLAPW_H_ALG3) */
+                          (3 N_A N_L with FLAPW_H_ALG3 and FLAPW_H_ALG1) */
   int n_pos;           /* rows of the H operand with sigma = +1 (all atoms) */
   int n_neg;           /* rows with sigma = -1 */
   int n_pivot2;        /* 2x2 pivots taken by the factorisation (all slots) */
