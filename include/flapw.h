@@ -293,8 +293,12 @@ int flapw_build_AB(flapw_handle h, const double* radial, void* A, void* B, void*
  * generalised to indefinite T), so that H = Z^H diag(sigma) Z with
  * Z_a = C^H [A_a; B_a] and S = Z_S^H Z_S with Z_S,a = [A_a; U B_a]: one
  * lower-triangle rank-K contraction each, K = 2 N_A N_L (Fig. agg stacking).
- * With options.h_method = FLAPW_H_ALG3 H is formed without the factorisation
- * as described at FLAPW_H_ALG3.
+ * The other H methods (FLAPW_H_ALG3, FLAPW_H_ALG1, FLAPW_H_SPHERICAL) form H
+ * as described at their definitions.
+ * The call returns once its work is enqueued: T, U and the slots are staged
+ * in one of two pinned buffers, each reused only after the copies of the call
+ * that last used it have run, so a third call may wait for the first; the
+ * host-memory outputs are complete after flapw_sync() or the stream.
  * A zero 1x1 pivot (a column that is zero on and below the diagonal after
  * the previous steps) contributes nothing and its row is dropped from Z.
  * Errors: FLAPW_ERR_OOM if the workspaces do not fit (returned here); a
